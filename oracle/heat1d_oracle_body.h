@@ -1,0 +1,84 @@
+/*
+ * Body of the oracle, written once for a generic REAL and included by
+ * heat1d_oracle.c for double (suffix _f64) and for float (suffix _f32).
+ * TEST INFRASTRUCTURE ONLY (see heat1d_oracle.c).
+ */
+
+/* Synchronous run, Section 2 Eq. (eqn:sync) with Dirichlet ends.
+ * Double-buffered Jacobi sweep; every interior point is updated from the
+ * previous time level only.  out receives u(K) (N values). */
+int SUF(oracle_sync)(int64_t N, REAL r, REAL c1, REAL cN, const REAL* u0, int64_t K, REAL* out) {
+  if (N < 3 || K < 0 || !u0 || !out) return ORACLE_EINVAL;
+  REAL* a = (REAL*)malloc(sizeof(REAL) * (size_t)N);
+  REAL* b = (REAL*)malloc(sizeof(REAL) * (size_t)N);
+  if (!a || !b) { free(a); free(b); return ORACLE_ENOMEM; }
+  memcpy(a, u0, sizeof(REAL) * (size_t)N);
+  a[0] = c1;
+  a[N - 1] = cN;
+  for (int64_t k = 0; k < K; ++k) {
+    for (int64_t i = 1; i < N - 1; ++i) {
+      REAL uL = a[i - 1], u = a[i], uR = a[i + 1];
+      b[i] = FMA(r, (uR - (REAL)2 * u) + uL, u);
+    }
+    b[0] = c1;
+    b[N - 1] = cN;
+    REAL* t = a; a = b; b = t;
+  }
+  memcpy(out, a, sizeof(REAL) * (size_t)N);
+  free(a);
+  free(b);
+  return ORACLE_OK;
+}
+
+/* Asynchronous run, Section 3 Eq. (eqn:async), as the switched linear system
+ * on the augmented state z(k) = [u(k); u(k-1); ...; u(k-q+1)].
+ *
+ * The last q+1 full states are kept in a ring hist[t mod (q+1)].  At step k a
+ * read that crosses a segment boundary takes the neighbour at time
+ * k - min(d, k), d taken from the trace; every other read takes time k.
+ * The new state goes into the slot of time k+1, which held time k-q: a time no
+ * read of step k can ask for.  out receives u(K).
+ *
+ * S = 1 (one segment) has no boundaries, and then trace may be NULL. */
+int SUF(oracle_async)(int64_t N, REAL r, REAL c1, REAL cN, int64_t S, int q, const REAL* u0, int64_t K,
+                      const uint8_t* trace, REAL* out) {
+  if (N < 3 || K < 0 || S < 1 || S > N || q < 1 || q > 255 || !u0 || !out) return ORACLE_EINVAL;
+  if (S > 1 && K > 0 && !trace) return ORACLE_EINVAL;
+  for (int64_t j = 0; S > 1 && j < K * (S - 1) * 2; ++j)
+    if (trace[j] >= q) return ORACLE_ETRACE;
+  int64_t Q = (int64_t)q + 1;
+  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S + 1));
+  int64_t* seg = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+  REAL* hist = (REAL*)malloc(sizeof(REAL) * (size_t)N * (size_t)Q);
+  if (!off || !seg || !hist) { free(off); free(seg); free(hist); return ORACLE_ENOMEM; }
+  oracle_segments(N, S, off);
+  for (int64_t s = 0; s < S; ++s)
+    for (int64_t i = off[s]; i < off[s + 1]; ++i) seg[i] = s;
+#define H(t, i) hist[(size_t)((t) % Q) * (size_t)N + (size_t)(i)]
+  for (int64_t i = 0; i < N; ++i) H(0, i) = u0[i];
+  H(0, 0) = c1;
+  H(0, N - 1) = cN;
+  for (int64_t k = 0; k < K; ++k) {
+    for (int64_t i = 1; i < N - 1; ++i) {
+      int64_t tL = k, tR = k;
+      if (seg[i - 1] != seg[i]) { /* segment seg[i] reads its left neighbour: boundary seg[i-1], side 1 */
+        int64_t d = trace[(k * (S - 1) + seg[i - 1]) * 2 + 1];
+        tL = k - (d < k ? d : k);
+      }
+      if (seg[i + 1] != seg[i]) { /* segment seg[i] reads its right neighbour: boundary seg[i], side 0 */
+        int64_t d = trace[(k * (S - 1) + seg[i]) * 2 + 0];
+        tR = k - (d < k ? d : k);
+      }
+      REAL uL = H(tL, i - 1), u = H(k, i), uR = H(tR, i + 1);
+      H(k + 1, i) = FMA(r, (uR - (REAL)2 * u) + uL, u);
+    }
+    H(k + 1, 0) = c1;
+    H(k + 1, N - 1) = cN;
+  }
+  for (int64_t i = 0; i < N; ++i) out[i] = H(K, i);
+#undef H
+  free(off);
+  free(seg);
+  free(hist);
+  return ORACLE_OK;
+}

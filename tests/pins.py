@@ -1,0 +1,160 @@
+"""Independent checks of the oracle: closed forms and brute force.
+
+Nothing here calls the oracle or the CUDA library.  Each helper restates what
+the mathematics fixes for the update of Section 2 (Eq. eqn:sync) and Section 3
+(Eq. eqn:async) in a form different from the oracle's sweep:
+
+* closed_form_sync: the discrete sine modes are eigenvectors of the FTCS
+  operator with Dirichlet ends; mode m decays by
+  lambda_m = 1 - 4 r sin^2(m pi dx / 2) per step, dx = 1/(N-1), and the linear
+  profile between c1 and cN is a fixed point.
+* brute_sync_fraction: the N x N matrix A of Eq. (eqn:sync), applied K times in
+  exact rational arithmetic.
+* brute_async_fraction: the switched system on the augmented state
+  z(k) = [u(k); u(k-1); ...; u(k-q+1)] with one explicit block matrix per step
+  built from the delays; times before 0 are served by z(0) = [u0; ...; u0].
+* brute_adjoint: gradients by the transposed products of those matrices.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+from scipy.fft import dst, idst
+
+
+def forced(u0, c1, cN):
+    u = np.array(u0, dtype=np.float64, copy=True)
+    u[0] = c1
+    u[-1] = cN
+    return u
+
+
+def closed_form_sync(u0, r, c1, cN, K):
+    """u(K) from the sine-mode expansion of u(0) - u_ss on the interior."""
+    u0 = forced(u0, c1, cN)
+    N = u0.size
+    n = N - 2
+    x = np.arange(N, dtype=np.float64) / (N - 1)
+    uss = c1 + (cN - c1) * x
+    f = (u0 - uss)[1:-1]
+    F = dst(f, type=1)
+    m = np.arange(1, n + 1, dtype=np.float64)
+    lam = 1.0 - 4.0 * r * np.sin(m * math.pi / (2.0 * (N - 1))) ** 2
+    # lam^K: lam may be negative for r > 1/4 and high modes
+    lamK = np.sign(lam) ** (K % 2) * np.exp(K * np.log(np.abs(lam))) if K > 0 else np.ones_like(lam)
+    out = uss.copy()
+    out[1:-1] += idst(F * lamK, type=1)
+    return out
+
+
+def _frac(v):
+    return Fraction(v) if not isinstance(v, Fraction) else v
+
+
+def sync_matrix_fraction(N, r):
+    r = _frac(r)
+    A = [[Fraction(0)] * N for _ in range(N)]
+    A[0][0] = Fraction(1)
+    A[N - 1][N - 1] = Fraction(1)
+    for i in range(1, N - 1):
+        A[i][i - 1] = r
+        A[i][i] = 1 - 2 * r
+        A[i][i + 1] = r
+    return A
+
+
+def matvec(A, x):
+    return [sum((a * b for a, b in zip(row, x) if a != 0), Fraction(0)) for row in A]
+
+
+def brute_sync_fraction(u0, r, c1, cN, K):
+    """A^K u(0), exact, with the ends forced first."""
+    u = [_frac(v) for v in u0]
+    u[0] = _frac(c1)
+    u[-1] = _frac(cN)
+    A = sync_matrix_fraction(len(u), r)
+    for _ in range(K):
+        u = matvec(A, u)
+    return u
+
+
+def segment_of(N, S):
+    base, extra = divmod(N, S)
+    seg, s, count = [], 0, 0
+    for s in range(S):
+        seg += [s] * (base + (1 if s < extra else 0))
+    return seg
+
+
+def async_step_matrix(N, r, S, q, dk):
+    """Block matrix (qN x qN) for one step of Eq. (eqn:async).
+
+    dk has shape (S-1, 2): dk[b][0] is the delay of segment b's read of its
+    right neighbour, dk[b][1] that of segment b+1's read of its left
+    neighbour.  Block j of z holds u(k-j).  Delays must already be clamped to
+    at most q-1 (the augmented state has q blocks)."""
+    r = _frac(r)
+    seg = segment_of(N, S)
+    M = [[Fraction(0)] * (q * N) for _ in range(q * N)]
+    M[0][0] = Fraction(1)
+    M[N - 1][N - 1] = Fraction(1)
+    for i in range(1, N - 1):
+        jl = int(dk[seg[i - 1]][1]) if seg[i - 1] != seg[i] else 0
+        jr = int(dk[seg[i]][0]) if seg[i + 1] != seg[i] else 0
+        M[i][i] += 1 - 2 * r
+        M[i][jl * N + i - 1] += r
+        M[i][jr * N + i + 1] += r
+    for j in range(1, q):  # shift the history down by one block
+        for i in range(N):
+            M[j * N + i][(j - 1) * N + i] = Fraction(1)
+    return M
+
+
+def brute_async_fraction(u0, r, c1, cN, S, q, trace):
+    """Exact u(K) of the switched system driven by trace (K, S-1, 2)."""
+    N = len(u0)
+    u = [_frac(v) for v in u0]
+    u[0] = _frac(c1)
+    u[-1] = _frac(cN)
+    z = u * q
+    trace = np.asarray(trace)
+    for k in range(trace.shape[0]):
+        M = async_step_matrix(N, r, S, q, trace[k])
+        z = matvec(M, z)
+    return z[:N]
+
+
+def brute_adjoint_float(u0, r, c1, cN, S, q, trace, u_obs):
+    """Loss and gradient w.r.t. u(0) through the transposed step matrices
+    (float64 products of the exact matrices).  Also returns dL/dr by the exact
+    derivative of each step matrix with respect to r."""
+    N = len(u0)
+    trace = np.asarray(trace)
+    K = trace.shape[0]
+    mats, dmats = [], []
+    for k in range(K):
+        M = np.array(async_step_matrix(N, r, S, q, trace[k]), dtype=np.float64)
+        mats.append(M)
+        # d M / d r: the r-dependent entries are +1 (neighbour reads) and -2 (self)
+        Mp = np.array(async_step_matrix(N, Fraction(1), S, q, trace[k]), dtype=np.float64)
+        M0 = np.array(async_step_matrix(N, Fraction(0), S, q, trace[k]), dtype=np.float64)
+        dmats.append(Mp - M0)
+    u = forced(u0, c1, cN)
+    zs = [np.tile(u, q)]
+    for M in mats:
+        zs.append(M @ zs[-1])
+    uK = zs[-1][:N]
+    e = uK - np.asarray(u_obs, dtype=np.float64)
+    loss = 0.5 * float(np.sum(e * e))
+    lam = np.zeros(q * N)
+    lam[1:N - 1] = e[1:N - 1]
+    gr = 0.0
+    for k in range(K - 1, -1, -1):
+        gr += float(lam @ (dmats[k] @ zs[k]))
+        lam = mats[k].T @ lam
+    g = lam.reshape(q, N).sum(axis=0)  # z(0) repeats u(0) in every block
+    g[0] = 0.0
+    g[-1] = 0.0
+    return loss, g, gr
