@@ -1,0 +1,360 @@
+"""Benchmark: grid-point updates/s of the synchronous and asynchronous FTCS
+runs on one GB300 per rank.
+
+Workload (the "sync vs async at scale" rod): N = 2^20 points in FP64,
+r = 0.25, c1 = -1, cN = 1, K = 1e5 steps, u(0) a sum of 16 sine modes
+(m uniform in [1, 512], amplitudes N(0, 1), seed = 1000 + rank), one segment
+per SM, delay window q = 3.
+
+One bench step is one pass of the whole path on that rod:
+  set-up (u(0) copied into the handle, ends forced)
+  -> synchronous run of K steps (persistent kernel, grid barrier every T steps)
+  -> asynchronous run of K steps (no barrier), delay trace recorded on device
+  -> replay of that trace (exact re-execution) .
+Updates per step = 3 * (N-2) * K.
+
+Under torchrun each rank runs its own rod on its own GPU (independent problems,
+no collective on the data path: weak scaling).  The CPU oracle arm
+(``--impl reference``) times the plain C oracle on a bounded sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/s, async vs sync, at stated error; % of HBM/SMEM roofline"
+UNIT = "updates/s"
+N_DEFAULT = 1 << 20
+K_DEFAULT = 100_000
+Q = 3
+# FP64 pipe: 1.25 TFLOP/s nominal for GB300 (recipe table) = 6.25e11 FP64
+# instructions/s at 2070 MHz; one update issues 3 of them (2 DFMA + 1 DADD).
+FP64_NOMINAL_TFLOPS = 1.25
+FP64_INSTR_PER_UPDATE = 3
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--N", type=int, default=N_DEFAULT)
+    p.add_argument("--K", type=int, default=K_DEFAULT)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+
+
+def oracle_sample(rod, seconds=10.0, S=152):
+    """Times the plain C oracle (single thread) on a bounded sample of the
+    workload: the synchronous sweep and the asynchronous replay on the full N
+    for Ks steps, Ks chosen for about `seconds` of CPU work."""
+    import oracle
+    N = rod.N
+    probe = 4
+    tr = np.zeros((probe, S - 1, 2), dtype=np.uint8)
+    t0 = time.perf_counter()
+    oracle.sync(rod.u0, rod.r, rod.c1, rod.cN, probe)
+    oracle.async_replay(rod.u0, rod.r, rod.c1, rod.cN, S, Q, probe, tr)
+    per_step = (time.perf_counter() - t0) / probe
+    Ks = max(2, int(seconds / max(per_step, 1e-9)))
+    from paper_1510_08982_gb300 import inputs
+    tr = inputs.delay_trace(Ks, S, Q, seed=0)
+    t0 = time.perf_counter()
+    oracle.sync(rod.u0, rod.r, rod.c1, rod.cN, Ks)
+    oracle.async_replay(rod.u0, rod.r, rod.c1, rod.cN, S, Q, Ks, tr)
+    dt = time.perf_counter() - t0
+    updates = 2 * (N - 2) * Ks
+    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "plain C oracle, one thread: synchronous sweep + asynchronous replay (seeded q=3 delays, "
+                      "S=%d) of the N=%d rod for %d steps each (%.1f s)" % (S, N, Ks, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1510_08982_gb300 import inputs
+    rod = inputs.sine_mode_rod(N=args.N, K=args.K, seed=1000)
+    for _ in range(args.warmup):
+        oracle_sample(rod, seconds=1.0)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(rod, seconds=8.0)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, 152),
+            "cpu_baseline": dict(last, value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def workload_config(args, S):
+    return {"workload": "sine-mode rod: N=%d FP64, r=0.25, c1=-1, cN=1, K=%d, 16 modes m~U[1,512] A~N(0,1), "
+                        "S=%d segments (one per SM), q=%d; step = sync + async (trace recorded) + replay"
+                        % (args.N, args.K, S, Q),
+            "N": args.N, "K": args.K, "segments": S, "q": Q,
+            "l2": "flushed between timed steps (256 MB write); the rod itself stays on-chip for the whole run"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1510_08982_gb300 import build, heat1d, inputs
+    build.build()
+    dev = torch.device("cuda", local)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    rod = inputs.sine_mode_rod(N=args.N, K=args.K, seed=1000 + rank)
+    N, K = rod.N, rod.K
+    M = N - 2
+    h = heat1d.Heat1d(N, rod.r, rod.c1, rod.cN, dtype="float64", segments=nsm, q=Q)
+    S = h.S
+    u0 = torch.tensor(rod.u0, dtype=torch.float64, device=dev)
+    trace = h.new_trace(K)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def step(evs=None):
+        """One pass: set-up, sync, async (trace), replay.  evs: 4 events
+        bracketing the three runs on the launching stream."""
+        h.set_u(u0)
+        if evs:
+            evs[0].record(stream)
+        h.run_sync(K)
+        if evs:
+            evs[1].record(stream)
+        h.set_u(u0)
+        h.run_async(K, trace)
+        if evs:
+            evs[2].record(stream)
+        h.set_u(u0)
+        h.replay(K, trace)
+        if evs:
+            evs[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    h.sync()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    t_sync = t_async = t_replay = total = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e_begin = torch.cuda.Event(enable_timing=True)
+        e_end = torch.cuda.Event(enable_timing=True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e_begin.record(stream)
+        step(evs)
+        e_end.record(stream)
+        e_end.synchronize()
+        total += e_begin.elapsed_time(e_end)
+        t_sync += evs[0].elapsed_time(evs[1])
+        t_async += evs[1].elapsed_time(evs[2])
+        t_replay += evs[2].elapsed_time(evs[3])
+    barrier()
+    clk = clocks.stop()
+    h.sync()
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    ms_per_step = total / args.steps
+    updates_per_step = 3 * M * K
+    value = world * updates_per_step / (ms_per_step * 1e-3)
+    per = {name: M * K / (t / args.steps * 1e-3) for name, t in
+           (("sync", t_sync), ("async", t_async), ("replay", t_replay))}
+
+    # --- error at the stated tolerance (untimed) -----------------------------------------
+    from scipy.fft import dst, idst
+    h.set_u(u0)
+    h.run_sync(K)
+    h.sync()
+    u_sync = h.get_u(device=False)
+    x = np.arange(N) / (N - 1)
+    uss = rod.c1 + (rod.cN - rod.c1) * x
+    f = (np.where(np.arange(N) == 0, rod.c1, np.where(np.arange(N) == N - 1, rod.cN, rod.u0)) - uss)[1:-1]
+    lam = 1.0 - 4.0 * rod.r * np.sin(np.arange(1, N - 1) * np.pi / (2.0 * (N - 1))) ** 2
+    exact = uss.copy()
+    exact[1:-1] += idst(dst(f, type=1) * np.exp(K * np.log(np.abs(lam))) * np.sign(lam) ** (K % 2), type=1)
+    err_sync = float(np.abs(u_sync - exact).max())
+    h.set_u(u0)
+    h.run_async(K, trace)
+    h.sync()
+    u_async = h.get_u(device=False)
+    h.set_u(u0)
+    h.replay(K, trace)
+    h.sync()
+    replay_exact = bool(np.array_equal(h.get_u(device=False), u_async))
+    async_vs_sync = float(np.abs(u_async - u_sync).max())
+    tr_host = trace.cpu().numpy()
+    hist = np.bincount(tr_host.reshape(-1), minlength=Q).tolist()
+
+    # --- e2e through the C ABI with host buffers ------------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        u_host = torch.tensor(rod.u0, dtype=torch.float64).pin_memory().numpy()
+        out_host = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+        tr_h = torch.empty(trace.numel(), dtype=torch.uint8).pin_memory().numpy().reshape(trace.shape)
+
+        def e2e_step():
+            h.set_u(u_host)
+            h.run_sync(K)
+            h.get_u(out_host, device=False)
+            h.set_u(u_host)
+            h.run_async(K, tr_h)
+            h.sync()
+            h.get_u(out_host, device=False)
+            h.set_u(u_host)
+            h.replay(K, tr_h)
+            h.sync()
+            h.get_u(out_host, device=False)
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        dt = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        tb = trace.numel()
+        e2e = {"value": world * updates_per_step / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 8 * N + tb, "d2h_bytes_per_step": 3 * 8 * N + tb,
+               "path": "heat1d_set_u/run_*/replay/get_u from pinned host buffers, host traces"}
+
+    # --- roofline of the dominant kernel (the asynchronous persistent kernel) -------------
+    peak_upd = FP64_NOMINAL_TFLOPS * 1e12 / 2 / FP64_INSTR_PER_UPDATE
+    achieved = per["async"]
+    roofline = {"bound": "alu", "kernel": "async_persistent_kernel<double,8>",
+                "achieved": achieved / 1e9, "peak": peak_upd / 1e9, "unit": "Gupdates/s",
+                "frac": achieved / peak_upd,
+                "peak_source": "recipe nominal FP64 1.25 TFLOP/s at 2070 MHz = 6.25e11 FP64-pipe instr/s, "
+                               "3 per update (2 DFMA + 1 DADD)",
+                "traffic": None,
+                "per_kernel": {k: {"Gupdates_per_s": v / 1e9, "frac": v / peak_upd} for k, v in per.items()}}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, S),
+            "sync_updates_per_s": per["sync"], "async_updates_per_s": per["async"],
+            "replay_updates_per_s": per["replay"],
+            "error": {"sync_vs_closed_form_max_abs": err_sync, "async_vs_sync_max_abs": async_vs_sync,
+                      "replay_bit_identical": replay_exact, "delay_histogram": hist},
+            "roofline": roofline, "clocks": clk, "e2e": e2e,
+            "gpu_launches": 6 * args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(rod, seconds=10.0, S=S)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

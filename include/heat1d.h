@@ -1,0 +1,149 @@
+/*
+ * heat1d.h -- C ABI of libheat1d, a GB300 (sm_103a) solver for the explicit
+ * forward-time, central-space (FTCS) update of the 1D heat equation in its
+ * synchronous and asynchronous forms.
+ *
+ * Method: Lee & Bhattacharya, "Asynchronous Parallel Computing Algorithm
+ * implemented in 1D Heat Equation with CUDA", arXiv:1510.08982.
+ *
+ *   Section 2, Eq. (eqn:sync):  u_i(k+1) = r u_{i+1}(k) + (1-2r) u_i(k) + r u_{i-1}(k),
+ *                               0 < r <= 1/2, Dirichlet ends u_1 = c1, u_N = c2 (here cN).
+ *   Section 3, Eq. (eqn:async): the same update where a neighbour value that
+ *                               lives in another processing element (PE) may be
+ *                               read from any of the q most recent steps.
+ *
+ * Conventions shared by every entry point:
+ *  - Storage is 0-based and contiguous: u[0] = c1 and u[N-1] = cN are never
+ *    updated (and are overwritten with c1, cN when a state is loaded).
+ *  - Arithmetic per interior point: v = fma(r, (u[i+1] - 2 u[i]) + u[i-1], u[i]),
+ *    the operation order of the paper's printed kernels (Section 4) with one
+ *    fused multiply-add.  F64 runs compute in double, F32 runs in float with r,
+ *    c1, cN rounded to float.
+ *  - The N points are split into S contiguous segments (the PEs of Section 2,
+ *    Fig. 1); the first N mod S segments hold one point more.  One CTA owns one
+ *    segment.  Asynchrony exists only across segment boundaries (Section 3).
+ *  - A delay trace is uint8[K][S-1][2]: entry (k, b, 0) is the delay d with
+ *    which segment b read its right neighbour's first point at step k, and
+ *    (k, b, 1) the delay with which segment b+1 read its left neighbour's last
+ *    point.  The value used was the neighbour's state at step k - d; every
+ *    recorded d is < q and <= k.
+ *  - Every run is enqueued on the handle's stream and returns at once; its
+ *    launch errors are returned directly, its device-side status (a timed-out
+ *    wait, a bad trace entry) by heat1d_sync().  Buffers passed in stay owned
+ *    by the caller; a pointer flagged on_device must be device memory of the
+ *    handle's device.  No C++ exception crosses this boundary.
+ *  - Thread safety: a handle must not be used from two host threads at once.
+ *    heat1d_last_error() is per host thread.
+ */
+#ifndef HEAT1D_H
+#define HEAT1D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct heat1d* heat1d_t;
+
+enum heat1d_dtype { HEAT1D_F32 = 0, HEAT1D_F64 = 1 };
+
+enum heat1d_status {
+  HEAT1D_OK = 0,
+  HEAT1D_ERR_INVAL = -1,        /* an argument is out of range */
+  HEAT1D_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  HEAT1D_ERR_TIMEOUT = -3,      /* a device-side wait exceeded spin_limit_ns */
+  HEAT1D_ERR_NOT_RESIDENT = -4, /* the segments cannot all be resident at once */
+  HEAT1D_ERR_TRACE = -5,        /* a replay trace entry is >= q */
+  HEAT1D_ERR_OOM = -6           /* device memory could not be allocated */
+};
+
+/* Run options.  Zero in a field means "choose automatically". */
+typedef struct heat1d_opts {
+  int64_t segments;      /* S, the number of segments (PEs).  0: one per SM. */
+  int32_t q;             /* delay window of the asynchronous run, 1..255 (Section 3's buffer
+                            length q).  0: 3. */
+  int32_t halo_steps;    /* T, steps advanced between two exchanges in the synchronous run
+                            (overlapped halos of width T).  0: automatic.  1: exchange and
+                            grid barrier after every step, as in Section 2. */
+  int32_t block_threads; /* threads per CTA for the compute warps.  0: automatic. */
+  int32_t elems_per_thread; /* points held in registers per thread (2, 4, 8 or 16).  0: automatic. */
+  int64_t spin_limit_ns; /* bound on every device-side wait.  0: 2e9 (2 s). */
+  int32_t stall_segment; /* fault injection for tests: when >= 0, that segment of an asynchronous
+                            run never publishes, so its neighbours' waits run out and the run
+                            ends with HEAT1D_ERR_TIMEOUT.  Default -1 (off). */
+  int32_t reserved[7];
+} heat1d_opts;
+
+/* Fills *o with the defaults (every field 0 except stall_segment = -1). */
+void heat1d_default_opts(heat1d_opts* o);
+
+/* Creates a handle for one rod of N points on the current CUDA device.
+ * Requires N >= 3, 0 < r <= 0.5 (Section 2's stability range) and
+ * dtype in {HEAT1D_F32, HEAT1D_F64}.  The state starts at zero with the ends
+ * set to c1 and cN.  Returns NULL on error (see heat1d_last_error). */
+heat1d_t heat1d_create(int64_t N, double r, double c1, double cN, int dtype);
+
+/* Frees the handle and its device memory.  NULL is accepted. */
+void heat1d_destroy(heat1d_t h);
+
+/* Message of the last error on this host thread ("" if none). */
+const char* heat1d_last_error(void);
+
+/* Sets the CUDA stream (a cudaStream_t; NULL is the legacy default stream). */
+int heat1d_set_stream(heat1d_t h, void* stream);
+
+/* Replaces the options.  Validates them against N; the segment split and the
+ * scratch buffers are rebuilt.  HEAT1D_ERR_INVAL if out of range. */
+int heat1d_set_opts(heat1d_t h, const heat1d_opts* o);
+int heat1d_get_opts(heat1d_t h, heat1d_opts* o);
+
+/* Number of segments S and, if offsets != NULL, the S+1 segment offsets
+ * (host array written by the call). */
+int64_t heat1d_num_segments(heat1d_t h, int64_t* offsets);
+
+/* Copies N values (dtype of the handle) into the state; u[0] and u[N-1] are
+ * then overwritten with c1 and cN.  on_device: 1 if u is device memory,
+ * 0 if host memory (then the call waits for the copy). */
+int heat1d_set_u(heat1d_t h, const void* u, int on_device);
+
+/* Copies the current state (N values) out.  With on_device = 0 the call waits
+ * for the stream. */
+int heat1d_get_u(heat1d_t h, void* u, int on_device);
+
+/* Synchronous run, Section 2 Eq. (eqn:sync): advances the state by K steps.
+ * One persistent cooperative launch; one CTA per segment holds its segment and
+ * T-wide halos in registers, exchanges the halos through global memory and
+ * meets the other CTAs at a grid-wide barrier every T steps.  The result is
+ * identical, bit for bit, to K single steps with a barrier after each. */
+int heat1d_run_sync(heat1d_t h, int64_t K);
+
+/* Asynchronous run, Section 3 Eq. (eqn:async): advances the state by K steps
+ * with no barrier.  Each segment publishes its two edge values after every
+ * step with a release store of its version counter and reads its neighbours'
+ * newest version v <= k (waiting only while v < k-q+1).  trace_out (may be
+ * NULL) receives the delays actually used, heat1d_trace_bytes(h, K) bytes in
+ * the layout above; trace_on_device says where it lives.  Host traces are
+ * complete when heat1d_sync() returns. */
+int heat1d_run_async(heat1d_t h, int64_t K, uint8_t* trace_out, int trace_on_device);
+
+/* Size in bytes of a trace of K steps: K * (S-1) * 2. */
+int64_t heat1d_trace_bytes(heat1d_t h, int64_t K);
+
+/* Replay of an asynchronous run, Section 3 Eq. (eqn:async) with the delays
+ * given: at step k a segment waits for, and uses, exactly the neighbour
+ * version k - min(d, k).  Same kernel as heat1d_run_async.  Entries >= q make
+ * the run return HEAT1D_ERR_TRACE from heat1d_sync() and leave the state
+ * unspecified. */
+int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device);
+
+/* Waits for the handle's stream and returns the device-side status of the
+ * runs enqueued since the previous heat1d_sync(): HEAT1D_OK,
+ * HEAT1D_ERR_TIMEOUT or HEAT1D_ERR_TRACE (HEAT1D_ERR_CUDA on a CUDA error). */
+int heat1d_sync(heat1d_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEAT1D_H */

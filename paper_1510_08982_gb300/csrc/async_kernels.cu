@@ -1,0 +1,327 @@
+// async_kernels.cu -- the asynchronous run of Section 3, Eq. (eqn:async), and
+// its exact replay, as one persistent cooperative launch with no barrier
+// between CTAs.
+//
+// One CTA owns one segment (a PE of Fig. 1).  Its compute warps hold the
+// segment plus one halo point per side in registers and step with no
+// asynchrony inside the CTA (Section 3).  One extra warp per CTA is the
+// "network": it publishes the segment's two edge values of every version to
+// global rings (release store of the segment's version counter) and copies
+// the neighbours' published versions into a ring in shared memory (the
+// buffer of Section 3 that keeps the q most recent values received).
+//
+// At step k a compute warp takes, from that local buffer, the newest
+// neighbour version v <= k; it waits only while v < k-q+1 (bounded delay,
+// k* in {k, ..., k-q+1}).  It records d = k - v for the trace.  In replay mode
+// it waits for, and takes, exactly v = k - min(d, k) from the given trace.
+//
+// Flow control: a segment cannot start step k until both neighbours have
+// published version k-q+1, so no two neighbours drift more than q steps
+// apart, and a ring of R >= 2q versions is never overwritten while a reader
+// may still need the slot.
+#include <algorithm>
+
+#include "common.cuh"
+#include "impl.h"
+
+namespace heat1d_impl {
+using namespace heat1d_dev;
+
+namespace {
+
+template <typename real>
+struct AsyncShared {
+  TileShared<real> tile;
+  real lring[kMaxRing];  // left neighbour's right-edge values, version v at v & (R-1)
+  real rring[kMaxRing];  // right neighbour's left-edge values
+  real own_l[kMaxRing];  // this segment's first point per version, for the comm warp
+  real own_r[kMaxRing];  // this segment's last point per version
+  int lavail, ravail;    // newest neighbour version held in lring / rring (-1: none)
+  int own_l_ver, own_r_ver;  // newest own version handed to the comm warp
+  int compute_done;          // 1: finished, 2: aborted
+};
+
+// Waits for the neighbour version this step needs and returns its value.
+// Returns false if the wait ran out or the run failed elsewhere.
+template <typename real>
+__device__ __forceinline__ bool fetch_halo(const SegmentRun& a, const int* avail, const real* ring, int k,
+                                           const uint8_t* trace_in, uint8_t* trace_out, size_t tidx, int d_replay,
+                                           real& value) {
+  int need;
+  if (trace_in) {
+    if (d_replay >= a.q) {
+      raise_status(a.status, HEAT1D_ERR_TRACE);
+      return false;
+    }
+    need = k - min(d_replay, k);
+  } else {
+    need = max(k - a.q + 1, 0);
+  }
+  int V = ld_acquire_cta_shared(avail);
+  if (V < need) {
+    const uint64_t t0 = global_timer_ns();
+    unsigned spins = 0;
+    while ((V = ld_acquire_cta_shared(avail)) < need) {
+      if ((++spins & 63u) == 0) {
+        if (status_failed(a.status)) return false;
+        if (static_cast<int64_t>(global_timer_ns() - t0) > a.spin_limit_ns) {
+          raise_status(a.status, HEAT1D_ERR_TIMEOUT);
+          return false;
+        }
+      }
+    }
+  }
+  const int vsel = trace_in ? need : min(V, k);
+  value = ring[vsel & (a.R - 1)];
+  if (trace_out) trace_out[tidx] = static_cast<uint8_t>(k - vsel);
+  return true;
+}
+
+// The communication warp's loop (one thread).
+template <typename real>
+__device__ void comm_loop(const SegmentRun& a, AsyncShared<real>& sh, int s) {
+  const int R = a.R, S = a.S;
+  const int K = static_cast<int>(a.K);
+  real* rings = static_cast<real*>(a.rings);
+  real* my_l = rings + (static_cast<size_t>(s) * 2 + 0) * R;
+  real* my_r = rings + (static_cast<size_t>(s) * 2 + 1) * R;
+  const real* nb_l = s > 0 ? rings + (static_cast<size_t>(s - 1) * 2 + 1) * R : nullptr;     // left nbr's right edge
+  const real* nb_r = s + 1 < S ? rings + (static_cast<size_t>(s + 1) * 2 + 0) * R : nullptr; // right nbr's left edge
+  int* my_prog = a.prog + static_cast<size_t>(s) * kProgStride;
+  const int* lprog = s > 0 ? a.prog + static_cast<size_t>(s - 1) * kProgStride : nullptr;
+  const int* rprog = s + 1 < S ? a.prog + static_cast<size_t>(s + 1) * kProgStride : nullptr;
+  const bool stalled = s == a.stall_segment;
+
+  int pub = -1, lseen = -1, rseen = -1;
+  uint64_t t_idle = global_timer_ns();
+  unsigned spins = 0;
+  while (true) {
+    bool busy = false;
+    // Publish the versions the compute warps have produced.
+    const int w = min(ld_acquire_cta_shared(&sh.own_l_ver), ld_acquire_cta_shared(&sh.own_r_ver));
+    if (!stalled && w > pub) {
+      for (int x = max(pub + 1, w - R + 1); x <= w; ++x) {
+        const int j = x & (R - 1);
+        st_cg(my_l + j, sh.own_l[j]);
+        st_cg(my_r + j, sh.own_r[j]);
+      }
+      st_release_gpu(my_prog, w);
+      pub = w;
+      busy = true;
+    }
+    // Pull the neighbours' new versions into the local buffers.
+    if (lprog) {
+      const int P = ld_acquire_gpu(lprog);
+      if (P > lseen) {
+        for (int x = max(lseen + 1, P - R + 1); x <= P; ++x) sh.lring[x & (R - 1)] = ld_cg(nb_l + (x & (R - 1)));
+        st_release_cta_shared(&sh.lavail, P);
+        lseen = P;
+        busy = true;
+      }
+    }
+    if (rprog) {
+      const int P = ld_acquire_gpu(rprog);
+      if (P > rseen) {
+        for (int x = max(rseen + 1, P - R + 1); x <= P; ++x) sh.rring[x & (R - 1)] = ld_cg(nb_r + (x & (R - 1)));
+        st_release_cta_shared(&sh.ravail, P);
+        rseen = P;
+        busy = true;
+      }
+    }
+    const int done = ld_acquire_cta_shared(&sh.compute_done);
+    if (done == 2 || (done == 1 && (pub >= K || stalled))) break;
+    if (busy) {
+      t_idle = global_timer_ns();
+    } else if ((++spins & 63u) == 0) {
+      if (status_failed(a.status)) break;
+      if (static_cast<int64_t>(global_timer_ns() - t_idle) > a.spin_limit_ns) {
+        raise_status(a.status, HEAT1D_ERR_TIMEOUT);
+        break;
+      }
+    }
+  }
+}
+
+template <typename real, int E>
+__global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_persistent_kernel(SegmentRun a) {
+  __shared__ AsyncShared<real> sh;
+  const int s = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwc = (blockDim.x >> 5) - 1;  // compute warps; the last warp communicates
+  const unsigned nthreads_c = static_cast<unsigned>(nwc) * 32u;
+  if (tid == 0) {
+    sh.lavail = -1;
+    sh.ravail = -1;
+    sh.own_l_ver = -1;
+    sh.own_r_ver = -1;
+    sh.compute_done = 0;
+  }
+  __syncthreads();
+
+  if (warp == nwc) {
+    if (lane == 0) comm_loop<real>(a, sh, s);
+    return;
+  }
+
+  const int64_t N = a.N;
+  const int64_t a0 = a.seg_off[s];
+  const int L = static_cast<int>(a.seg_off[s + 1] - a0);
+  const int K = static_cast<int>(a.K);
+  const int S = a.S;
+  const real r = static_cast<real>(a.r), c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
+  const real* __restrict__ uin = static_cast<const real*>(a.u_in);
+  real* __restrict__ uout = static_cast<real*>(a.u_out);
+  const bool has_left = s > 0, has_right = s + 1 < S;
+
+  // Slot j holds global point a0 - 1 + j: slot 0 and slot L+1 are the halos.
+  real v[E];
+  unsigned fixed = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int slot = tid * E + e;
+    const int64_t g = a0 - 1 + slot;
+    real x = static_cast<real>(0);
+    if (slot >= 1 && slot <= L) x = uin[g];
+    if (g == 0) x = c1;
+    if (g == N - 1) x = cN;
+    v[e] = x;
+    if (slot == 0 || slot >= L + 1 || g <= 0 || g >= N - 1) fixed |= 1u << e;
+  }
+  const bool warp_fixed = __any_sync(kFullMask, fixed != 0u);
+  const int t_first = 1 / E, e_first = 1 % E;  // slot 1: first own point
+  const int t_last = L / E, e_last = L % E;     // slot L: last own point
+  const int t_rh = (L + 1) / E, e_rh = (L + 1) % E;  // slot L+1: right halo
+
+  // Version 0 of the edges goes to the comm warp.
+  if (tid == t_first) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e == e_first) sh.own_l[0] = v[e];
+    st_release_cta_shared(&sh.own_l_ver, 0);
+  }
+  if (tid == t_last) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e == e_last) sh.own_r[0] = v[e];
+    st_release_cta_shared(&sh.own_r_ver, 0);
+  }
+
+  const uint8_t* trace_in = a.trace_in;
+  uint8_t* trace_out = a.trace_out;
+  const size_t tstride = static_cast<size_t>(S - 1) * 2;
+  const size_t tl = has_left ? static_cast<size_t>(s - 1) * 2 + 1 : 0;  // side 1 of boundary s-1
+  const size_t tr = static_cast<size_t>(s) * 2 + 0;                     // side 0 of boundary s
+  int dl_next = 0, dr_next = 0;
+  if (trace_in && K > 0) {
+    if (tid == 0 && has_left) dl_next = __ldg(trace_in + tl);
+    if (tid == t_rh && has_right) dr_next = __ldg(trace_in + tr);
+  }
+
+  int parity = 0;
+  bool aborted = false;
+  for (int k = 0; k < K; ++k) {
+    bool fail = false;
+    if (tid == 0 && has_left) {
+      const int d = dl_next;
+      if (trace_in && k + 1 < K) dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
+      real val;
+      if (fetch_halo<real>(a, &sh.lavail, sh.lring, k, trace_in, trace_out, static_cast<size_t>(k) * tstride + tl, d,
+                           val))
+        v[0] = val;
+      else
+        fail = true;
+    }
+    if (tid == t_rh && has_right) {
+      const int d = dr_next;
+      if (trace_in && k + 1 < K) dr_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tr);
+      real val;
+      if (fetch_halo<real>(a, &sh.ravail, sh.rring, k, trace_in, trace_out, static_cast<size_t>(k) * tstride + tr, d,
+                           val)) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (e == e_rh) v[e] = val;
+      } else {
+        fail = true;
+      }
+    }
+    const bool any_fail = warp_fixed
+                              ? tile_step<real, E, true>(v, fixed, r, sh.tile, parity, warp, lane, nwc, nthreads_c, fail)
+                              : tile_step<real, E, false>(v, fixed, r, sh.tile, parity, warp, lane, nwc, nthreads_c, fail);
+    parity ^= 1;
+    if (any_fail) {
+      aborted = true;
+      break;
+    }
+    const int ver = k + 1, j = ver & (a.R - 1);
+    if (tid == t_first) {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e == e_first) sh.own_l[j] = v[e];
+      st_release_cta_shared(&sh.own_l_ver, ver);
+    }
+    if (tid == t_last) {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e == e_last) sh.own_r[j] = v[e];
+      st_release_cta_shared(&sh.own_r_ver, ver);
+    }
+  }
+
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int slot = tid * E + e;
+    if (slot >= 1 && slot <= L) uout[a0 - 1 + slot] = v[e];
+  }
+  named_barrier_sync(1, nthreads_c);
+  if (tid == 0) st_release_cta_shared(&sh.compute_done, aborted ? 2 : 1);
+}
+
+template <typename real, int E>
+int launch_async_t(const SegmentRun& a, int threads, cudaStream_t st) {
+  SegmentRun args = a;
+  void* params[] = {&args};
+  cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(async_persistent_kernel<real, E>), dim3(a.S),
+                                              dim3(threads + 32), params, 0, st);
+  if (e == cudaErrorCooperativeLaunchTooLarge) {
+    cudaGetLastError();
+    return HEAT1D_ERR_NOT_RESIDENT;
+  }
+  return e == cudaSuccess ? HEAT1D_OK : HEAT1D_ERR_CUDA;
+}
+
+template <typename real, int E>
+int resident_t(int threads) {
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, async_persistent_kernel<real, E>, threads + 32, 0) !=
+      cudaSuccess)
+    return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * nsm;
+}
+
+}  // namespace
+
+int launch_async_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st) {
+  const bool f64 = dtype == HEAT1D_F64;
+  switch (E) {
+    case 2: return f64 ? launch_async_t<double, 2>(a, threads, st) : launch_async_t<float, 2>(a, threads, st);
+    case 4: return f64 ? launch_async_t<double, 4>(a, threads, st) : launch_async_t<float, 4>(a, threads, st);
+    case 8: return f64 ? launch_async_t<double, 8>(a, threads, st) : launch_async_t<float, 8>(a, threads, st);
+    case 16: return f64 ? launch_async_t<double, 16>(a, threads, st) : launch_async_t<float, 16>(a, threads, st);
+    default: return HEAT1D_ERR_INVAL;
+  }
+}
+
+int max_resident_async(int dtype, int E, int threads) {
+  const bool f64 = dtype == HEAT1D_F64;
+  switch (E) {
+    case 2: return f64 ? resident_t<double, 2>(threads) : resident_t<float, 2>(threads);
+    case 4: return f64 ? resident_t<double, 4>(threads) : resident_t<float, 4>(threads);
+    case 8: return f64 ? resident_t<double, 8>(threads) : resident_t<float, 8>(threads);
+    case 16: return f64 ? resident_t<double, 16>(threads) : resident_t<float, 16>(threads);
+    default: return 0;
+  }
+}
+
+}  // namespace heat1d_impl

@@ -1,0 +1,420 @@
+// heat1d_api.cu -- the C ABI of libheat1d (declared in include/heat1d.h).
+//
+// Argument checks, the segment split, scratch-buffer ownership and the choice
+// of launch shape live here; every step of the computation runs in the
+// kernels of sync_kernels.cu and async_kernels.cu.
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "heat1d.h"
+#include "impl.h"
+
+using heat1d_impl::SegmentRun;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return HEAT1D_ERR_CUDA;
+}
+
+#define HEAT1D_CUDA(call)                                \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+// Sets the two Dirichlet ends of a device state (Section 2: u_1 = c1, u_N = cN).
+template <typename real>
+__global__ void set_ends_kernel(real* u, int64_t N, double c1, double cN) {
+  if (threadIdx.x == 0) u[0] = static_cast<real>(c1);
+  if (threadIdx.x == 1) u[N - 1] = static_cast<real>(cN);
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct heat1d {
+  int64_t N = 0;
+  double r = 0, c1 = 0, cN = 0;
+  int dtype = HEAT1D_F64;
+  size_t esize = 8;
+  int device = 0, nsm = 0;
+  cudaStream_t stream = nullptr;
+  heat1d_opts opts{};
+
+  // resolved configuration
+  int S = 1, q = 3, R = 8, T = 1;
+  std::vector<int64_t> off;
+  int64_t Lmin = 0, Lmax = 0;
+
+  // device memory (owned)
+  void* u[2] = {nullptr, nullptr};
+  int cur = 0;
+  int64_t* d_off = nullptr;
+  void* edges = nullptr;
+  void* rings = nullptr;
+  int* prog = nullptr;
+  void* ctl = nullptr;  // [0]: grid barrier counter, [32]: status word (separate lines)
+  uint8_t* d_trace = nullptr;
+  size_t d_trace_bytes = 0;
+
+  unsigned* barrier() { return static_cast<unsigned*>(ctl); }
+  int* status() { return static_cast<int*>(ctl) + 32; }
+};
+
+namespace {
+
+void free_scratch(heat1d* h) {
+  cudaFree(h->d_off);
+  cudaFree(h->edges);
+  cudaFree(h->rings);
+  cudaFree(h->prog);
+  h->d_off = nullptr;
+  h->edges = nullptr;
+  h->rings = nullptr;
+  h->prog = nullptr;
+}
+
+// Resolves the options against N and (re)allocates the scratch buffers.
+int configure(heat1d* h, const heat1d_opts& o) {
+  if (o.segments < 0 || o.q < 0 || o.q > 255 || o.halo_steps < 0 || o.block_threads < 0 ||
+      o.elems_per_thread < 0 || o.spin_limit_ns < 0)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: negative or out-of-range option");
+  if (o.elems_per_thread && o.elems_per_thread != 2 && o.elems_per_thread != 4 && o.elems_per_thread != 8 &&
+      o.elems_per_thread != 16)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: elems_per_thread must be 2, 4, 8 or 16");
+  if (o.block_threads % 32 != 0 || o.block_threads > 1024)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: block_threads must be a multiple of 32, at most 1024");
+  int64_t S = o.segments ? o.segments : h->nsm;
+  S = std::min<int64_t>(S, h->N);
+  if (S < 1 || S > INT_MAX) return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: bad segment count");
+
+  std::vector<int64_t> off(S + 1);
+  const int64_t base = h->N / S, extra = h->N % S;
+  int64_t pos = 0;
+  for (int64_t s = 0; s < S; ++s) {
+    off[s] = pos;
+    pos += base + (s < extra ? 1 : 0);
+  }
+  off[S] = pos;
+  const int64_t Lmax = base + (extra ? 1 : 0), Lmin = base;
+
+  const int q = o.q ? o.q : 3;
+  int R = 1;
+  while (R < 2 * q) R <<= 1;
+  if (R > heat1d_impl::kMaxRing) return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: q too large");
+  int T = o.halo_steps ? o.halo_steps : 32;
+  if (T > Lmin) {
+    if (o.halo_steps) return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: halo_steps exceeds the shortest segment");
+    T = static_cast<int>(Lmin);
+  }
+  if (T < 1) T = 1;
+
+  free_scratch(h);
+  h->S = static_cast<int>(S);
+  h->q = q;
+  h->R = R;
+  h->T = T;
+  h->off = off;
+  h->Lmin = Lmin;
+  h->Lmax = Lmax;
+  h->opts = o;
+  if (h->opts.spin_limit_ns == 0) h->opts.spin_limit_ns = 2000000000LL;
+  HEAT1D_CUDA(cudaMalloc(&h->d_off, sizeof(int64_t) * (S + 1)));
+  HEAT1D_CUDA(cudaMemcpy(h->d_off, off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice));
+  HEAT1D_CUDA(cudaMalloc(&h->edges, h->esize * 2 * S * 2 * T));
+  HEAT1D_CUDA(cudaMalloc(&h->rings, h->esize * S * 2 * R));
+  HEAT1D_CUDA(cudaMalloc(&h->prog, sizeof(int) * S * heat1d_impl::kProgStride));
+  return HEAT1D_OK;
+}
+
+// Launch shape for a tile of `slots` points: the fewest points per thread E
+// whose thread count fits the kernel's CTA limit minus `reserved` threads (the
+// asynchronous kernel's communication warp), unless E or the thread count is
+// forced by the options.
+int pick_shape(const heat1d* h, int64_t slots, int reserved, int* E, int* threads) {
+  const int forced_E = h->opts.elems_per_thread;
+  const int Es[4] = {2, 4, 8, 16};
+  for (int i = 0; i < 4; ++i) {
+    const int e = Es[i];
+    if (forced_E && e != forced_E) continue;
+    const int64_t limit = heat1d_impl::max_tile_threads(static_cast<int>(h->esize), e) - reserved;
+    int64_t t = std::max<int64_t>(round_up((slots + e - 1) / e, 32), 32);
+    if (h->opts.block_threads) {
+      if (h->opts.block_threads < t) continue;
+      t = h->opts.block_threads;
+    }
+    if (t <= limit) {
+      *E = e;
+      *threads = static_cast<int>(t);
+      return HEAT1D_OK;
+    }
+  }
+  return fail(HEAT1D_ERR_INVAL,
+              "segments too long for the on-chip kernels (" + std::to_string(slots) +
+                  " points per CTA); use more segments");
+}
+
+SegmentRun base_run(heat1d* h, int64_t K) {
+  SegmentRun a{};
+  a.N = h->N;
+  a.K = K;
+  a.S = h->S;
+  a.seg_off = h->d_off;
+  a.u_in = h->u[h->cur];
+  a.u_out = h->u[1 - h->cur];
+  a.r = h->r;
+  a.c1 = h->c1;
+  a.cN = h->cN;
+  a.status = h->status();
+  a.spin_limit_ns = h->opts.spin_limit_ns;
+  a.T = h->T;
+  a.edges = h->edges;
+  a.barrier = h->barrier();
+  a.q = h->q;
+  a.R = h->R;
+  a.prog = h->prog;
+  a.rings = h->rings;
+  a.stall_segment = h->opts.stall_segment;
+  return a;
+}
+
+int ensure_trace_staging(heat1d* h, size_t bytes) {
+  if (bytes <= h->d_trace_bytes) return HEAT1D_OK;
+  cudaFree(h->d_trace);
+  h->d_trace = nullptr;
+  h->d_trace_bytes = 0;
+  cudaError_t e = cudaMalloc(&h->d_trace, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(trace staging)");
+  h->d_trace_bytes = bytes;
+  return HEAT1D_OK;
+}
+
+int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device, const uint8_t* trace_in,
+                     int in_on_device) {
+  if (K < 0 || K >= INT_MAX) return fail(HEAT1D_ERR_INVAL, "K out of range");
+  if (K == 0) return HEAT1D_OK;
+  int E = 0, threads = 0;
+  int rc = pick_shape(h, h->Lmax + 2, 32, &E, &threads);
+  if (rc) return rc;
+  const size_t tbytes = static_cast<size_t>(K) * (h->S - 1) * 2;
+  SegmentRun a = base_run(h, K);
+  uint8_t* out_dev = nullptr;
+  if (trace_out && tbytes) {
+    if (out_on_device) {
+      out_dev = trace_out;
+    } else {
+      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
+      out_dev = h->d_trace;
+    }
+  }
+  const uint8_t* in_dev = nullptr;
+  if (trace_in) {
+    if (tbytes == 0) {
+      in_dev = nullptr;  // one segment: nothing to replay
+    } else if (in_on_device) {
+      in_dev = trace_in;
+    } else {
+      if (out_dev && out_dev == h->d_trace) return fail(HEAT1D_ERR_INVAL, "host trace in and out at once");
+      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
+      HEAT1D_CUDA(cudaMemcpyAsync(h->d_trace, trace_in, tbytes, cudaMemcpyHostToDevice, h->stream));
+      in_dev = h->d_trace;
+    }
+  }
+  a.trace_out = out_dev;
+  a.trace_in = in_dev;
+  HEAT1D_CUDA(cudaMemsetAsync(h->prog, 0xff, sizeof(int) * h->S * heat1d_impl::kProgStride, h->stream));
+  rc = heat1d_impl::launch_async_persistent(a, h->dtype, E, threads, h->stream);
+  if (rc == HEAT1D_ERR_NOT_RESIDENT)
+    return fail(rc, "asynchronous run: " + std::to_string(h->S) + " CTAs cannot all be resident");
+  if (rc) return cuda_fail(cudaGetLastError(), "launch_async_persistent");
+  h->cur = 1 - h->cur;
+  if (out_dev && !out_on_device)
+    HEAT1D_CUDA(cudaMemcpyAsync(trace_out, out_dev, tbytes, cudaMemcpyDeviceToHost, h->stream));
+  return HEAT1D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void heat1d_default_opts(heat1d_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->stall_segment = -1;
+}
+
+const char* heat1d_last_error(void) { return g_last_error.c_str(); }
+
+heat1d_t heat1d_create(int64_t N, double r, double c1, double cN, int dtype) {
+  if (N < 3) {
+    fail(HEAT1D_ERR_INVAL, "heat1d_create: N must be >= 3");
+    return nullptr;
+  }
+  if (!(r > 0.0 && r <= 0.5)) {
+    fail(HEAT1D_ERR_INVAL, "heat1d_create: r must be in (0, 0.5] (Section 2 stability range)");
+    return nullptr;
+  }
+  if (dtype != HEAT1D_F32 && dtype != HEAT1D_F64) {
+    fail(HEAT1D_ERR_INVAL, "heat1d_create: dtype must be HEAT1D_F32 or HEAT1D_F64");
+    return nullptr;
+  }
+  heat1d* h = new heat1d();
+  h->N = N;
+  h->r = r;
+  h->c1 = c1;
+  h->cN = cN;
+  h->dtype = dtype;
+  h->esize = dtype == HEAT1D_F64 ? 8 : 4;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->u[0], h->esize * N);
+  if (e == cudaSuccess) e = cudaMalloc(&h->u[1], h->esize * N);
+  if (e == cudaSuccess) e = cudaMalloc(&h->ctl, 256);
+  if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, 256);
+  if (e == cudaSuccess) e = cudaMemset(h->u[0], 0, h->esize * N);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "heat1d_create");
+    heat1d_destroy(h);
+    return nullptr;
+  }
+  heat1d_opts o;
+  heat1d_default_opts(&o);
+  if (configure(h, o) != HEAT1D_OK) {
+    heat1d_destroy(h);
+    return nullptr;
+  }
+  if (h->dtype == HEAT1D_F64)
+    set_ends_kernel<double><<<1, 32, 0, h->stream>>>(static_cast<double*>(h->u[0]), N, c1, cN);
+  else
+    set_ends_kernel<float><<<1, 32, 0, h->stream>>>(static_cast<float*>(h->u[0]), N, c1, cN);
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+    cuda_fail(e, "heat1d_create");
+    heat1d_destroy(h);
+    return nullptr;
+  }
+  return h;
+}
+
+void heat1d_destroy(heat1d_t h) {
+  if (!h) return;
+  free_scratch(h);
+  cudaFree(h->u[0]);
+  cudaFree(h->u[1]);
+  cudaFree(h->ctl);
+  cudaFree(h->d_trace);
+  delete h;
+}
+
+int heat1d_set_stream(heat1d_t h, void* stream) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  h->stream = static_cast<cudaStream_t>(stream);
+  return HEAT1D_OK;
+}
+
+int heat1d_set_opts(heat1d_t h, const heat1d_opts* o) {
+  if (!h || !o) return fail(HEAT1D_ERR_INVAL, "null argument");
+  HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
+  return configure(h, *o);
+}
+
+int heat1d_get_opts(heat1d_t h, heat1d_opts* o) {
+  if (!h || !o) return fail(HEAT1D_ERR_INVAL, "null argument");
+  *o = h->opts;
+  o->segments = h->S;
+  o->q = h->q;
+  o->halo_steps = h->T;
+  return HEAT1D_OK;
+}
+
+int64_t heat1d_num_segments(heat1d_t h, int64_t* offsets) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  if (offsets) std::memcpy(offsets, h->off.data(), sizeof(int64_t) * (h->S + 1));
+  return h->S;
+}
+
+int heat1d_set_u(heat1d_t h, const void* u, int on_device) {
+  if (!h || !u) return fail(HEAT1D_ERR_INVAL, "null argument");
+  HEAT1D_CUDA(cudaMemcpyAsync(h->u[h->cur], u, h->esize * h->N,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  if (h->dtype == HEAT1D_F64)
+    set_ends_kernel<double><<<1, 32, 0, h->stream>>>(static_cast<double*>(h->u[h->cur]), h->N, h->c1, h->cN);
+  else
+    set_ends_kernel<float><<<1, 32, 0, h->stream>>>(static_cast<float*>(h->u[h->cur]), h->N, h->c1, h->cN);
+  HEAT1D_CUDA(cudaGetLastError());
+  if (!on_device) HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
+  return HEAT1D_OK;
+}
+
+int heat1d_get_u(heat1d_t h, void* u, int on_device) {
+  if (!h || !u) return fail(HEAT1D_ERR_INVAL, "null argument");
+  HEAT1D_CUDA(cudaMemcpyAsync(u, h->u[h->cur], h->esize * h->N,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  if (!on_device) HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
+  return HEAT1D_OK;
+}
+
+int heat1d_run_sync(heat1d_t h, int64_t K) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  if (K < 0) return fail(HEAT1D_ERR_INVAL, "K must be >= 0");
+  if (K == 0) return HEAT1D_OK;
+  int E = 0, threads = 0;
+  int rc = pick_shape(h, h->Lmax + 2 * h->T, 0, &E, &threads);
+  if (rc) return rc;
+  SegmentRun a = base_run(h, K);
+  HEAT1D_CUDA(cudaMemsetAsync(h->barrier(), 0, sizeof(unsigned), h->stream));
+  rc = heat1d_impl::launch_sync_persistent(a, h->dtype, E, threads, h->stream);
+  if (rc == HEAT1D_ERR_NOT_RESIDENT)
+    return fail(rc, "synchronous run: " + std::to_string(h->S) + " CTAs cannot all be resident");
+  if (rc) return cuda_fail(cudaGetLastError(), "launch_sync_persistent");
+  h->cur = 1 - h->cur;
+  return HEAT1D_OK;
+}
+
+int heat1d_run_async(heat1d_t h, int64_t K, uint8_t* trace_out, int trace_on_device) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  return run_async_common(h, K, trace_out, trace_on_device, nullptr, 0);
+}
+
+int64_t heat1d_trace_bytes(heat1d_t h, int64_t K) {
+  if (!h || K < 0) return fail(HEAT1D_ERR_INVAL, "bad argument");
+  return K * (h->S - 1) * 2;
+}
+
+int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  if (!trace && h->S > 1 && K > 0) return fail(HEAT1D_ERR_INVAL, "heat1d_replay: trace is NULL");
+  static const uint8_t dummy = 0;
+  return run_async_common(h, K, nullptr, 0, trace ? trace : &dummy, trace ? trace_on_device : 0);
+}
+
+int heat1d_sync(heat1d_t h) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
+  int st = 0;
+  HEAT1D_CUDA(cudaMemcpy(&st, h->status(), sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    HEAT1D_CUDA(cudaMemset(h->status(), 0, sizeof(int)));
+    if (st == HEAT1D_ERR_TIMEOUT) return fail(st, "a device-side wait exceeded spin_limit_ns");
+    if (st == HEAT1D_ERR_TRACE) return fail(st, "a replay trace entry is >= q");
+    return fail(st, "device status " + std::to_string(st));
+  }
+  return HEAT1D_OK;
+}
+
+}  // extern "C"

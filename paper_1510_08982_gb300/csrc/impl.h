@@ -1,0 +1,58 @@
+// impl.h -- internal interface between the C ABI (heat1d_api.cu) and the
+// kernel translation units.  Not installed; not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace heat1d_impl {
+
+// Largest ring of the asynchronous run (versions kept per directed edge).
+constexpr int kMaxRing = 512;
+// Padding, in ints, between the per-segment version counters (one 128-byte
+// line each, so that CTAs never share a line they write).
+constexpr int kProgStride = 32;
+
+// Arguments of one persistent run over the segments of one rod.
+struct SegmentRun {
+  int64_t N;
+  int64_t K;
+  int S;
+  const int64_t* seg_off;  // device, S+1 offsets
+  const void* u_in;        // device, N values
+  void* u_out;             // device, N values (a different buffer)
+  double r, c1, cN;
+  int* status;             // device status word (0 = healthy)
+  int64_t spin_limit_ns;
+
+  // synchronous run
+  int T;                   // halo width = steps between exchanges
+  void* edges;             // [2][S][2T] values
+  unsigned* barrier;       // grid barrier counter, zero at launch
+
+  // asynchronous run / replay
+  int q;                   // delay window
+  int R;                   // ring length (power of two, >= 2q)
+  int* prog;               // [S * kProgStride] published versions, -1 at launch
+  void* rings;             // [S][2][R] values: [s][0] left edge, [s][1] right edge
+  uint8_t* trace_out;      // device or NULL
+  const uint8_t* trace_in; // device, replay only
+  int stall_segment;       // -1: off
+};
+
+// Largest CTA (threads) of the register-tile kernels for a dtype and E: a
+// tile of more than 64 bytes per thread needs more than 64 registers per
+// thread, so it is limited to 512 threads.
+constexpr int max_tile_threads(int elem_bytes, int E) { return elem_bytes * E > 64 ? 512 : 1024; }
+
+// Launch the persistent kernels (cooperative launch: all S CTAs resident).
+// E is the number of points per thread (2, 4, 8 or 16); `threads` the compute
+// threads per CTA (a multiple of 32).  Return a heat1d_status code.
+int launch_sync_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
+int launch_async_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
+
+// Largest number of CTAs of these kernels that can be resident at once.
+int max_resident_sync(int dtype, int E, int threads);
+int max_resident_async(int dtype, int E, int threads);
+
+}  // namespace heat1d_impl

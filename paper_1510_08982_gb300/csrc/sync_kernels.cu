@@ -1,0 +1,177 @@
+// sync_kernels.cu -- the synchronous run of Section 2, Eq. (eqn:sync), as one
+// persistent cooperative launch.
+//
+// The paper's synchronous code relaunches a kernel (and copies the state to
+// the host and back) every step; Section 4 names __syncthreads() as the better
+// way to impose the per-step synchronisation.  Here one CTA owns one segment
+// (the PE of Fig. 1) for the whole run.  The segment and T halo points on each
+// side live in registers.  The CTA advances T steps on its own (the valid region
+// shrinks by one point per side per step, the overlapped-halo trapezoid), then
+// publishes its first and last T points, meets every other CTA at a grid-wide
+// barrier, and reloads its halos from its neighbours.  Halo points are
+// recomputed redundantly with the same arithmetic, so the result is identical,
+// bit for bit, to a barrier after every step (T = 1).
+#include <algorithm>
+
+#include "common.cuh"
+#include "impl.h"
+
+namespace heat1d_impl {
+using namespace heat1d_dev;
+
+namespace {
+
+// Grid barrier on a counter that starts at zero: arrival number `epoch`
+// (0-based) completes when the counter reaches S*(epoch+1).  Called by one
+// thread per CTA between two __syncthreads().  Returns false on a timeout or a
+// failure raised elsewhere.
+__device__ bool grid_barrier(unsigned* counter, unsigned target, int* status, int64_t limit_ns) {
+  __threadfence();
+  atomicAdd(counter, 1u);
+  const uint64_t t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (true) {
+    const unsigned c = ld_acquire_gpu_u32(counter);
+    if (static_cast<int>(c - target) >= 0) break;
+    if ((++spins & 63u) == 0) {
+      if (status_failed(status)) return false;
+      if (static_cast<int64_t>(global_timer_ns() - t0) > limit_ns) {
+        raise_status(status, HEAT1D_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+  __threadfence();
+  return true;
+}
+
+template <typename real, int E>
+__global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_persistent_kernel(SegmentRun a) {
+  __shared__ TileShared<real> sh;
+  __shared__ int sh_ok;
+  const int s = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int64_t N = a.N;
+  const int64_t a0 = a.seg_off[s];
+  const int L = static_cast<int>(a.seg_off[s + 1] - a0);
+  const int T = a.T;
+  const int Lh = L + 2 * T;
+  const real r = static_cast<real>(a.r), c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
+  const real* __restrict__ uin = static_cast<const real*>(a.u_in);
+  real* __restrict__ uout = static_cast<real*>(a.u_out);
+  real* edges = static_cast<real*>(a.edges);
+
+  // Slot j of the tile holds global point a0 - T + j.
+  real v[E];
+  unsigned fixed = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int slot = tid * E + e;
+    const int64_t g = a0 - T + slot;
+    real x = static_cast<real>(0);
+    if (slot < Lh && g >= 0 && g < N) x = uin[g];
+    if (g == 0) x = c1;
+    if (g == N - 1) x = cN;
+    v[e] = x;
+    if (slot >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
+  }
+
+  int parity = 0;
+  unsigned epoch = 0;
+  for (int64_t k0 = 0; k0 < a.K; k0 += T) {
+    const int tb = static_cast<int>(std::min<int64_t>(T, a.K - k0));
+    tile_steps<real, E>(v, fixed, r, sh, parity, warp, lane, nwarps, blockDim.x, tb);
+    if (k0 + tb >= a.K) break;
+
+    // Publish the first T and the last T points of the segment.
+    real* mine = edges + (static_cast<size_t>(epoch & 1u) * a.S + s) * 2 * T;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int slot = tid * E + e;
+      if (slot >= T && slot < 2 * T) st_cg(mine + (slot - T), v[e]);
+      if (slot >= L && slot < L + T) st_cg(mine + T + (slot - L), v[e]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      sh_ok = grid_barrier(a.barrier, static_cast<unsigned>(a.S) * (epoch + 1u), a.status, a.spin_limit_ns);
+    }
+    __syncthreads();
+    if (!sh_ok) return;  // CTA-uniform: every thread reads the same flag
+
+    // Reload the halos: the left neighbour's last T points, the right
+    // neighbour's first T points.
+    if (s > 0) {
+      const real* left = edges + (static_cast<size_t>(epoch & 1u) * a.S + (s - 1)) * 2 * T;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int slot = tid * E + e;
+        if (slot < T) v[e] = ld_cg(left + T + slot);
+      }
+    }
+    if (s + 1 < a.S) {
+      const real* right = edges + (static_cast<size_t>(epoch & 1u) * a.S + (s + 1)) * 2 * T;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int slot = tid * E + e;
+        if (slot >= L + T && slot < L + 2 * T) v[e] = ld_cg(right + (slot - L - T));
+      }
+    }
+    ++epoch;
+  }
+
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int slot = tid * E + e;
+    if (slot >= T && slot < T + L) uout[a0 + (slot - T)] = v[e];
+  }
+}
+
+template <typename real, int E>
+int launch_sync_t(const SegmentRun& a, int threads, cudaStream_t st) {
+  SegmentRun args = a;
+  void* params[] = {&args};
+  cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(sync_persistent_kernel<real, E>), dim3(a.S),
+                                              dim3(threads), params, 0, st);
+  if (e == cudaErrorCooperativeLaunchTooLarge) {
+    cudaGetLastError();
+    return HEAT1D_ERR_NOT_RESIDENT;
+  }
+  return e == cudaSuccess ? HEAT1D_OK : HEAT1D_ERR_CUDA;
+}
+
+template <typename real, int E>
+int resident_t(int threads) {
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sync_persistent_kernel<real, E>, threads, 0) !=
+      cudaSuccess)
+    return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * nsm;
+}
+
+}  // namespace
+
+int launch_sync_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st) {
+  const bool f64 = dtype == HEAT1D_F64;
+  switch (E) {
+    case 2: return f64 ? launch_sync_t<double, 2>(a, threads, st) : launch_sync_t<float, 2>(a, threads, st);
+    case 4: return f64 ? launch_sync_t<double, 4>(a, threads, st) : launch_sync_t<float, 4>(a, threads, st);
+    case 8: return f64 ? launch_sync_t<double, 8>(a, threads, st) : launch_sync_t<float, 8>(a, threads, st);
+    case 16: return f64 ? launch_sync_t<double, 16>(a, threads, st) : launch_sync_t<float, 16>(a, threads, st);
+    default: return HEAT1D_ERR_INVAL;
+  }
+}
+
+int max_resident_sync(int dtype, int E, int threads) {
+  const bool f64 = dtype == HEAT1D_F64;
+  switch (E) {
+    case 2: return f64 ? resident_t<double, 2>(threads) : resident_t<float, 2>(threads);
+    case 4: return f64 ? resident_t<double, 4>(threads) : resident_t<float, 4>(threads);
+    case 8: return f64 ? resident_t<double, 8>(threads) : resident_t<float, 8>(threads);
+    case 16: return f64 ? resident_t<double, 16>(threads) : resident_t<float, 16>(threads);
+    default: return 0;
+  }
+}
+
+}  // namespace heat1d_impl

@@ -1,0 +1,255 @@
+"""Python binding of libheat1d (C ABI in include/heat1d.h).
+
+Argument marshalling only: every step of a run executes in the library's CUDA
+kernels.  PyTorch provides device memory and the CUDA stream (each call is
+enqueued on ``torch.cuda.current_stream()``).  There is no CPU fallback: if
+the library is missing, ``load()`` raises.
+
+Names follow the C ABI: ``Heat1d.run_sync``, ``run_async``, ``replay``,
+``trace_bytes``, ``sync``, ``set_u``, ``get_u``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libheat1d.so")
+
+F32, F64 = 0, 1
+OK, ERR_INVAL, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_RESIDENT, ERR_TRACE, ERR_OOM = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {OK: "HEAT1D_OK", ERR_INVAL: "HEAT1D_ERR_INVAL", ERR_CUDA: "HEAT1D_ERR_CUDA",
+                ERR_TIMEOUT: "HEAT1D_ERR_TIMEOUT", ERR_NOT_RESIDENT: "HEAT1D_ERR_NOT_RESIDENT",
+                ERR_TRACE: "HEAT1D_ERR_TRACE", ERR_OOM: "HEAT1D_ERR_OOM"}
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_last_error", "heat1d_set_stream",
+           "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
+           "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync"]
+
+
+class Heat1dError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("segments", ctypes.c_int64), ("q", ctypes.c_int32), ("halo_steps", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("elems_per_thread", ctypes.c_int32),
+                ("spin_limit_ns", ctypes.c_int64), ("stall_segment", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+_lib = None
+
+
+def load():
+    """Loads libheat1d.so (built by ``python -m paper_1510_08982_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libheat1d.so is not built (%s); run `python -m paper_1510_08982_gb300.build` "
+                           "or __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "heat1d_default_opts": (None, [ctypes.POINTER(Opts)]),
+        "heat1d_create": (vp, [i64, dbl, dbl, dbl, i32]),
+        "heat1d_destroy": (None, [vp]),
+        "heat1d_last_error": (ctypes.c_char_p, []),
+        "heat1d_set_stream": (i32, [vp, vp]),
+        "heat1d_set_opts": (i32, [vp, ctypes.POINTER(Opts)]),
+        "heat1d_get_opts": (i32, [vp, ctypes.POINTER(Opts)]),
+        "heat1d_num_segments": (i64, [vp, vp]),
+        "heat1d_set_u": (i32, [vp, vp, i32]),
+        "heat1d_get_u": (i32, [vp, vp, i32]),
+        "heat1d_run_sync": (i32, [vp, i64]),
+        "heat1d_run_async": (i32, [vp, i64, vp, i32]),
+        "heat1d_trace_bytes": (i64, [vp, i64]),
+        "heat1d_replay": (i32, [vp, i64, vp, i32]),
+        "heat1d_sync": (i32, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().heat1d_last_error().decode()
+
+
+def _check(rc):
+    if rc != OK:
+        raise Heat1dError(rc, last_error())
+    return rc
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(dtype):
+    torch = _torch()
+    if dtype in (torch.float64, np.float64, "f64", "float64"):
+        return F64
+    if dtype in (torch.float32, np.float32, "f32", "float32"):
+        return F32
+    raise ValueError("dtype must be float32 or float64")
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    load().heat1d_default_opts(ctypes.byref(o))
+    return o
+
+
+class Heat1d:
+    """One rod of N points: state, options and scratch on the current device.
+
+    ``opts`` keywords: segments, q, halo_steps, block_threads,
+    elems_per_thread, spin_limit_ns, stall_segment (see heat1d_opts)."""
+
+    def __init__(self, N, r, c1, cN, dtype="float64", **opts):
+        torch = _torch()
+        self.lib = load()
+        self.N = int(N)
+        self.code = _dtype_code(dtype)
+        self.torch_dtype = torch.float64 if self.code == F64 else torch.float32
+        self.np_dtype = np.float64 if self.code == F64 else np.float32
+        torch.cuda.init()
+        h = self.lib.heat1d_create(self.N, float(r), float(c1), float(cN), self.code)
+        if not h:
+            raise Heat1dError(ERR_INVAL, last_error())
+        self.h = ctypes.c_void_p(h)
+        if opts:
+            self.set_opts(**opts)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.heat1d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- config
+    def _stream(self):
+        torch = _torch()
+        _check(self.lib.heat1d_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def set_opts(self, **kw):
+        o = default_opts()
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError("unknown option %r" % k)
+            setattr(o, k, int(v))
+        _check(self.lib.heat1d_set_opts(self.h, ctypes.byref(o)))
+
+    def get_opts(self) -> dict:
+        o = Opts()
+        _check(self.lib.heat1d_get_opts(self.h, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in Opts._fields_ if k != "reserved"}
+
+    @property
+    def segments(self) -> np.ndarray:
+        S = self.lib.heat1d_num_segments(self.h, None)
+        off = np.zeros(S + 1, dtype=np.int64)
+        self.lib.heat1d_num_segments(self.h, off.ctypes.data_as(ctypes.c_void_p))
+        return off
+
+    @property
+    def S(self) -> int:
+        return int(self.lib.heat1d_num_segments(self.h, None))
+
+    # ---------------------------------------------------------------- state
+    def set_u(self, u):
+        """u: a CUDA tensor (device copy) or a host array/tensor of N values."""
+        torch = _torch()
+        self._stream()
+        if isinstance(u, torch.Tensor) and u.is_cuda:
+            t = u.to(self.torch_dtype).contiguous()
+            if t.numel() != self.N:
+                raise ValueError("u has %d values, expected %d" % (t.numel(), self.N))
+            _check(self.lib.heat1d_set_u(self.h, ctypes.c_void_p(t.data_ptr()), 1))
+            self._keep = t  # alive until the copy is done
+        else:
+            a = np.ascontiguousarray(u.cpu().numpy() if isinstance(u, torch.Tensor) else u, dtype=self.np_dtype)
+            if a.size != self.N:
+                raise ValueError("u has %d values, expected %d" % (a.size, self.N))
+            _check(self.lib.heat1d_set_u(self.h, a.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def get_u(self, out=None, device=True):
+        """The current state as a CUDA tensor (device=True) or numpy array."""
+        torch = _torch()
+        self._stream()
+        if device:
+            if out is None:
+                out = torch.empty(self.N, dtype=self.torch_dtype, device="cuda")
+            _check(self.lib.heat1d_get_u(self.h, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        a = np.empty(self.N, dtype=self.np_dtype) if out is None else out
+        _check(self.lib.heat1d_get_u(self.h, a.ctypes.data_as(ctypes.c_void_p), 0))
+        return a
+
+    # ---------------------------------------------------------------- runs
+    def trace_bytes(self, K) -> int:
+        return int(self.lib.heat1d_trace_bytes(self.h, int(K)))
+
+    def new_trace(self, K, device=True):
+        torch = _torch()
+        shape = (int(K), max(self.S - 1, 0), 2)
+        if device:
+            return torch.empty(shape, dtype=torch.uint8, device="cuda")
+        return np.empty(shape, dtype=np.uint8)
+
+    def run_sync(self, K):
+        self._stream()
+        _check(self.lib.heat1d_run_sync(self.h, int(K)))
+
+    def run_async(self, K, trace_out=None):
+        """trace_out: None, a CUDA uint8 tensor or a host uint8 array of
+        trace_bytes(K) bytes (host arrays are complete after sync())."""
+        self._stream()
+        ptr, on_dev = self._trace_ptr(trace_out, K)
+        _check(self.lib.heat1d_run_async(self.h, int(K), ptr, on_dev))
+
+    def replay(self, K, trace):
+        self._stream()
+        ptr, on_dev = self._trace_ptr(trace, K)
+        _check(self.lib.heat1d_replay(self.h, int(K), ptr, on_dev))
+
+    def sync(self):
+        """Waits for the stream; raises on a device-side failure."""
+        _check(self.lib.heat1d_sync(self.h))
+
+    def _trace_ptr(self, t, K):
+        torch = _torch()
+        if t is None:
+            return None, 0
+        n = self.trace_bytes(K)
+        if isinstance(t, torch.Tensor):
+            if t.dtype != torch.uint8 or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("trace must be a contiguous uint8 tensor of %d bytes" % n)
+            if t.is_cuda:
+                return ctypes.c_void_p(t.data_ptr()), 1
+            t = t.numpy()
+        if not isinstance(t, np.ndarray) or t.dtype != np.uint8 or not t.flags.c_contiguous or t.size != n:
+            raise ValueError("trace must be a contiguous uint8 array of %d bytes" % n)
+        return t.ctypes.data_as(ctypes.c_void_p), 0

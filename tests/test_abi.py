@@ -1,0 +1,61 @@
+"""The C ABI library builds, loads and exports every symbol of include/heat1d.h
+(CPU only: no compute call is made without a GPU)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1510_08982_gb300 import build as build_mod
+from paper_1510_08982_gb300 import heat1d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "heat1d.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(heat1d_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_mod.build()
+    return heat1d.load()
+
+
+def test_header_declares_the_binding_names():
+    assert header_functions() == sorted(heat1d.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_opts_struct_layout_matches_header():
+    # int64 segments, 4 x int32, int64 spin_limit, int32 stall + 7 reserved
+    assert ctypes.sizeof(heat1d.Opts) == 8 + 4 * 4 + 8 + 4 + 7 * 4
+    assert heat1d.Opts.spin_limit_ns.offset == 24
+
+
+def test_default_opts(lib):
+    o = heat1d.default_opts()
+    assert o.segments == 0 and o.q == 0 and o.stall_segment == -1
+
+
+def test_create_rejects_bad_arguments_without_a_gpu(lib):
+    # argument checks come before any CUDA call
+    assert not lib.heat1d_create(2, 0.25, 0.0, 1.0, heat1d.F64)
+    assert "N must be" in heat1d.last_error()
+    assert not lib.heat1d_create(100, 0.75, 0.0, 1.0, heat1d.F64)
+    assert "r must be" in heat1d.last_error()
+    assert not lib.heat1d_create(100, 0.25, 0.0, 1.0, 7)
+    assert "dtype" in heat1d.last_error()
+
+
+def test_build_is_in_tree_for_sm103a():
+    assert build_mod.LIB.startswith(os.path.join(ROOT, "paper_1510_08982_gb300"))
+    assert "arch=compute_103a,code=sm_103a" in build_mod.ARCH
