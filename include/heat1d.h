@@ -142,6 +142,38 @@ int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_devi
  * HEAT1D_ERR_TIMEOUT or HEAT1D_ERR_TRACE (HEAT1D_ERR_CUDA on a CUDA error). */
 int heat1d_sync(heat1d_t h);
 
+/* Synchronous run that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- for example
+ * code running inside a host callback or an allocator hook, a plug-in that may
+ * not grow the process's device memory, or a loop that forbids allocation
+ * after start-up.  The handle API allocates state and scratch at
+ * heat1d_create(), which such callers cannot do.
+ *
+ * Computes the same K steps as heat1d_run_sync() (same kernel, same result
+ * bit for bit) from u_in to u_out: two distinct device buffers of N values of
+ * `dtype`, owned by the caller.  u_out[0] and u_out[N-1] receive c1 and cN.
+ * segments: S, in [1, 256], or 0 for one per SM (at most 256); each segment
+ * must fit one CTA (about 16K points in F32 and 8K in F64).  The halo width is
+ * min(32, N/S).  The run is enqueued on `stream` (a cudaStream_t, NULL for the
+ * legacy default stream).  If status_out is not NULL it must be a device int;
+ * it receives the run's device status (HEAT1D_OK or HEAT1D_ERR_TIMEOUT) when
+ * the run completes on the stream.
+ *
+ * The kernel's scratch (halo buffers, barrier counter, status word, segment
+ * offsets; about 260 KB) lives in one fixed __device__ array inside the
+ * library: every GPU that loads the library holds it until the process exits.
+ * Calls reuse it: each call clears what must start at zero, so results never
+ * depend on an earlier call, but two calls that overlap on the GPU (different
+ * streams, or different host threads, without ordering between them) race on
+ * that array and give wrong results.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture begins.  No call allocates device or
+ * pinned memory.  Returns HEAT1D_ERR_INVAL (message in heat1d_last_error())
+ * for sizes beyond these limits, HEAT1D_ERR_NOT_RESIDENT if the segments cannot
+ * all be resident, HEAT1D_ERR_CUDA on a launch failure. */
+int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N, double r, double c1, double cN, int dtype,
+                            int64_t K, int64_t segments, void* stream, int* status_out);
+
 #ifdef __cplusplus
 }
 #endif

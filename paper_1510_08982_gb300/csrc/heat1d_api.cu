@@ -48,6 +48,8 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
+void heat1d_impl::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct heat1d {
   int64_t N = 0;
   double r = 0, c1 = 0, cN = 0;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace heat1d_impl {
@@ -50,6 +51,9 @@ constexpr int max_tile_threads(int elem_bytes, int E) { return elem_bytes * E > 
 // threads per CTA (a multiple of 32).  Return a heat1d_status code.
 int launch_sync_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
 int launch_async_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
+
+// Sets the message returned by heat1d_last_error() on this host thread.
+void set_last_error(const std::string& msg);
 
 // Largest number of CTAs of these kernels that can be resident at once.
 int max_resident_sync(int dtype, int E, int threads);

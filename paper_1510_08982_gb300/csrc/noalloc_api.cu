@@ -1,0 +1,167 @@
+// noalloc_api.cu -- heat1d_run_sync_noalloc: the synchronous run for callers
+// that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs where allocation is not
+// allowed or not safe, such as a host callback, a custom allocator's own
+// hooks, a plug-in that must not grow the process's device footprint, or a
+// real-time loop that forbids allocation after start-up.  The handle API
+// allocates its state and scratch when a handle is created, so it is not open
+// to them.  This entry point takes the caller's input and output buffers and
+// keeps the synchronous kernel's scratch (the halo exchange buffers, the grid
+// barrier counter, the status word and the segment offsets) in one file-scope
+// __device__ array of fixed size.  Every GPU that loads the library holds that
+// array until the process exits.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "heat1d.h"
+#include "impl.h"
+
+namespace {
+
+// Limits of the shared scratch array.
+constexpr int kNoallocMaxSegments = 256;
+constexpr int kNoallocMaxHalo = 32;
+// Layout (bytes): [0, 256) control words (barrier counter at 0, status at 128);
+// [256, 256 + 8*(S+1)) segment offsets; then the halo buffers [2][S][2T] values.
+constexpr size_t kCtlBytes = 256;
+constexpr size_t kOffBytes = 8 * (kNoallocMaxSegments + 1);
+constexpr size_t kEdgeOffset = (kCtlBytes + kOffBytes + 255) / 256 * 256;
+constexpr size_t kEdgeBytes = size_t(2) * kNoallocMaxSegments * 2 * kNoallocMaxHalo * sizeof(double);
+constexpr size_t kScratchBytes = kEdgeOffset + kEdgeBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// Per-device address of g_noalloc_scratch, looked up once per device.
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Clears the control words and writes the segment offsets (the first N mod S
+// segments hold one point more), so that nothing depends on an earlier call.
+__global__ void noalloc_prepare_kernel(unsigned char* scratch, int64_t N, int S) {
+  unsigned* barrier = reinterpret_cast<unsigned*>(scratch);
+  int* status = reinterpret_cast<int*>(scratch + 128);
+  int64_t* off = reinterpret_cast<int64_t*>(scratch + kCtlBytes);
+  const int64_t base = N / S, extra = N % S;
+  for (int s = threadIdx.x; s <= S; s += blockDim.x) off[s] = s * base + (s < extra ? s : extra);
+  if (threadIdx.x == 0) {
+    *barrier = 0u;
+    *status = 0;
+  }
+}
+
+// Copies the run's device status to the caller's word.
+__global__ void noalloc_status_kernel(const unsigned char* scratch, int* status_out) {
+  if (threadIdx.x == 0) *status_out = *reinterpret_cast<const int*>(scratch + 128);
+}
+
+int fail(int code, const std::string& msg) {
+  heat1d_impl::set_last_error(msg);
+  return code;
+}
+
+// Looks up the scratch array's device address for the current device.
+int scratch_address(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(HEAT1D_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(HEAT1D_ERR_INVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HEAT1D_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  return HEAT1D_OK;
+}
+
+}  // namespace
+
+extern "C" int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N, double r, double c1, double cN,
+                                       int dtype, int64_t K, int64_t segments, void* stream, int* status_out) {
+  if (!u_in || !u_out) return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: null buffer");
+  if (u_in == u_out) return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: u_in and u_out must differ");
+  if (N < 3) return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: N must be >= 3");
+  if (!(r > 0.0 && r <= 0.5)) return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: r must be in (0, 0.5]");
+  if (dtype != HEAT1D_F32 && dtype != HEAT1D_F64)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: dtype must be HEAT1D_F32 or HEAT1D_F64");
+  if (K < 0) return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: K must be >= 0");
+  if (segments < 0 || segments > kNoallocMaxSegments)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: segments must be in [0, 256] (the size of the "
+                                  "library's fixed scratch array)");
+
+  unsigned char* scratch = nullptr;
+  int rc = scratch_address(&scratch);
+  if (rc) return rc;
+
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int64_t S = segments ? segments : std::min<int64_t>(nsm, kNoallocMaxSegments);
+  S = std::min<int64_t>(S, N);
+  const int64_t Lmin = N / S, Lmax = N / S + (N % S ? 1 : 0);
+  const int T = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kNoallocMaxHalo, Lmin)));
+  const size_t esize = dtype == HEAT1D_F64 ? 8 : 4;
+
+  // Launch shape: fewest points per thread that fit one CTA.
+  const int64_t slots = Lmax + 2 * T;
+  int E = 0, threads = 0;
+  const int Es[4] = {2, 4, 8, 16};
+  for (int i = 0; i < 4 && !E; ++i) {
+    const int64_t per_thread = (slots + Es[i] - 1) / Es[i];
+    const int64_t t = std::max<int64_t>((per_thread + 31) / 32 * 32, 32);
+    if (t <= heat1d_impl::max_tile_threads(static_cast<int>(esize), Es[i])) {
+      E = Es[i];
+      threads = static_cast<int>(t);
+    }
+  }
+  if (!E)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: " + std::to_string(Lmax) +
+                                      " points per segment exceed one CTA; pass more segments (at most 256)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  noalloc_prepare_kernel<<<1, 256, 0, st>>>(scratch, N, static_cast<int>(S));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(HEAT1D_ERR_CUDA, std::string("prepare: ") + cudaGetErrorString(e));
+
+  {
+    // K = 0 still launches: the kernel then only copies u(0), ends forced.
+    heat1d_impl::SegmentRun a{};
+    a.N = N;
+    a.K = K;
+    a.S = static_cast<int>(S);
+    a.seg_off = reinterpret_cast<const int64_t*>(scratch + kCtlBytes);
+    a.u_in = u_in;
+    a.u_out = u_out;
+    a.r = r;
+    a.c1 = c1;
+    a.cN = cN;
+    a.status = reinterpret_cast<int*>(scratch + 128);
+    a.spin_limit_ns = 2000000000LL;
+    a.T = T;
+    a.edges = scratch + kEdgeOffset;
+    a.barrier = reinterpret_cast<unsigned*>(scratch);
+    a.stall_segment = -1;
+    rc = heat1d_impl::launch_sync_persistent(a, dtype, E, threads, st);
+    if (rc == HEAT1D_ERR_NOT_RESIDENT)
+      return fail(rc, "heat1d_run_sync_noalloc: " + std::to_string(S) + " CTAs cannot all be resident");
+    if (rc) {
+      e = cudaGetLastError();
+      return fail(HEAT1D_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+    }
+  }
+  if (status_out) {
+    noalloc_status_kernel<<<1, 32, 0, st>>>(scratch, status_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HEAT1D_ERR_CUDA, std::string("status: ") + cudaGetErrorString(e));
+  }
+  return HEAT1D_OK;
+}

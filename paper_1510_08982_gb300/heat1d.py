@@ -27,7 +27,8 @@ STATUS_NAMES = {OK: "HEAT1D_OK", ERR_INVAL: "HEAT1D_ERR_INVAL", ERR_CUDA: "HEAT1
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_last_error", "heat1d_set_stream",
            "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
-           "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync"]
+           "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync",
+           "heat1d_run_sync_noalloc"]
 
 
 class Heat1dError(RuntimeError):
@@ -72,6 +73,7 @@ def load():
         "heat1d_trace_bytes": (i64, [vp, i64]),
         "heat1d_replay": (i32, [vp, i64, vp, i32]),
         "heat1d_sync": (i32, [vp]),
+        "heat1d_run_sync_noalloc": (i32, [vp, vp, i64, dbl, dbl, dbl, i32, i64, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -253,3 +255,20 @@ class Heat1d:
         if not isinstance(t, np.ndarray) or t.dtype != np.uint8 or not t.flags.c_contiguous or t.size != n:
             raise ValueError("trace must be a contiguous uint8 array of %d bytes" % n)
         return t.ctypes.data_as(ctypes.c_void_p), 0
+
+
+def run_sync_noalloc(u_in, u_out, r, c1, cN, K, segments=0, status_out=None):
+    """heat1d_run_sync_noalloc on CUDA tensors u_in -> u_out (same dtype, N
+    values each) on the current stream; allocates nothing.  status_out: an
+    optional CUDA int32 tensor that receives the device status."""
+    torch = _torch()
+    lib = load()
+    if not (u_in.is_cuda and u_out.is_cuda) or u_in.dtype != u_out.dtype or u_in.numel() != u_out.numel():
+        raise ValueError("u_in and u_out must be CUDA tensors of the same dtype and size")
+    if not (u_in.is_contiguous() and u_out.is_contiguous()):
+        raise ValueError("u_in and u_out must be contiguous")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    sp = None if status_out is None else ctypes.c_void_p(status_out.data_ptr())
+    _check(lib.heat1d_run_sync_noalloc(ctypes.c_void_p(u_in.data_ptr()), ctypes.c_void_p(u_out.data_ptr()),
+                                       u_in.numel(), float(r), float(c1), float(cN), _dtype_code(u_in.dtype),
+                                       int(K), int(segments), st, sp))
