@@ -31,7 +31,7 @@ namespace {
 
 template <typename real>
 struct AsyncShared {
-  TileShared<real> tile;
+  LockstepShared<real> tile;
   real lring[kMaxRing];  // left neighbour's right-edge values, version v at v & (R-1)
   real rring[kMaxRing];  // right neighbour's left-edge values
   real own_l[kMaxRing];  // this segment's first point per version, for the comm warp
@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
     sh.own_r_ver = -1;
     sh.compute_done = 0;
   }
+  if (tid == 0) sh.tile.abort = 0;
   __syncthreads();
 
   if (warp == nwc) {
@@ -168,7 +169,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
   const int L = static_cast<int>(a.seg_off[s + 1] - a0);
   const int K = static_cast<int>(a.K);
   const int S = a.S;
-  const real r = static_cast<real>(a.r), c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
+  const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
+  const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};  // one = 1 at run time
   const real* __restrict__ uin = static_cast<const real*>(a.u_in);
   real* __restrict__ uout = static_cast<real*>(a.u_out);
   const bool has_left = s > 0, has_right = s + 1 < S;
@@ -187,7 +189,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
     v[e] = x;
     if (slot == 0 || slot >= L + 1 || g <= 0 || g >= N - 1) fixed |= 1u << e;
   }
-  const bool warp_fixed = __any_sync(kFullMask, fixed != 0u);
+  const int mode = tile_mode<E>(fixed);
+  const int nwarps_c = nwc;
   const int t_first = 1 / E, e_first = 1 % E;  // slot 1: first own point
   const int t_last = L / E, e_last = L % E;     // slot L: last own point
   const int t_rh = (L + 1) / E, e_rh = (L + 1) % E;  // slot L+1: right halo
@@ -217,10 +220,13 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
     if (tid == t_rh && has_right) dr_next = __ldg(trace_in + tr);
   }
 
-  int parity = 0;
   bool aborted = false;
   for (int k = 0; k < K; ++k) {
-    bool fail = false;
+    // Leave together when a wait anywhere in the CTA gave up.
+    if (__shfl_sync(kFullMask, lane == 0 ? ld_volatile_shared(&sh.tile.abort) : 0, 0)) {
+      aborted = true;
+      break;
+    }
     if (tid == 0 && has_left) {
       const int d = dl_next;
       if (trace_in && k + 1 < K) dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
                            val))
         v[0] = val;
       else
-        fail = true;
+        *reinterpret_cast<volatile int*>(&sh.tile.abort) = 1;
     }
     if (tid == t_rh && has_right) {
       const int d = dr_next;
@@ -241,17 +247,10 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
         for (int e = 0; e < E; ++e)
           if (e == e_rh) v[e] = val;
       } else {
-        fail = true;
+        *reinterpret_cast<volatile int*>(&sh.tile.abort) = 1;
       }
     }
-    const bool any_fail = warp_fixed
-                              ? tile_step<real, E, true>(v, fixed, r, sh.tile, parity, warp, lane, nwc, nthreads_c, fail)
-                              : tile_step<real, E, false>(v, fixed, r, sh.tile, parity, warp, lane, nwc, nthreads_c, fail);
-    parity ^= 1;
-    if (any_fail) {
-      aborted = true;
-      break;
-    }
+    lockstep_step_any<real, E>(mode, v, fixed, coef, sh.tile, static_cast<unsigned>(k), warp, lane, nwarps_c);
     const int ver = k + 1, j = ver & (a.R - 1);
     if (tid == t_first) {
 #pragma unroll

@@ -51,12 +51,14 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
   __shared__ int sh_ok;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  tile_shared_init(sh, tid);
   const int64_t N = a.N;
   const int64_t a0 = a.seg_off[s];
   const int L = static_cast<int>(a.seg_off[s + 1] - a0);
   const int T = a.T;
   const int Lh = L + 2 * T;
-  const real r = static_cast<real>(a.r), c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
+  const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
+  const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};  // one = 1 at run time
   const real* __restrict__ uin = static_cast<const real*>(a.u_in);
   real* __restrict__ uout = static_cast<real*>(a.u_out);
   real* edges = static_cast<real*>(a.edges);
@@ -76,11 +78,15 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
     if (slot >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
   }
 
-  int parity = 0;
+  const int mode = tile_mode<E>(fixed);
+  __syncthreads();
+
   unsigned epoch = 0;
   for (int64_t k0 = 0; k0 < a.K; k0 += T) {
     const int tb = static_cast<int>(std::min<int64_t>(T, a.K - k0));
-    tile_steps<real, E>(v, fixed, r, sh, parity, warp, lane, nwarps, blockDim.x, tb);
+    if (!tile_steps<real, E>(mode, v, fixed, coef, sh, static_cast<unsigned>(k0), warp, lane, nwarps, tb,
+                             a.spin_limit_ns))
+      raise_status(a.status, HEAT1D_ERR_TIMEOUT);
     if (k0 + tb >= a.K) break;
 
     // Publish the first T and the last T points of the segment.
@@ -93,7 +99,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
     }
     __syncthreads();
     if (tid == 0) {
-      sh_ok = grid_barrier(a.barrier, static_cast<unsigned>(a.S) * (epoch + 1u), a.status, a.spin_limit_ns);
+      sh_ok = !sh.abort &&
+              grid_barrier(a.barrier, static_cast<unsigned>(a.S) * (epoch + 1u), a.status, a.spin_limit_ns);
     }
     __syncthreads();
     if (!sh_ok) return;  // CTA-uniform: every thread reads the same flag
