@@ -72,7 +72,11 @@ typedef struct heat1d_opts {
   int32_t stall_segment; /* fault injection for tests: when >= 0, that segment of an asynchronous
                             run never publishes, so its neighbours' waits run out and the run
                             ends with HEAT1D_ERR_TIMEOUT.  Default -1 (off). */
-  int32_t reserved[7];
+  int32_t sync_mode;     /* synchronous run: 0 automatic, 1 on-chip (one CTA per segment, the
+                            segment in registers), 2 streamed (temporal blocking through HBM:
+                            tiles of block_threads * elems_per_thread points, halo_steps steps
+                            per pass).  Automatic picks on-chip when every segment fits one CTA. */
+  int32_t reserved[6];
 } heat1d_opts;
 
 /* Fills *o with the defaults (every field 0 except stall_segment = -1). */
@@ -112,10 +116,14 @@ int heat1d_set_u(heat1d_t h, const void* u, int on_device);
 int heat1d_get_u(heat1d_t h, void* u, int on_device);
 
 /* Synchronous run, Section 2 Eq. (eqn:sync): advances the state by K steps.
- * One persistent cooperative launch; one CTA per segment holds its segment and
- * T-wide halos in registers, exchanges the halos through global memory and
- * meets the other CTAs at a grid-wide barrier every T steps.  The result is
- * identical, bit for bit, to K single steps with a barrier after each. */
+ * One persistent cooperative launch.  On-chip mode: one CTA per segment holds
+ * its segment and T-wide halos in registers, exchanges the halos through
+ * global memory and meets the other CTAs at a grid-wide barrier every T steps.
+ * Streamed mode (rods too long for on-chip): tiles with T-wide halos are read
+ * from HBM, advanced T steps in registers and written back, one pass per T
+ * steps, with per-tile pass counters instead of a grid barrier.  Either way
+ * the result is identical, bit for bit, to K single steps with a barrier
+ * after each. */
 int heat1d_run_sync(heat1d_t h, int64_t K);
 
 /* Asynchronous run, Section 3 Eq. (eqn:async): advances the state by K steps

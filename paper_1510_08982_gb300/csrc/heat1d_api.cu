@@ -61,6 +61,9 @@ struct heat1d {
 
   // resolved configuration
   int S = 1, q = 3, R = 8, T = 1;
+  // streamed synchronous run: steps per pass, halo, tile shape
+  int Ts = 8, Th = 8, sE = 8, sthreads = 256, W = 0;
+  int64_t ntiles = 0;
   std::vector<int64_t> off;
   int64_t Lmin = 0, Lmax = 0;
 
@@ -71,6 +74,7 @@ struct heat1d {
   void* edges = nullptr;
   void* rings = nullptr;
   int* prog = nullptr;
+  int* done = nullptr;  // streamed run: passes completed per tile
   void* ctl = nullptr;  // [0]: grid barrier counter, [32]: status word (separate lines)
   uint8_t* d_trace = nullptr;
   size_t d_trace_bytes = 0;
@@ -86,10 +90,12 @@ void free_scratch(heat1d* h) {
   cudaFree(h->edges);
   cudaFree(h->rings);
   cudaFree(h->prog);
+  cudaFree(h->done);
   h->d_off = nullptr;
   h->edges = nullptr;
   h->rings = nullptr;
   h->prog = nullptr;
+  h->done = nullptr;
 }
 
 // Resolves the options against N and (re)allocates the scratch buffers.
@@ -120,14 +126,39 @@ int configure(heat1d* h, const heat1d_opts& o) {
   int R = 1;
   while (R < 2 * q) R <<= 1;
   if (R > heat1d_impl::kMaxRing) return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: q too large");
+  // On-chip synchronous runs take halos from the neighbouring segment only,
+  // so their T is at most the shortest segment (clamped unless on-chip mode
+  // was asked for explicitly).
   int T = o.halo_steps ? o.halo_steps : 32;
   if (T > Lmin) {
-    if (o.halo_steps) return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: halo_steps exceeds the shortest segment");
+    if (o.halo_steps && o.sync_mode == 1)
+      return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: halo_steps exceeds the shortest segment");
     T = static_cast<int>(Lmin);
   }
   if (T < 1) T = 1;
+  if (o.sync_mode < 0 || o.sync_mode > 2) return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: sync_mode must be 0, 1 or 2");
+
+  // Streamed shape: 16-byte vectors, so E and the halo are multiples of
+  // 16 / sizeof(real) points and every tile starts on a 16-byte boundary.
+  const int vn = static_cast<int>(16 / h->esize);
+  const int Ts = o.halo_steps ? o.halo_steps : 8;
+  const int Th = (Ts + vn - 1) / vn * vn;
+  const int sE = o.elems_per_thread ? o.elems_per_thread : (h->esize == 8 ? 8 : 16);
+  const int sthreads = o.block_threads ? o.block_threads : 256;
+  if (sE % vn != 0 && o.sync_mode == 2)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: streamed runs need elems_per_thread a multiple of 16 bytes");
+  const int64_t W = static_cast<int64_t>(sthreads) * sE - 2 * Th;
+  if (o.sync_mode == 2 && (W < vn || sthreads > heat1d_impl::max_tile_threads(static_cast<int>(h->esize), sE)))
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: streamed tile too small for halo_steps, or too many threads");
+  const int64_t ntiles = W >= vn ? (h->N + W - 1) / W : 0;
 
   free_scratch(h);
+  h->Ts = Ts;
+  h->Th = Th;
+  h->sE = sE;
+  h->sthreads = sthreads;
+  h->W = static_cast<int>(W);
+  h->ntiles = ntiles;
   h->S = static_cast<int>(S);
   h->q = q;
   h->R = R;
@@ -142,6 +173,38 @@ int configure(heat1d* h, const heat1d_opts& o) {
   HEAT1D_CUDA(cudaMalloc(&h->edges, h->esize * 2 * S * 2 * T));
   HEAT1D_CUDA(cudaMalloc(&h->rings, h->esize * S * 2 * R));
   HEAT1D_CUDA(cudaMalloc(&h->prog, sizeof(int) * S * heat1d_impl::kProgStride));
+  if (ntiles > 0) HEAT1D_CUDA(cudaMalloc(&h->done, sizeof(int) * ntiles));
+  return HEAT1D_OK;
+}
+
+// The streamed synchronous run (temporal blocking through HBM).
+int run_streamed(heat1d* h, int64_t K) {
+  if (h->ntiles <= 0 || (h->sE != 4 && h->sE != 8 && h->sE != 16))
+    return fail(HEAT1D_ERR_INVAL, "streamed run: invalid tile shape (elems_per_thread must be 4, 8 or 16)");
+  heat1d_impl::StreamRun a{};
+  a.N = h->N;
+  a.K = K;
+  a.T = h->Ts;
+  a.Th = h->Th;
+  a.W = h->W;
+  a.ntiles = h->ntiles;
+  a.u_a = h->u[h->cur];
+  a.u_b = h->u[1 - h->cur];
+  a.r = h->r;
+  a.c1 = h->c1;
+  a.cN = h->cN;
+  a.done = h->done;
+  a.status = h->status();
+  a.spin_limit_ns = h->opts.spin_limit_ns;
+  const int resident = heat1d_impl::max_resident_stream(h->dtype, h->sE, h->sthreads);
+  if (resident <= 0) return fail(HEAT1D_ERR_NOT_RESIDENT, "streamed run: kernel cannot be resident");
+  const int grid = static_cast<int>(std::min<int64_t>(h->ntiles, resident));
+  HEAT1D_CUDA(cudaMemsetAsync(h->done, 0, sizeof(int) * h->ntiles, h->stream));
+  int rc = heat1d_impl::launch_stream(a, h->dtype, h->sE, h->sthreads, grid, h->stream);
+  if (rc == HEAT1D_ERR_NOT_RESIDENT) return fail(rc, "streamed run: grid cannot be resident");
+  if (rc) return cuda_fail(cudaGetLastError(), "launch_stream");
+  const int64_t npass = (K + h->Ts - 1) / h->Ts;
+  if (npass & 1) h->cur = 1 - h->cur;
   return HEAT1D_OK;
 }
 
@@ -340,7 +403,7 @@ int heat1d_get_opts(heat1d_t h, heat1d_opts* o) {
   *o = h->opts;
   o->segments = h->S;
   o->q = h->q;
-  o->halo_steps = h->T;
+  o->halo_steps = h->opts.halo_steps ? h->opts.halo_steps : h->T;
   return HEAT1D_OK;
 }
 
@@ -376,8 +439,11 @@ int heat1d_run_sync(heat1d_t h, int64_t K) {
   if (K < 0) return fail(HEAT1D_ERR_INVAL, "K must be >= 0");
   if (K == 0) return HEAT1D_OK;
   int E = 0, threads = 0;
-  int rc = pick_shape(h, h->Lmax + 2 * h->T, 0, &E, &threads);
-  if (rc) return rc;
+  int rc = h->opts.sync_mode == 2 ? HEAT1D_ERR_INVAL : pick_shape(h, h->Lmax + 2 * h->T, 0, &E, &threads);
+  if (rc) {
+    if (h->opts.sync_mode == 1) return rc;
+    return run_streamed(h, K);
+  }
   SegmentRun a = base_run(h, K);
   HEAT1D_CUDA(cudaMemsetAsync(h->barrier(), 0, sizeof(unsigned), h->stream));
   rc = heat1d_impl::launch_sync_persistent(a, h->dtype, E, threads, h->stream);

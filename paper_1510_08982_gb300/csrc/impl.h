@@ -41,6 +41,22 @@ struct SegmentRun {
   int stall_segment;       // -1: off
 };
 
+// Arguments of one temporally blocked synchronous run streamed through HBM.
+struct StreamRun {
+  int64_t N;
+  int64_t K;
+  int T;                   // steps per pass
+  int Th;                  // halo points loaded per side (>= T, 16-byte multiple)
+  int W;                   // tile width (points written per tile), 16-byte multiple
+  int64_t ntiles;
+  void* u_a;               // state at pass 0 (read), then alternating
+  void* u_b;
+  double r, c1, cN;
+  int* done;               // [ntiles] passes completed per tile, 0 at launch
+  int* status;
+  int64_t spin_limit_ns;
+};
+
 // Largest CTA (threads) of the register-tile kernels for a dtype and E: a
 // tile of more than 64 bytes per thread needs more than 64 registers per
 // thread, so it is limited to 512 threads.
@@ -54,6 +70,11 @@ int launch_async_persistent(const SegmentRun& a, int dtype, int E, int threads, 
 
 // Sets the message returned by heat1d_last_error() on this host thread.
 void set_last_error(const std::string& msg);
+
+// Streamed synchronous run: one cooperative launch of `grid` CTAs of `threads`
+// threads, E points per thread (4, 8 or 16); tiles of threads*E slots.
+int launch_stream(const StreamRun& a, int dtype, int E, int threads, int grid, cudaStream_t st);
+int max_resident_stream(int dtype, int E, int threads);
 
 // Largest number of CTAs of these kernels that can be resident at once.
 int max_resident_sync(int dtype, int E, int threads);

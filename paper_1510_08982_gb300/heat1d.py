@@ -41,7 +41,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("segments", ctypes.c_int64), ("q", ctypes.c_int32), ("halo_steps", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("elems_per_thread", ctypes.c_int32),
                 ("spin_limit_ns", ctypes.c_int64), ("stall_segment", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("sync_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 _lib = None
@@ -117,7 +117,7 @@ class Heat1d:
     """One rod of N points: state, options and scratch on the current device.
 
     ``opts`` keywords: segments, q, halo_steps, block_threads,
-    elems_per_thread, spin_limit_ns, stall_segment (see heat1d_opts)."""
+    elems_per_thread, spin_limit_ns, stall_segment, sync_mode (see heat1d_opts)."""
 
     def __init__(self, N, r, c1, cN, dtype="float64", **opts):
         torch = _torch()
