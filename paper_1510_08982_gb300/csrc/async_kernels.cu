@@ -29,9 +29,9 @@ using namespace heat1d_dev;
 
 namespace {
 
-template <typename real>
+template <typename real, int E>
 struct AsyncShared {
-  LockstepShared<real> tile;
+  WindowShared<real, async_window_halo(sizeof(real), E)> win;
   real lring[kMaxRing];  // left neighbour's right-edge values, version v at v & (R-1)
   real rring[kMaxRing];  // right neighbour's left-edge values
   real own_l[kMaxRing];  // this segment's first point per version, for the comm warp
@@ -40,6 +40,8 @@ struct AsyncShared {
   int own_l_ver, own_r_ver;  // newest own version handed to the comm warp
   int compute_done;          // 1: finished, 2: aborted
 };
+
+
 
 // Waits for the neighbour version this step needs and returns its value.
 // Returns false if the wait ran out or the run failed elsewhere.
@@ -78,8 +80,8 @@ __device__ __forceinline__ bool fetch_halo(const SegmentRun& a, const int* avail
 }
 
 // The communication warp's loop (one thread).
-template <typename real>
-__device__ void comm_loop(const SegmentRun& a, AsyncShared<real>& sh, int s) {
+template <typename real, int E>
+__device__ void comm_loop(const SegmentRun& a, AsyncShared<real, E>& sh, int s) {
   const int R = a.R, S = a.S;
   const int K = static_cast<int>(a.K);
   real* rings = static_cast<real*>(a.rings);
@@ -144,7 +146,9 @@ __device__ void comm_loop(const SegmentRun& a, AsyncShared<real>& sh, int s) {
 
 template <typename real, int E>
 __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_persistent_kernel(SegmentRun a) {
-  __shared__ AsyncShared<real> sh;
+  using Win = Window<E, async_window_halo(sizeof(real), E)>;
+  constexpr int kRefresh = Win::H;  // steps between two halo refreshes
+  __shared__ AsyncShared<real, E> sh;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwc = (blockDim.x >> 5) - 1;  // compute warps; the last warp communicates
@@ -156,11 +160,10 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
     sh.own_r_ver = -1;
     sh.compute_done = 0;
   }
-  if (tid == 0) sh.tile.abort = 0;
   __syncthreads();
 
   if (warp == nwc) {
-    if (lane == 0) comm_loop<real>(a, sh, s);
+    if (lane == 0) comm_loop<real, E>(a, sh, s);
     return;
   }
 
@@ -175,34 +178,41 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
   real* __restrict__ uout = static_cast<real*>(a.u_out);
   const bool has_left = s > 0, has_right = s + 1 < S;
 
-  // Slot j holds global point a0 - 1 + j: slot 0 and slot L+1 are the halos.
+  // Position p holds global point a0 - 1 + p: positions 0 and L+1 are the
+  // halos, written from the neighbours' versions before every step.
   real v[E];
   unsigned fixed = 0;
+  int e_first = -1, e_last = -1, e_rh = -1;  // slots of this thread holding positions 1, L (owners) and L+1
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int slot = tid * E + e;
-    const int64_t g = a0 - 1 + slot;
+    const int p = Win::pos(warp, lane, e);
+    const int64_t g = a0 - 1 + p;
     real x = static_cast<real>(0);
-    if (slot >= 1 && slot <= L) x = uin[g];
+    if (p >= 1 && p <= L) x = uin[g];
     if (g == 0) x = c1;
     if (g == N - 1) x = cN;
     v[e] = x;
-    if (slot == 0 || slot >= L + 1 || g <= 0 || g >= N - 1) fixed |= 1u << e;
+    if (p == 0 || p >= L + 1 || g <= 0 || g >= N - 1) fixed |= 1u << e;
+    const bool own = Win::owner(warp, lane, e, nwc);
+    if (p == 1 && own) e_first = e;
+    if (p == L && own) e_last = e;
+    // the copy of position L+1 in the same warp as position L's owner
+    if (p == L + 1 && ((e > 0 && Win::owner(warp, lane, e - 1, nwc)) ||
+                       (e == 0 && lane > 0 && Win::owner(warp, lane - 1, E - 1, nwc))))
+      e_rh = e;
   }
   const int mode = tile_mode<E>(fixed);
-  const int nwarps_c = nwc;
-  const int t_first = 1 / E, e_first = 1 % E;  // slot 1: first own point
-  const int t_last = L / E, e_last = L % E;     // slot L: last own point
-  const int t_rh = (L + 1) / E, e_rh = (L + 1) % E;  // slot L+1: right halo
+  const bool left_reader = has_left && warp == 0 && lane == 0;  // position 0 is (warp 0, lane 0, slot 0)
+  const bool right_reader = has_right && e_rh >= 0;
 
   // Version 0 of the edges goes to the comm warp.
-  if (tid == t_first) {
+  if (e_first >= 0) {
 #pragma unroll
     for (int e = 0; e < E; ++e)
       if (e == e_first) sh.own_l[0] = v[e];
     st_release_cta_shared(&sh.own_l_ver, 0);
   }
-  if (tid == t_last) {
+  if (e_last >= 0) {
 #pragma unroll
     for (int e = 0; e < E; ++e)
       if (e == e_last) sh.own_r[0] = v[e];
@@ -216,18 +226,15 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
   const size_t tr = static_cast<size_t>(s) * 2 + 0;                     // side 0 of boundary s
   int dl_next = 0, dr_next = 0;
   if (trace_in && K > 0) {
-    if (tid == 0 && has_left) dl_next = __ldg(trace_in + tl);
-    if (tid == t_rh && has_right) dr_next = __ldg(trace_in + tr);
+    if (left_reader) dl_next = __ldg(trace_in + tl);
+    if (right_reader) dr_next = __ldg(trace_in + tr);
   }
 
+  bool failed = false;   // a wait of this thread gave up: no more waits until the CTA leaves
   bool aborted = false;
+  int parity = 0;
   for (int k = 0; k < K; ++k) {
-    // Leave together when a wait anywhere in the CTA gave up.
-    if (__shfl_sync(kFullMask, lane == 0 ? ld_volatile_shared(&sh.tile.abort) : 0, 0)) {
-      aborted = true;
-      break;
-    }
-    if (tid == 0 && has_left) {
+    if (left_reader && !failed) {
       const int d = dl_next;
       if (trace_in && k + 1 < K) dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
       real val;
@@ -235,9 +242,9 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
                            val))
         v[0] = val;
       else
-        *reinterpret_cast<volatile int*>(&sh.tile.abort) = 1;
+        failed = true;
     }
-    if (tid == t_rh && has_right) {
+    if (right_reader && !failed) {
       const int d = dr_next;
       if (trace_in && k + 1 < K) dr_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tr);
       real val;
@@ -247,29 +254,39 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
         for (int e = 0; e < E; ++e)
           if (e == e_rh) v[e] = val;
       } else {
-        *reinterpret_cast<volatile int*>(&sh.tile.abort) = 1;
+        failed = true;
       }
     }
-    lockstep_step_any<real, E>(mode, v, fixed, coef, sh.tile, static_cast<unsigned>(k), warp, lane, nwarps_c);
+    warp_step_any<real, E>(mode, v, fixed, coef);
     const int ver = k + 1, j = ver & (a.R - 1);
-    if (tid == t_first) {
+    if (e_first >= 0) {
 #pragma unroll
       for (int e = 0; e < E; ++e)
         if (e == e_first) sh.own_l[j] = v[e];
       st_release_cta_shared(&sh.own_l_ver, ver);
     }
-    if (tid == t_last) {
+    if (e_last >= 0) {
 #pragma unroll
       for (int e = 0; e < E; ++e)
         if (e == e_last) sh.own_r[j] = v[e];
       st_release_cta_shared(&sh.own_r_ver, ver);
     }
+    // Refresh the warp halos every kRefresh steps (and after the last step);
+    // the refresh barrier also tells every warp whether a wait gave up.
+    if (ver % kRefresh == 0 || ver == K) {
+      const bool any_failed = warp_refresh<real, E, Win::H>(v, sh.win, parity, warp, lane, nwc, nthreads_c, failed);
+      parity ^= 1;
+      if (any_failed) {
+        aborted = true;
+        break;
+      }
+    }
   }
 
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int slot = tid * E + e;
-    if (slot >= 1 && slot <= L) uout[a0 - 1 + slot] = v[e];
+    const int p = Win::pos(warp, lane, e);
+    if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) uout[a0 - 1 + p] = v[e];
   }
   named_barrier_sync(1, nthreads_c);
   if (tid == 0) st_release_cta_shared(&sh.compute_done, aborted ? 2 : 1);

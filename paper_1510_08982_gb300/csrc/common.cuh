@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "heat1d.h"
+#include "impl.h"
 
 namespace heat1d_dev {
 
@@ -121,76 +122,30 @@ __device__ __forceinline__ float ftcs(float r, float /*one*/, float uL, float u,
   return __fmaf_rn(r, __fadd_rn(__fmaf_rn(-2.0f, u, uR), uL), u);
 }
 
-// ------------------------------------------------------------ register tile
+// ------------------------------------------------------------ warp windows
 //
-// A CTA (or its compute warps) holds a contiguous run of "slots" in registers:
-// thread t holds slots t*E .. t*E+E-1 in v[0..E-1].  One step updates every
-// slot whose bit in `fixed` is clear from its two neighbours; neighbours in
-// the same thread come from registers, across lanes from shuffles, and across
-// warps from shared memory.  Slots whose bit is set keep their value
-// (Dirichlet ends, halo ends, padding).
+// The compute warps of a CTA hold a contiguous run of points ("positions")
+// in registers.  Warp w covers the window of 32*E positions starting at w*D,
+// D = 32*E - 2*H, 1 <= H <= E/2: lane l holds positions w*D + l*E + e in v[e].
+// Adjacent windows overlap by 2*H positions, so each warp carries H halo
+// points on each side that belong to its neighbours.
 //
-// There is no CTA-wide barrier per step.  Lane 0 and lane 31 of warp w publish
-// the warp's first and last value of step k in a two-parity shared array and
-// then a per-warp flag (release at CTA scope); lane 0 of warp w+1 and lane 31
-// of warp w-1 wait for that flag (acquire) before reading.  A warp therefore
-// waits only for its two neighbours, and warps may be one step apart, which
-// keeps the arithmetic pipe busy across step boundaries.  Two parities
-// suffice: a warp cannot publish step k+2 (overwriting step k) before both
-// neighbours have published step k+1, i.e. have finished reading step k.
-
-template <typename real>
-struct TileShared {
-  real first[2][32];      // v[0] of lane 0 of each warp, per step parity
-  real last[2][32];       // v[E-1] of lane 31 of each warp, per step parity
-  unsigned fflag[32];     // step whose `first` value warp w has published (+1; 0 = none)
-  unsigned lflag[32];     // same for `last`
-  int abort;              // non-zero: stop waiting, leave the step loop
-};
-
-// Must be called by the CTA before the first step, followed by a barrier.
-template <typename real>
-__device__ __forceinline__ void tile_shared_init(TileShared<real>& sh, int tid) {
-  if (tid < 32) {
-    sh.fflag[tid] = 0u;
-    sh.lflag[tid] = 0u;
-  }
-  if (tid == 0) sh.abort = 0;
-}
-
-__device__ __forceinline__ unsigned ld_acquire_cta_shared_u32(const unsigned* p) {
-  unsigned v;
-  unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
-  asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_cta_shared_u32(unsigned* p, unsigned v) {
-  unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
-  asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ int ld_volatile_shared(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
-
-// Waits until *flag has reached `want` (wrap-safe).  Gives up, setting the
-// CTA's abort flag, when the abort flag is already set or after `limit_ns`.
-static __device__ __noinline__ bool tile_wait_flag(const unsigned* flag, unsigned want, int* abort, int64_t limit_ns) {
-  unsigned spins = 0;
-  uint64_t t0 = 0;
-  while (static_cast<int>(ld_acquire_cta_shared_u32(flag) - want) < 0) {
-    if (ld_volatile_shared(abort)) return false;
-    if ((++spins & 255u) == 0) {
-      const uint64_t t = global_timer_ns();
-      if (t0 == 0) {
-        t0 = t;
-      } else if (static_cast<int64_t>(t - t0) > limit_ns) {
-        *reinterpret_cast<volatile int*>(abort) = 1;
-        return false;
-      }
-    }
-  }
-  return true;
-}
+// A step inside a warp needs no other warp: neighbours within a thread come
+// from registers, across lanes from shuffles; lane 0's first point and lane
+// 31's last point read garbage and become invalid, and the invalid region
+// grows by one point per side per step.  After at most H steps the warps
+// refresh their halos from their neighbours' valid points through shared
+// memory, with one CTA barrier.  The redundant work is 2H/(32E) of the
+// arithmetic and the warps synchronise once per H steps, not per step
+// (the choice of H per kernel is in impl.h).
+// Because the halo points are recomputed with the same arithmetic, results
+// are bit-identical to updating every point once per step.
+//
+// Positions whose bit in `fixed` is set keep their value (Dirichlet ends,
+// halo points written from outside, padding).  Positions in an overlap are
+// held by two warps; only the "owner" (warp w owns its interior positions
+// [w*D + H, w*D + 32E - H); warp 0 and the last warp also own the CTA's outer
+// H positions) publishes or stores them.
 
 // Stencil coefficients: r, and a run-time 1.0 (see ftcs).
 template <typename real>
@@ -199,10 +154,30 @@ struct Coef {
   real one;
 };
 
-// How a warp steps: every slot updated, some slots fixed (select), or every
-// slot fixed (padding warps: no arithmetic, but they publish and wait like the
-// others, so that no warp runs ahead of its neighbours -- a halo slot written
-// from outside the tile may sit in such a warp).
+template <int E, int H_>
+struct Window {
+  static_assert(E >= 2 && E % 2 == 0, "E must be even");
+  static constexpr int H = H_;            // halo points per warp side
+  static constexpr int D = 32 * E - 2 * H;  // stride between warp windows
+  static_assert(H >= 1 && 2 * H <= E, "halo must fit in lanes 0 and 31");
+  __device__ static __forceinline__ int pos(int warp, int lane, int e) { return warp * D + lane * E + e; }
+  __device__ static __forceinline__ bool owner(int warp, int lane, int e, int nwarps) {
+    if (lane == 0 && e < H) return warp == 0;
+    if (lane == 31 && e >= E - H) return warp == nwarps - 1;
+    return true;
+  }
+};
+
+// Halo exchange buffers: two parities (a warp cannot write parity p again
+// before every warp passed the barrier of the refresh in between).
+template <typename real, int H>
+struct WindowShared {
+  real to_right[2][32][H];  // lane 31's positions [E-2H, E-H): the next warp's left halo
+  real to_left[2][32][H];   // lane 0's positions [H, 2H): the previous warp's right halo
+};
+
+// How a warp steps: every point updated, some points fixed (select), or every
+// point fixed (padding warps: no arithmetic).
 enum TileMode { kTileFree = 0, kTileMasked = 1, kTileIdle = 2 };
 
 template <int E>
@@ -212,133 +187,83 @@ __device__ __forceinline__ int tile_mode(unsigned fixed) {
   return __any_sync(kFullMask, fixed != 0u) ? kTileMasked : kTileFree;
 }
 
-// One step k -> k+1 of the warp.  Returns false (warp-uniform) if a wait gave
-// up because the CTA is aborting; the values are then unspecified.
+// One step of one warp (no other warp involved).
 template <typename real, int E, int kMode>
-__device__ __forceinline__ bool tile_step(real (&v)[E], unsigned fixed, Coef<real> c, TileShared<real>& sh,
-                                          unsigned k, int warp, int lane, int nwarps, int64_t limit_ns) {
-  const int p = k & 1u;
-  if (lane == 0) {
-    sh.first[p][warp] = v[0];
-    st_release_cta_shared_u32(&sh.fflag[warp], k + 1u);
+__device__ __forceinline__ void warp_step(real (&v)[E], unsigned fixed, Coef<real> c) {
+  const real left = __shfl_up_sync(kFullMask, v[E - 1], 1);
+  const real right = __shfl_down_sync(kFullMask, v[0], 1);
+  if (kMode == kTileIdle) return;
+  real prev = left;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const real cur = v[e];
+    const real nxt = (e + 1 < E) ? v[e + 1] : right;
+    const real nv = ftcs(c.r, c.one, prev, cur, nxt);
+    if (kMode == kTileMasked) {
+      v[e] = ((fixed >> e) & 1u) ? cur : nv;
+    } else {
+      v[e] = nv;
+    }
+    prev = cur;
   }
+}
+
+template <typename real, int E>
+__device__ __forceinline__ void warp_step_any(int mode, real (&v)[E], unsigned fixed, Coef<real> c) {
+  if (mode == kTileFree)
+    warp_step<real, E, kTileFree>(v, fixed, c);
+  else if (mode == kTileMasked)
+    warp_step<real, E, kTileMasked>(v, fixed, c);
+  else
+    warp_step<real, E, kTileIdle>(v, fixed, c);
+}
+
+// Refreshes every warp's halos from its neighbours (one barrier over the
+// `nthreads` compute threads, named barrier 1).  Returns the OR of `flag`
+// over those threads, so that a failure seen by one thread reaches all of
+// them at the same point.
+template <typename real, int E, int H>
+__device__ __forceinline__ bool warp_refresh(real (&v)[E], WindowShared<real, H>& sh, int parity, int warp, int lane,
+                                             int nwarps, unsigned nthreads, bool flag) {
   if (lane == 31) {
-    sh.last[p][warp] = v[E - 1];
-    st_release_cta_shared_u32(&sh.lflag[warp], k + 1u);
+#pragma unroll
+    for (int i = 0; i < H; ++i) sh.to_right[parity][warp][i] = v[E - 2 * H + i];
   }
-  real left = __shfl_up_sync(kFullMask, v[E - 1], 1);
-  real right = __shfl_down_sync(kFullMask, v[0], 1);
-  bool ok = true;
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < H; ++i) sh.to_left[parity][warp][i] = v[H + i];
+  }
+  const bool any = named_barrier_or(1, nthreads, flag);
   if (lane == 0 && warp > 0) {
-    ok = tile_wait_flag(&sh.lflag[warp - 1], k + 1u, &sh.abort, limit_ns);
-    left = sh.last[p][warp - 1];
+#pragma unroll
+    for (int i = 0; i < H; ++i) v[i] = sh.to_right[parity][warp - 1][i];
   }
   if (lane == 31 && warp + 1 < nwarps) {
-    ok = tile_wait_flag(&sh.fflag[warp + 1], k + 1u, &sh.abort, limit_ns);
-    right = sh.first[p][warp + 1];
-  }
-  if (!__all_sync(kFullMask, ok)) return false;
-  if (kMode == kTileIdle) return true;
-  real prev = left;
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const real cur = v[e];
-    const real nxt = (e + 1 < E) ? v[e + 1] : right;
-    const real nv = ftcs(c.r, c.one, prev, cur, nxt);
-    if (kMode == kTileMasked) {
-      v[e] = ((fixed >> e) & 1u) ? cur : nv;
-    } else {
-      v[e] = nv;
+    for (int i = 0; i < H; ++i) v[E - H + i] = sh.to_left[parity][warp + 1][i];
+  }
+  return any;
+}
+
+// Advances the CTA `steps` steps: runs of at most H warp steps, each followed
+// by a refresh, so the windows are fully valid again when it returns.
+template <typename real, int E, int H>
+__device__ __forceinline__ void warp_advance(int mode, real (&v)[E], unsigned fixed, Coef<real> c,
+                                             WindowShared<real, H>& sh, int& parity, int warp, int lane, int nwarps,
+                                             unsigned nthreads, int steps) {
+  for (int done = 0; done < steps;) {
+    const int n = min(H, steps - done);
+    if (mode == kTileFree) {
+      for (int j = 0; j < n; ++j) warp_step<real, E, kTileFree>(v, fixed, c);
+    } else if (mode == kTileMasked) {
+      for (int j = 0; j < n; ++j) warp_step<real, E, kTileMasked>(v, fixed, c);
     }
-    prev = cur;
-  }
-  return true;
-}
-
-// One step in the warp's mode (mode from tile_mode, warp-uniform).
-template <typename real, int E>
-__device__ __forceinline__ bool tile_step_any(int mode, real (&v)[E], unsigned fixed, Coef<real> c,
-                                              TileShared<real>& sh, unsigned k, int warp, int lane, int nwarps,
-                                              int64_t limit_ns) {
-  if (mode == kTileFree)
-    return tile_step<real, E, kTileFree>(v, fixed, c, sh, k, warp, lane, nwarps, limit_ns);
-  if (mode == kTileMasked)
-    return tile_step<real, E, kTileMasked>(v, fixed, c, sh, k, warp, lane, nwarps, limit_ns);
-  return tile_step<real, E, kTileIdle>(v, fixed, c, sh, k, warp, lane, nwarps, limit_ns);
-}
-
-// ------------------------------------------------------------ lockstep tile
-//
-// The same step with a CTA-wide barrier per step instead of neighbour flags,
-// so that no warp is ever more than one step away from any other.  The
-// asynchronous run uses it: there the two edge warps must not lag behind the
-// rest of the segment, or the delay seen by the neighbouring segments grows
-// (with neighbour flags alone the skew across a CTA can reach one step per
-// warp).  Two parities of edge values and one barrier per step suffice.
-
-template <typename real>
-struct LockstepShared {
-  real first[2][32];
-  real last[2][32];
-  int abort;  // set by a failed wait; every warp leaves at the next step
-};
-
-template <typename real, int E, int kMode>
-__device__ __forceinline__ void lockstep_step(real (&v)[E], unsigned fixed, Coef<real> c, LockstepShared<real>& sh,
-                                              unsigned k, int warp, int lane, int nwarps) {
-  const int p = k & 1u;
-  if (lane == 0) sh.first[p][warp] = v[0];
-  if (lane == 31) sh.last[p][warp] = v[E - 1];
-  real left = __shfl_up_sync(kFullMask, v[E - 1], 1);
-  real right = __shfl_down_sync(kFullMask, v[0], 1);
-  named_barrier_sync(1, static_cast<unsigned>(nwarps) * 32u);
-  if (kMode == kTileIdle) return;
-  if (lane == 0 && warp > 0) left = sh.last[p][warp - 1];
-  if (lane == 31 && warp + 1 < nwarps) right = sh.first[p][warp + 1];
-  real prev = left;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const real cur = v[e];
-    const real nxt = (e + 1 < E) ? v[e + 1] : right;
-    const real nv = ftcs(c.r, c.one, prev, cur, nxt);
-    if (kMode == kTileMasked) {
-      v[e] = ((fixed >> e) & 1u) ? cur : nv;
-    } else {
-      v[e] = nv;
-    }
-    prev = cur;
+    warp_refresh<real, E, H>(v, sh, parity, warp, lane, nwarps, nthreads, false);
+    parity ^= 1;
+    done += n;
   }
 }
 
-template <typename real, int E>
-__device__ __forceinline__ void lockstep_step_any(int mode, real (&v)[E], unsigned fixed, Coef<real> c,
-                                                  LockstepShared<real>& sh, unsigned k, int warp, int lane,
-                                                  int nwarps) {
-  if (mode == kTileFree)
-    lockstep_step<real, E, kTileFree>(v, fixed, c, sh, k, warp, lane, nwarps);
-  else if (mode == kTileMasked)
-    lockstep_step<real, E, kTileMasked>(v, fixed, c, sh, k, warp, lane, nwarps);
-  else
-    lockstep_step<real, E, kTileIdle>(v, fixed, c, sh, k, warp, lane, nwarps);
-}
-
-// Runs steps k0 .. k0+steps-1.  Returns false if the CTA aborted.
-template <typename real, int E>
-__device__ __forceinline__ bool tile_steps(int mode, real (&v)[E], unsigned fixed, Coef<real> c,
-                                           TileShared<real>& sh, unsigned k0, int warp, int lane, int nwarps,
-                                           int steps, int64_t limit_ns) {
-  bool ok = true;
-  if (mode == kTileFree) {
-    for (int j = 0; j < steps && ok; ++j)
-      ok = tile_step<real, E, kTileFree>(v, fixed, c, sh, k0 + j, warp, lane, nwarps, limit_ns);
-  } else if (mode == kTileMasked) {
-    for (int j = 0; j < steps && ok; ++j)
-      ok = tile_step<real, E, kTileMasked>(v, fixed, c, sh, k0 + j, warp, lane, nwarps, limit_ns);
-  } else {
-    for (int j = 0; j < steps && ok; ++j)
-      ok = tile_step<real, E, kTileIdle>(v, fixed, c, sh, k0 + j, warp, lane, nwarps, limit_ns);
-  }
-  return ok;
-}
+__device__ __forceinline__ int ld_volatile_shared(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
 }  // namespace heat1d_dev

@@ -44,7 +44,6 @@ __global__ void set_ends_kernel(real* u, int64_t N, double c1, double cN) {
   if (threadIdx.x == 1) u[N - 1] = static_cast<real>(cN);
 }
 
-int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
@@ -129,7 +128,7 @@ int configure(heat1d* h, const heat1d_opts& o) {
   // On-chip synchronous runs take halos from the neighbouring segment only,
   // so their T is at most the shortest segment (clamped unless on-chip mode
   // was asked for explicitly).
-  int T = o.halo_steps ? o.halo_steps : 32;
+  int T = o.halo_steps ? o.halo_steps : 64;
   if (T > Lmin) {
     if (o.halo_steps && o.sync_mode == 1)
       return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: halo_steps exceeds the shortest segment");
@@ -147,7 +146,8 @@ int configure(heat1d* h, const heat1d_opts& o) {
   const int sthreads = o.block_threads ? o.block_threads : 256;
   if (sE % vn != 0 && o.sync_mode == 2)
     return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: streamed runs need elems_per_thread a multiple of 16 bytes");
-  const int64_t W = static_cast<int64_t>(sthreads) * sE - 2 * Th;
+  const int64_t W =
+      heat1d_impl::window_width(sthreads / 32, sE, heat1d_impl::sync_window_halo(static_cast<int>(h->esize), sE)) - 2 * Th;
   if (o.sync_mode == 2 && (W < vn || sthreads > heat1d_impl::max_tile_threads(static_cast<int>(h->esize), sE)))
     return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: streamed tile too small for halo_steps, or too many threads");
   const int64_t ntiles = W >= vn ? (h->N + W - 1) / W : 0;
@@ -208,18 +208,20 @@ int run_streamed(heat1d* h, int64_t K) {
   return HEAT1D_OK;
 }
 
-// Launch shape for a tile of `slots` points: the fewest points per thread E
-// whose thread count fits the kernel's CTA limit minus `reserved` threads (the
-// asynchronous kernel's communication warp), unless E or the thread count is
-// forced by the options.
-int pick_shape(const heat1d* h, int64_t slots, int reserved, int* E, int* threads) {
+// Launch shape for a tile of `slots` positions: the fewest points per thread E
+// whose warp count (overlapping warp windows of 32E points, see common.cuh)
+// fits the kernel's CTA limit minus `reserved` threads (the asynchronous
+// kernel's communication warp), unless E or the thread count is forced.
+int pick_shape(const heat1d* h, int64_t slots, int reserved, bool async_kernel, int* E, int* threads) {
   const int forced_E = h->opts.elems_per_thread;
   const int Es[4] = {2, 4, 8, 16};
   for (int i = 0; i < 4; ++i) {
     const int e = Es[i];
     if (forced_E && e != forced_E) continue;
     const int64_t limit = heat1d_impl::max_tile_threads(static_cast<int>(h->esize), e) - reserved;
-    int64_t t = std::max<int64_t>(round_up((slots + e - 1) / e, 32), 32);
+    const int es = static_cast<int>(h->esize);
+    const int H = async_kernel ? heat1d_impl::async_window_halo(es, e) : heat1d_impl::sync_window_halo(es, e);
+    int64_t t = 32 * heat1d_impl::window_warps(slots, e, H);
     if (h->opts.block_threads) {
       if (h->opts.block_threads < t) continue;
       t = h->opts.block_threads;
@@ -275,7 +277,7 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   if (K < 0 || K >= INT_MAX) return fail(HEAT1D_ERR_INVAL, "K out of range");
   if (K == 0) return HEAT1D_OK;
   int E = 0, threads = 0;
-  int rc = pick_shape(h, h->Lmax + 2, 32, &E, &threads);
+  int rc = pick_shape(h, h->Lmax + 2, 32, true, &E, &threads);
   if (rc) return rc;
   const size_t tbytes = static_cast<size_t>(K) * (h->S - 1) * 2;
   SegmentRun a = base_run(h, K);
@@ -439,7 +441,7 @@ int heat1d_run_sync(heat1d_t h, int64_t K) {
   if (K < 0) return fail(HEAT1D_ERR_INVAL, "K must be >= 0");
   if (K == 0) return HEAT1D_OK;
   int E = 0, threads = 0;
-  int rc = h->opts.sync_mode == 2 ? HEAT1D_ERR_INVAL : pick_shape(h, h->Lmax + 2 * h->T, 0, &E, &threads);
+  int rc = h->opts.sync_mode == 2 ? HEAT1D_ERR_INVAL : pick_shape(h, h->Lmax + 2 * h->T, 0, false, &E, &threads);
   if (rc) {
     if (h->opts.sync_mode == 1) return rc;
     return run_streamed(h, K);

@@ -62,6 +62,21 @@ struct StreamRun {
 // thread, so it is limited to 512 threads.
 constexpr int max_tile_threads(int elem_bytes, int E) { return elem_bytes * E > 64 ? 512 : 1024; }
 
+// Warp windows (common.cuh): warp w covers 32E positions starting at w*D,
+// D = 32E - 2H, where H (halo points per warp side = steps between two
+// refreshes) trades redundant arithmetic (2H/32E) against barriers (one per
+// H steps).  The synchronous kernels use H = E/2 in FP32 and E/4 in FP64
+// (at least 1): FP64 arithmetic is costly, so less redundancy is worth more
+// barriers.  The asynchronous kernel uses H = E/2: its edge warps must not be
+// held back by frequent barriers.  A CTA of nw compute warps covers
+// nw*D + 2H positions.
+constexpr int sync_window_halo(int elem_bytes, int E) { return elem_bytes == 8 ? (E >= 4 ? E / 4 : 1) : E / 2; }
+constexpr int async_window_halo(int /*elem_bytes*/, int E) { return E / 2; }
+constexpr int64_t window_width(int64_t nwarps, int E, int H) { return nwarps * (32 * E - 2 * H) + 2 * H; }
+constexpr int64_t window_warps(int64_t positions, int E, int H) {
+  return positions <= 2 * H ? 1 : (positions - 2 * H + (32 * E - 2 * H) - 1) / (32 * E - 2 * H);
+}
+
 // Launch the persistent kernels (cooperative launch: all S CTAs resident).
 // E is the number of points per thread (2, 4, 8 or 16); `threads` the compute
 // threads per CTA (a multiple of 32).  Return a heat1d_status code.

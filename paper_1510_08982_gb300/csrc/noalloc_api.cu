@@ -117,8 +117,8 @@ extern "C" int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N,
   int E = 0, threads = 0;
   const int Es[4] = {2, 4, 8, 16};
   for (int i = 0; i < 4 && !E; ++i) {
-    const int64_t per_thread = (slots + Es[i] - 1) / Es[i];
-    const int64_t t = std::max<int64_t>((per_thread + 31) / 32 * 32, 32);
+    const int64_t t =
+        32 * heat1d_impl::window_warps(slots, Es[i], heat1d_impl::sync_window_halo(static_cast<int>(esize), Es[i]));
     if (t <= heat1d_impl::max_tile_threads(static_cast<int>(esize), Es[i])) {
       E = Es[i];
       threads = static_cast<int>(t);

@@ -62,13 +62,12 @@ __device__ bool wait_tile(const int* done, int want, int* status, int64_t limit_
 template <typename real, int E>
 __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) stream_kernel(StreamRun a) {
   using V = typename Vec16<real>::type;
+  using Win = Window<E, sync_window_halo(sizeof(real), E)>;
   constexpr int VN = Vec16<real>::n;
   static_assert(E % VN == 0, "E must be a multiple of the 16-byte vector width");
-  __shared__ TileShared<real> sh;
+  __shared__ WindowShared<real, Win::H> sh;
   __shared__ int sh_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  tile_shared_init(sh, tid);
-  __syncthreads();
 
   const int64_t N = a.N;
   const int Th = a.Th, W = a.W;
@@ -76,7 +75,10 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) stream_k
   const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};
   real* buf[2] = {static_cast<real*>(a.u_a), static_cast<real*>(a.u_b)};
   const int npass = static_cast<int>((a.K + a.T - 1) / a.T);
-  unsigned kstep = 0;  // steps taken by this CTA's tiles so far (flag sequence)
+  const int p0 = Win::pos(warp, lane, 0);  // this thread's first position
+  // lanes 1..30 own all their positions; lanes 0 and 31 may hold halo copies
+  const bool owns_all = Win::owner(warp, lane, 0, nwarps) && Win::owner(warp, lane, E - 1, nwarps);
+  int parity = 0;
 
   for (int p = 0; p < npass; ++p) {
     const real* __restrict__ src = buf[p & 1];
@@ -93,9 +95,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) stream_k
         __syncthreads();
         if (!sh_ok) return;
       }
-      // Load: slot s holds global point g0 + s, g0 = j*W - Th.
-      const int64_t g0 = j * W - Th;
-      const int64_t gt = g0 + static_cast<int64_t>(tid) * E;
+      // Load: position q holds global point g0 + q, g0 = j*W - Th.
+      const int64_t gt = j * W - Th + p0;
       real v[E];
       if (gt >= 0 && gt + E <= N) {
 #pragma unroll
@@ -121,13 +122,10 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) stream_k
         if (g <= 0 || g >= N - 1) fixed |= 1u << e;
       }
       const int mode = tile_mode<E>(fixed);
-      if (!tile_steps<real, E>(mode, v, fixed, coef, sh, kstep, warp, lane, nwarps, tb, a.spin_limit_ns))
-        raise_status(a.status, HEAT1D_ERR_TIMEOUT);
-      kstep += tb;
+      warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
 
-      // Store the W own points (slots Th .. Th+W-1) that lie inside the rod.
-      const int s0 = tid * E;
-      if (s0 >= Th && s0 + E <= Th + W && gt >= 0 && gt + E <= N) {
+      // Store the W own points (positions Th .. Th+W-1) inside the rod.
+      if (owns_all && p0 >= Th && p0 + E <= Th + W && gt >= 0 && gt + E <= N) {
 #pragma unroll
         for (int i = 0; i < E / VN; ++i) {
           V x;
@@ -139,9 +137,9 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) stream_k
       } else {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const int s = s0 + e;
+          const int q = p0 + e;
           const int64_t g = gt + e;
-          if (s >= Th && s < Th + W && g >= 0 && g < N) __stcg(dst + g, v[e]);
+          if (q >= Th && q < Th + W && g >= 0 && g < N && Win::owner(warp, lane, e, nwarps)) __stcg(dst + g, v[e]);
         }
       }
       __syncthreads();
@@ -149,7 +147,6 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) stream_k
         __threadfence();
         st_release_gpu(a.done + j, p + 1);
       }
-      if (sh.abort) return;  // CTA-uniform after the barrier above
     }
   }
 }

@@ -47,11 +47,11 @@ __device__ bool grid_barrier(unsigned* counter, unsigned target, int* status, in
 
 template <typename real, int E>
 __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_persistent_kernel(SegmentRun a) {
-  __shared__ TileShared<real> sh;
+  using Win = Window<E, sync_window_halo(sizeof(real), E)>;
+  __shared__ WindowShared<real, Win::H> sh;
   __shared__ int sh_ok;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  tile_shared_init(sh, tid);
   const int64_t N = a.N;
   const int64_t a0 = a.seg_off[s];
   const int L = static_cast<int>(a.seg_off[s + 1] - a0);
@@ -63,64 +63,61 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
   real* __restrict__ uout = static_cast<real*>(a.u_out);
   real* edges = static_cast<real*>(a.edges);
 
-  // Slot j of the tile holds global point a0 - T + j.
+  // Position p of the CTA holds global point a0 - T + p.
   real v[E];
   unsigned fixed = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int slot = tid * E + e;
-    const int64_t g = a0 - T + slot;
+    const int p = Win::pos(warp, lane, e);
+    const int64_t g = a0 - T + p;
     real x = static_cast<real>(0);
-    if (slot < Lh && g >= 0 && g < N) x = uin[g];
+    if (p < Lh && g >= 0 && g < N) x = uin[g];
     if (g == 0) x = c1;
     if (g == N - 1) x = cN;
     v[e] = x;
-    if (slot >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
+    if (p >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
   }
-
   const int mode = tile_mode<E>(fixed);
-  __syncthreads();
 
+  int parity = 0;
   unsigned epoch = 0;
   for (int64_t k0 = 0; k0 < a.K; k0 += T) {
     const int tb = static_cast<int>(std::min<int64_t>(T, a.K - k0));
-    if (!tile_steps<real, E>(mode, v, fixed, coef, sh, static_cast<unsigned>(k0), warp, lane, nwarps, tb,
-                             a.spin_limit_ns))
-      raise_status(a.status, HEAT1D_ERR_TIMEOUT);
+    warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
     if (k0 + tb >= a.K) break;
 
     // Publish the first T and the last T points of the segment.
     real* mine = edges + (static_cast<size_t>(epoch & 1u) * a.S + s) * 2 * T;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int slot = tid * E + e;
-      if (slot >= T && slot < 2 * T) st_cg(mine + (slot - T), v[e]);
-      if (slot >= L && slot < L + T) st_cg(mine + T + (slot - L), v[e]);
+      const int p = Win::pos(warp, lane, e);
+      if (!Win::owner(warp, lane, e, nwarps)) continue;
+      if (p >= T && p < 2 * T) st_cg(mine + (p - T), v[e]);
+      if (p >= L && p < L + T) st_cg(mine + T + (p - L), v[e]);
     }
     __syncthreads();
     if (tid == 0) {
-      sh_ok = !sh.abort &&
-              grid_barrier(a.barrier, static_cast<unsigned>(a.S) * (epoch + 1u), a.status, a.spin_limit_ns);
+      sh_ok = grid_barrier(a.barrier, static_cast<unsigned>(a.S) * (epoch + 1u), a.status, a.spin_limit_ns);
     }
     __syncthreads();
     if (!sh_ok) return;  // CTA-uniform: every thread reads the same flag
 
-    // Reload the halos: the left neighbour's last T points, the right
-    // neighbour's first T points.
+    // Reload the halos (every copy): the left neighbour's last T points, the
+    // right neighbour's first T points.
     if (s > 0) {
       const real* left = edges + (static_cast<size_t>(epoch & 1u) * a.S + (s - 1)) * 2 * T;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int slot = tid * E + e;
-        if (slot < T) v[e] = ld_cg(left + T + slot);
+        const int p = Win::pos(warp, lane, e);
+        if (p < T) v[e] = ld_cg(left + T + p);
       }
     }
     if (s + 1 < a.S) {
       const real* right = edges + (static_cast<size_t>(epoch & 1u) * a.S + (s + 1)) * 2 * T;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int slot = tid * E + e;
-        if (slot >= L + T && slot < L + 2 * T) v[e] = ld_cg(right + (slot - L - T));
+        const int p = Win::pos(warp, lane, e);
+        if (p >= L + T && p < L + 2 * T) v[e] = ld_cg(right + (p - L - T));
       }
     }
     ++epoch;
@@ -128,8 +125,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int slot = tid * E + e;
-    if (slot >= T && slot < T + L) uout[a0 + (slot - T)] = v[e];
+    const int p = Win::pos(warp, lane, e);
+    if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) uout[a0 + (p - T)] = v[e];
   }
 }
 
