@@ -4,11 +4,13 @@
 //
 // One CTA owns one segment (a PE of Fig. 1).  Its compute warps hold the
 // segment plus one halo point per side in registers and step with no
-// asynchrony inside the CTA (Section 3).  One extra warp per CTA is the
-// "network": it publishes the segment's two edge values of every version to
-// global rings (release store of the segment's version counter) and copies
-// the neighbours' published versions into a ring in shared memory (the
-// buffer of Section 3 that keeps the q most recent values received).
+// asynchrony inside the CTA (Section 3).  Three extra warps per CTA are the
+// "network": one publishes the segment's two edge values of every version to
+// global rings (release store of the segment's version counter), one per
+// neighbour copies that neighbour's published versions into a ring in shared
+// memory (the buffer of Section 3 that keeps the q most recent values
+// received).  Separate warps let the publish fence and the two neighbours'
+// L2 round trips overlap.
 //
 // At step k a compute warp takes, from that local buffer, the newest
 // neighbour version v <= k; it waits only while v < k-q+1 (bounded delay,
@@ -79,27 +81,24 @@ __device__ __forceinline__ bool fetch_halo(const SegmentRun& a, const int* avail
   return true;
 }
 
-// The communication warp's loop (one thread).
+// The three communication warps (one thread each does the work).
+
+// Publisher: pushes every new version of the segment's two edge values to its
+// global rings, then release-stores the segment's version counter.
 template <typename real, int E>
-__device__ void comm_loop(const SegmentRun& a, AsyncShared<real, E>& sh, int s) {
-  const int R = a.R, S = a.S;
+__device__ void publish_loop(const SegmentRun& a, AsyncShared<real, E>& sh, int s) {
+  const int R = a.R;
   const int K = static_cast<int>(a.K);
   real* rings = static_cast<real*>(a.rings);
   real* my_l = rings + (static_cast<size_t>(s) * 2 + 0) * R;
   real* my_r = rings + (static_cast<size_t>(s) * 2 + 1) * R;
-  const real* nb_l = s > 0 ? rings + (static_cast<size_t>(s - 1) * 2 + 1) * R : nullptr;     // left nbr's right edge
-  const real* nb_r = s + 1 < S ? rings + (static_cast<size_t>(s + 1) * 2 + 0) * R : nullptr; // right nbr's left edge
   int* my_prog = a.prog + static_cast<size_t>(s) * kProgStride;
-  const int* lprog = s > 0 ? a.prog + static_cast<size_t>(s - 1) * kProgStride : nullptr;
-  const int* rprog = s + 1 < S ? a.prog + static_cast<size_t>(s + 1) * kProgStride : nullptr;
   const bool stalled = s == a.stall_segment;
-
-  int pub = -1, lseen = -1, rseen = -1;
+  const bool replay = a.trace_in != nullptr;
+  int pub = -1;
   uint64_t t_idle = global_timer_ns();
   unsigned spins = 0;
   while (true) {
-    bool busy = false;
-    // Publish the versions the compute warps have produced.
     const int w = min(ld_acquire_cta_shared(&sh.own_l_ver), ld_acquire_cta_shared(&sh.own_r_ver));
     if (!stalled && w > pub) {
       for (int x = max(pub + 1, w - R + 1); x <= w; ++x) {
@@ -109,32 +108,47 @@ __device__ void comm_loop(const SegmentRun& a, AsyncShared<real, E>& sh, int s) 
       }
       st_release_gpu(my_prog, w);
       pub = w;
-      busy = true;
-    }
-    // Pull the neighbours' new versions into the local buffers.
-    if (lprog) {
-      const int P = ld_acquire_gpu(lprog);
-      if (P > lseen) {
-        for (int x = max(lseen + 1, P - R + 1); x <= P; ++x) sh.lring[x & (R - 1)] = ld_cg(nb_l + (x & (R - 1)));
-        st_release_cta_shared(&sh.lavail, P);
-        lseen = P;
-        busy = true;
-      }
-    }
-    if (rprog) {
-      const int P = ld_acquire_gpu(rprog);
-      if (P > rseen) {
-        for (int x = max(rseen + 1, P - R + 1); x <= P; ++x) sh.rring[x & (R - 1)] = ld_cg(nb_r + (x & (R - 1)));
-        st_release_cta_shared(&sh.ravail, P);
-        rseen = P;
-        busy = true;
-      }
+      t_idle = global_timer_ns();
+      continue;
     }
     const int done = ld_acquire_cta_shared(&sh.compute_done);
     if (done == 2 || (done == 1 && (pub >= K || stalled))) break;
-    if (busy) {
+    // Back off between polls: a tight shared-memory spin takes issue and
+    // shared-memory slots from the compute warps.  A replay waits on exact
+    // versions, so its publisher naps less (measured on the 2^20-point rod:
+    // free runs are fastest at 256 ns, replays at 64 ns).
+    __nanosleep(replay ? 64 : 256);
+    if ((++spins & 63u) == 0) {
+      if (status_failed(a.status)) break;
+      if (static_cast<int64_t>(global_timer_ns() - t_idle) > a.spin_limit_ns) {
+        raise_status(a.status, HEAT1D_ERR_TIMEOUT);
+        break;
+      }
+    }
+  }
+}
+
+// Puller: copies each new version of one neighbour's facing edge value from
+// its global ring into the local ring, then release-stores the newest version
+// held (the buffer of Section 3 that keeps the most recent received values).
+template <typename real, int E>
+__device__ void pull_loop(const SegmentRun& a, AsyncShared<real, E>& sh, const int* nprog, const real* nring,
+                          real* lring, int* avail) {
+  const int R = a.R;
+  int seen = -1;
+  uint64_t t_idle = global_timer_ns();
+  unsigned spins = 0;
+  while (true) {
+    const int P = ld_acquire_gpu(nprog);
+    if (P > seen) {
+      for (int x = max(seen + 1, P - R + 1); x <= P; ++x) lring[x & (R - 1)] = ld_cg(nring + (x & (R - 1)));
+      st_release_cta_shared(avail, P);
+      seen = P;
       t_idle = global_timer_ns();
-    } else if ((++spins & 63u) == 0) {
+      continue;
+    }
+    if (ld_acquire_cta_shared(&sh.compute_done)) break;  // no more reads needed
+    if ((++spins & 63u) == 0) {
       if (status_failed(a.status)) break;
       if (static_cast<int64_t>(global_timer_ns() - t_idle) > a.spin_limit_ns) {
         raise_status(a.status, HEAT1D_ERR_TIMEOUT);
@@ -151,7 +165,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
   __shared__ AsyncShared<real, E> sh;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nwc = (blockDim.x >> 5) - 1;  // compute warps; the last warp communicates
+  const int nwc = (blockDim.x >> 5) - kCommWarps;  // compute warps; the last three communicate
   const unsigned nthreads_c = static_cast<unsigned>(nwc) * 32u;
   if (tid == 0) {
     sh.lavail = -1;
@@ -162,8 +176,21 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
   }
   __syncthreads();
 
-  if (warp == nwc) {
-    if (lane == 0) comm_loop<real, E>(a, sh, s);
+  if (warp >= nwc) {
+    if (lane == 0) {
+      real* rings = static_cast<real*>(a.rings);
+      if (warp == nwc) {
+        publish_loop<real, E>(a, sh, s);
+      } else if (warp == nwc + 1) {
+        if (s > 0)  // left neighbour's right edge
+          pull_loop<real, E>(a, sh, a.prog + static_cast<size_t>(s - 1) * kProgStride,
+                             rings + (static_cast<size_t>(s - 1) * 2 + 1) * a.R, sh.lring, &sh.lavail);
+      } else {
+        if (s + 1 < a.S)  // right neighbour's left edge
+          pull_loop<real, E>(a, sh, a.prog + static_cast<size_t>(s + 1) * kProgStride,
+                             rings + (static_cast<size_t>(s + 1) * 2 + 0) * a.R, sh.rring, &sh.ravail);
+      }
+    }
     return;
   }
 
@@ -297,7 +324,7 @@ int launch_async_t(const SegmentRun& a, int threads, cudaStream_t st) {
   SegmentRun args = a;
   void* params[] = {&args};
   cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(async_persistent_kernel<real, E>), dim3(a.S),
-                                              dim3(threads + 32), params, 0, st);
+                                              dim3(threads + 32 * kCommWarps), params, 0, st);
   if (e == cudaErrorCooperativeLaunchTooLarge) {
     cudaGetLastError();
     return HEAT1D_ERR_NOT_RESIDENT;
@@ -308,7 +335,7 @@ int launch_async_t(const SegmentRun& a, int threads, cudaStream_t st) {
 template <typename real, int E>
 int resident_t(int threads) {
   int per_sm = 0, dev = 0, nsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, async_persistent_kernel<real, E>, threads + 32, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, async_persistent_kernel<real, E>, threads + 32 * kCommWarps, 0) !=
       cudaSuccess)
     return 0;
   cudaGetDevice(&dev);

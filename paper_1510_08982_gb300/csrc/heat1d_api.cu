@@ -277,7 +277,7 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   if (K < 0 || K >= INT_MAX) return fail(HEAT1D_ERR_INVAL, "K out of range");
   if (K == 0) return HEAT1D_OK;
   int E = 0, threads = 0;
-  int rc = pick_shape(h, h->Lmax + 2, 32, true, &E, &threads);
+  int rc = pick_shape(h, h->Lmax + 2, 32 * heat1d_impl::kCommWarps, true, &E, &threads);
   if (rc) return rc;
   const size_t tbytes = static_cast<size_t>(K) * (h->S - 1) * 2;
   SegmentRun a = base_run(h, K);

@@ -10,6 +10,9 @@ namespace heat1d_impl {
 
 // Largest ring of the asynchronous run (versions kept per directed edge).
 constexpr int kMaxRing = 512;
+// Communication warps per CTA of the asynchronous kernel (publisher, left
+// puller, right puller).
+constexpr int kCommWarps = 3;
 // Padding, in ints, between the per-segment version counters (one 128-byte
 // line each, so that CTAs never share a line they write).
 constexpr int kProgStride = 32;
