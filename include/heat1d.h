@@ -150,6 +150,50 @@ int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_devi
  * HEAT1D_ERR_TIMEOUT or HEAT1D_ERR_TRACE (HEAT1D_ERR_CUDA on a CUDA error). */
 int heat1d_sync(heat1d_t h);
 
+/* ------------------------------------------------------------ batched rods
+ *
+ * Many independent rods of uneven N, r and K advanced by the synchronous
+ * update (Section 2, Eq. (eqn:sync)) in one persistent launch.  Rod j lives in
+ * u_packed[offset .. offset+N-1] (dtype of the batch; rods must not overlap)
+ * and is advanced K steps in place; when K > 0 its ends become c1 and cN.
+ * The result for each rod is identical, bit for bit, to heat1d_run_sync on
+ * that rod alone. */
+typedef struct heat1d_rod {
+  int64_t offset; /* first point of the rod in the packed state */
+  int64_t N;      /* points, >= 3 */
+  int64_t K;      /* steps, >= 0 */
+  double r;       /* 0 < r <= 0.5 */
+  double c1, cN;  /* Dirichlet ends */
+} heat1d_rod;
+
+typedef struct heat1d_batch* heat1d_batch_t;
+
+/* Plans a batch once: validates the rods, sorts the work (warp batches for
+ * rods of at most 32 * elems_per_thread points, one CTA for rods that fit a
+ * CTA, parts with halo_steps-deep halos for longer rods), uploads the plan
+ * and allocates its scratch.  Options used: elems_per_thread (4, 8, 16;
+ * default 16 in F32, 8 in F64), block_threads (default 256), halo_steps
+ * (default 32 in F32, 16 in F64), spin_limit_ns.  NULL on error. */
+heat1d_batch_t heat1d_batch_create(const heat1d_rod* rods, int64_t nrods, int dtype, const heat1d_opts* o);
+
+/* Enqueues one run of the planned batch on `stream` (device pointer
+ * u_packed).  Only memsets and one kernel launch: no allocation and no
+ * synchronisation, so the call can be captured in a CUDA graph. */
+int heat1d_batch_run(heat1d_batch_t b, void* u_packed, void* stream);
+
+/* Waits for the last run's stream; returns its device status. */
+int heat1d_batch_sync(heat1d_batch_t b);
+
+/* info[8]: warp batches, single-CTA rods, rod parts, CTAs, threads per CTA,
+ * elems_per_thread, halo_steps, points per CTA. */
+int heat1d_batch_describe(heat1d_batch_t b, int64_t* info);
+
+void heat1d_batch_destroy(heat1d_batch_t b);
+
+/* One-shot form: plan, run, wait, free.  u_packed is a device pointer. */
+int heat1d_run_batched(const heat1d_rod* rods, int64_t nrods, void* u_packed, int dtype, const heat1d_opts* o,
+                       void* stream);
+
 /* Synchronous run that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- for example
  * code running inside a host callback or an allocator hook, a plug-in that may

@@ -1,0 +1,274 @@
+// batched_kernels.cu -- many rods of uneven N, r and K in one persistent
+// cooperative launch (the synchronous update of Section 2, Eq. (eqn:sync),
+// applied to each rod independently).
+//
+// The host plans work items, each one CTA's worth, in an order of decreasing
+// work; every CTA takes the next item from a global counter until the queue
+// is empty.  Three kinds of item:
+//   - a warp batch: up to one small rod per warp (the rod fits one warp
+//     window of 32*E points); each warp runs its rod alone, registers and
+//     shuffles only, no synchronisation at all;
+//   - a whole rod in one CTA: the overlapping warp windows of common.cuh,
+//     one CTA barrier every H steps;
+//   - one part of a rod too long for one CTA: the rod is split into parts
+//     with T-wide overlapped halos; parts exchange their edge points through
+//     global memory every T steps and wait only for their two neighbouring
+//     parts (release/acquire pass counters, no grid barrier).
+// The parts of a rod are consecutive in the queue and a rod never has more
+// parts than there are CTAs, so every part a CTA waits for is already held
+// by another CTA or will be taken next: the launch cannot deadlock.  All
+// waits are bounded.  Results are bit-identical to stepping each rod alone.
+#include <algorithm>
+
+#include "common.cuh"
+#include "impl.h"
+
+namespace heat1d_impl {
+using namespace heat1d_dev;
+
+namespace {
+
+__device__ bool wait_flag_at_least(const int* flag, int want, int* status, int64_t limit_ns) {
+  if (ld_acquire_gpu(flag) >= want) return true;
+  const uint64_t t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (ld_acquire_gpu(flag) < want) {
+    if ((++spins & 31u) == 0) {
+      if (status_failed(status)) return false;
+      if (static_cast<int64_t>(global_timer_ns() - t0) > limit_ns) {
+        raise_status(status, HEAT1D_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// A small rod advanced by one warp: positions lane*E + e.
+template <typename real, int E>
+__device__ void run_warp_rod(const BatchRod& rd, real* u, int lane) {
+  real* x = u + rd.offset;
+  const int N = static_cast<int>(rd.N);
+  const real c1 = static_cast<real>(rd.c1), cN = static_cast<real>(rd.cN);
+  const Coef<real> coef{static_cast<real>(rd.r), static_cast<real>(rd.N > 0)};
+  real v[E];
+  unsigned fixed = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = lane * E + e;
+    real y = p < N ? x[p] : static_cast<real>(0);
+    if (p == 0) y = c1;
+    if (p == N - 1) y = cN;
+    v[e] = y;
+    if (p == 0 || p >= N - 1) fixed |= 1u << e;
+  }
+  const int mode = tile_mode<E>(fixed);
+  if (mode == kTileFree) {
+    for (int64_t k = 0; k < rd.K; ++k) warp_step<real, E, kTileFree>(v, fixed, coef);
+  } else if (mode == kTileMasked) {
+    for (int64_t k = 0; k < rd.K; ++k) warp_step<real, E, kTileMasked>(v, fixed, coef);
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = lane * E + e;
+    if (p < N) x[p] = v[e];
+  }
+}
+
+template <typename real, int E>
+__global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_kernel(BatchRun a) {
+  using Win = Window<E, sync_window_halo(sizeof(real), E)>;
+  __shared__ WindowShared<real, Win::H> sh;
+  __shared__ int sh_item;
+  __shared__ int sh_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  real* u = static_cast<real*>(a.u);
+  real* edges = static_cast<real*>(a.edges);
+  int parity = 0;
+
+  while (true) {
+    if (tid == 0) sh_item = static_cast<int>(atomicAdd(a.counter, 1u));
+    __syncthreads();
+    const int64_t idx = sh_item;
+    if (idx >= a.nitems) break;
+    const BatchItem it = a.items[idx];
+
+    if (it.kind == kBatchWarps) {
+      if (warp < it.count) run_warp_rod<real, E>(a.rods[a.warp_rods[it.rod + warp]], u, lane);
+    } else if (it.kind == kBatchRod) {
+      // The whole rod in this CTA; its ends are fixed, so nothing degrades.
+      const BatchRod rd = a.rods[it.rod];
+      real* x = u + rd.offset;
+      const int N = static_cast<int>(rd.N);
+      const real c1 = static_cast<real>(rd.c1), cN = static_cast<real>(rd.cN);
+      const Coef<real> coef{static_cast<real>(rd.r), static_cast<real>(rd.N > 0)};
+      real v[E];
+      unsigned fixed = 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        real y = p < N ? x[p] : static_cast<real>(0);
+        if (p == 0) y = c1;
+        if (p == N - 1) y = cN;
+        v[e] = y;
+        if (p == 0 || p >= N - 1) fixed |= 1u << e;
+      }
+      const int mode = tile_mode<E>(fixed);
+      for (int64_t k0 = 0; k0 < rd.K; k0 += (1 << 30)) {
+        const int steps = static_cast<int>(std::min<int64_t>(rd.K - k0, 1 << 30));
+        warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, steps);
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        if (p < N && Win::owner(warp, lane, e, nwarps)) x[p] = v[e];
+      }
+    } else {
+      // One part: positions [0, L+2T) hold rod points a0 - T + p.
+      const BatchRod rd = a.rods[it.rod];
+      real* x = u + rd.offset;
+      const int64_t N = rd.N;
+      const int T = it.T, L = it.L, Lh = L + 2 * T;
+      const int64_t a0 = it.a0;
+      const real c1 = static_cast<real>(rd.c1), cN = static_cast<real>(rd.cN);
+      const Coef<real> coef{static_cast<real>(rd.r), static_cast<real>(rd.N > 0)};
+      const size_t estride = static_cast<size_t>(4) * a.Tmax;
+      int* myflag = a.flags + it.slot;
+      real v[E];
+      unsigned fixed = 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        const int64_t g = a0 - T + p;
+        real y = static_cast<real>(0);
+        if (p < Lh && g >= 0 && g < N) y = x[g];
+        if (g == 0) y = c1;
+        if (g == N - 1) y = cN;
+        v[e] = y;
+        if (p >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
+      }
+      const int mode = tile_mode<E>(fixed);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release_gpu(myflag, 1);  // loaded: neighbours may now overwrite their own points
+      }
+      bool ok = true;
+      int epoch = 0;
+      for (int64_t k0 = 0; k0 < rd.K; k0 += T) {
+        const int tb = static_cast<int>(std::min<int64_t>(T, rd.K - k0));
+        warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
+        if (k0 + tb >= rd.K) break;
+        real* mine = edges + it.slot * estride + (epoch & 1) * 2 * a.Tmax;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int p = Win::pos(warp, lane, e);
+          if (!Win::owner(warp, lane, e, nwarps)) continue;
+          if (p >= T && p < 2 * T) st_cg(mine + (p - T), v[e]);
+          if (p >= L && p < L + T) st_cg(mine + a.Tmax + (p - L), v[e]);
+        }
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          st_release_gpu(myflag, epoch + 2);
+          bool w = true;
+          if (it.part > 0) w = wait_flag_at_least(myflag - 1, epoch + 2, a.status, a.spin_limit_ns);
+          if (w && it.part + 1 < it.nparts) w = wait_flag_at_least(myflag + 1, epoch + 2, a.status, a.spin_limit_ns);
+          sh_ok = w;
+        }
+        __syncthreads();
+        if (!sh_ok) {
+          ok = false;
+          break;
+        }
+        if (it.part > 0) {
+          const real* left = edges + (it.slot - 1) * estride + (epoch & 1) * 2 * a.Tmax;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int p = Win::pos(warp, lane, e);
+            if (p < T) v[e] = ld_cg(left + a.Tmax + p);
+          }
+        }
+        if (it.part + 1 < it.nparts) {
+          const real* right = edges + (it.slot + 1) * estride + (epoch & 1) * 2 * a.Tmax;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int p = Win::pos(warp, lane, e);
+            if (p >= L + T && p < Lh) v[e] = ld_cg(right + (p - L - T));
+          }
+        }
+        ++epoch;
+      }
+      if (!ok) return;  // CTA-uniform (sh_ok); the status word holds the failure
+      // The neighbours must have loaded their halos before our points change.
+      if (tid == 0) {
+        bool w = true;
+        if (it.part > 0) w = wait_flag_at_least(myflag - 1, 1, a.status, a.spin_limit_ns);
+        if (w && it.part + 1 < it.nparts) w = wait_flag_at_least(myflag + 1, 1, a.status, a.spin_limit_ns);
+        sh_ok = w;
+      }
+      __syncthreads();
+      if (!sh_ok) return;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) x[a0 - T + p] = v[e];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename real, int E>
+int launch_batched_t(const BatchRun& a, int threads, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, batched_kernel<real, E>, a);
+  if (e == cudaErrorCooperativeLaunchTooLarge) {
+    cudaGetLastError();
+    return HEAT1D_ERR_NOT_RESIDENT;
+  }
+  return e == cudaSuccess ? HEAT1D_OK : HEAT1D_ERR_CUDA;
+}
+
+template <typename real, int E>
+int resident_batched_t(int threads) {
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<real, E>, threads, 0) != cudaSuccess)
+    return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * nsm;
+}
+
+}  // namespace
+
+int launch_batched(const BatchRun& a, int dtype, int E, int threads, int grid, cudaStream_t st) {
+  const bool f64 = dtype == HEAT1D_F64;
+  switch (E) {
+    case 4: return f64 ? launch_batched_t<double, 4>(a, threads, grid, st) : launch_batched_t<float, 4>(a, threads, grid, st);
+    case 8: return f64 ? launch_batched_t<double, 8>(a, threads, grid, st) : launch_batched_t<float, 8>(a, threads, grid, st);
+    case 16: return f64 ? launch_batched_t<double, 16>(a, threads, grid, st) : launch_batched_t<float, 16>(a, threads, grid, st);
+    default: return HEAT1D_ERR_INVAL;
+  }
+}
+
+int max_resident_batched(int dtype, int E, int threads) {
+  const bool f64 = dtype == HEAT1D_F64;
+  switch (E) {
+    case 4: return f64 ? resident_batched_t<double, 4>(threads) : resident_batched_t<float, 4>(threads);
+    case 8: return f64 ? resident_batched_t<double, 8>(threads) : resident_batched_t<float, 8>(threads);
+    case 16: return f64 ? resident_batched_t<double, 16>(threads) : resident_batched_t<float, 16>(threads);
+    default: return 0;
+  }
+}
+
+}  // namespace heat1d_impl

@@ -488,3 +488,261 @@ int heat1d_sync(heat1d_t h) {
 }
 
 }  // extern "C"
+
+// ============================================================ batched rods
+
+struct heat1d_batch {
+  int dtype = HEAT1D_F64;
+  size_t esize = 8;
+  int E = 8, threads = 256, grid = 0, T = 16;
+  int64_t cap = 0;  // positions per CTA
+  int64_t spin_limit_ns = 2000000000LL;
+  int64_t nrods = 0, nitems = 0, nparts = 0, counts[3] = {0, 0, 0};
+  heat1d_impl::BatchRod* d_rods = nullptr;
+  int* d_warp_rods = nullptr;
+  heat1d_impl::BatchItem* d_items = nullptr;
+  void* d_ctl = nullptr;  // [0]: queue counter, [32]: status word
+  int* d_flags = nullptr;
+  void* d_edges = nullptr;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+void batch_free(heat1d_batch* b) {
+  cudaFree(b->d_rods);
+  cudaFree(b->d_warp_rods);
+  cudaFree(b->d_items);
+  cudaFree(b->d_ctl);
+  cudaFree(b->d_flags);
+  cudaFree(b->d_edges);
+}
+
+// Plans the work items: rods that fit one warp window go into warp batches
+// (grouped by K so that the warps of a batch finish together), rods that fit
+// one CTA become one item, longer rods are split into parts of at most
+// cap - 2T points.  Units are queued by decreasing work (points x steps);
+// the parts of a rod stay consecutive.
+int batch_plan(heat1d_batch* b, const heat1d_rod* rods, int64_t nrods, std::vector<heat1d_impl::BatchRod>& out_rods,
+               std::vector<int>& warp_rods, std::vector<heat1d_impl::BatchItem>& items) {
+  const int nwarps = b->threads / 32;
+  const int64_t warp_cap = 32LL * b->E;
+  struct Unit {
+    double work;
+    int kind;
+    int first, count;  // warp batch: range in warp_rods; else rod index
+  };
+  std::vector<Unit> units;
+  std::vector<int> small;
+  out_rods.resize(nrods);
+  for (int64_t j = 0; j < nrods; ++j) {
+    const heat1d_rod& r = rods[j];
+    if (r.N < 3 || r.K < 0 || r.offset < 0 || !(r.r > 0.0 && r.r <= 0.5))
+      return fail(HEAT1D_ERR_INVAL, "batched rods: rod " + std::to_string(j) +
+                                        " needs N >= 3, K >= 0, offset >= 0 and 0 < r <= 0.5");
+    out_rods[j] = heat1d_impl::BatchRod{r.offset, r.N, r.K, r.r, r.c1, r.cN};
+    if (r.K == 0) continue;
+    if (r.N <= warp_cap) {
+      small.push_back(static_cast<int>(j));
+    } else if (r.N <= b->cap) {
+      units.push_back(Unit{static_cast<double>(r.N) * r.K, heat1d_impl::kBatchRod, static_cast<int>(j), 1});
+    } else {
+      units.push_back(Unit{static_cast<double>(r.N) * r.K, heat1d_impl::kBatchPart, static_cast<int>(j), 1});
+    }
+  }
+  std::stable_sort(small.begin(), small.end(), [&](int x, int y) { return rods[x].K > rods[y].K; });
+  for (size_t i = 0; i < small.size(); i += nwarps) {
+    const int cnt = static_cast<int>(std::min<size_t>(nwarps, small.size() - i));
+    double work = 0;
+    for (int w = 0; w < cnt; ++w) work += static_cast<double>(rods[small[i + w]].N) * rods[small[i]].K;
+    units.push_back(Unit{work, heat1d_impl::kBatchWarps, static_cast<int>(warp_rods.size()), cnt});
+    for (int w = 0; w < cnt; ++w) warp_rods.push_back(small[i + w]);
+  }
+  std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.work > y.work; });
+  int slot = 0;
+  for (const Unit& un : units) {
+    heat1d_impl::BatchItem it{};
+    it.kind = un.kind;
+    it.rod = un.first;
+    it.count = un.count;
+    if (un.kind != heat1d_impl::kBatchPart) {
+      items.push_back(it);
+      b->counts[un.kind] += 1;
+      continue;
+    }
+    const heat1d_rod& r = rods[un.first];
+    const int64_t per = b->cap - 2 * b->T;
+    const int64_t P = (r.N + per - 1) / per;
+    if (P > b->grid)
+      return fail(HEAT1D_ERR_INVAL, "batched rods: rod " + std::to_string(un.first) + " needs " + std::to_string(P) +
+                                        " CTAs at once, more than can be resident");
+    const int64_t base = r.N / P, extra = r.N % P;
+    if (base < b->T) return fail(HEAT1D_ERR_INVAL, "batched rods: parts shorter than the halo depth");
+    int64_t pos = 0;
+    for (int64_t p = 0; p < P; ++p) {
+      const int64_t L = base + (p < extra ? 1 : 0);
+      it.part = static_cast<int>(p);
+      it.nparts = static_cast<int>(P);
+      it.T = b->T;
+      it.L = static_cast<int>(L);
+      it.slot = slot++;
+      it.a0 = pos;
+      pos += L;
+      items.push_back(it);
+      b->counts[heat1d_impl::kBatchPart] += 1;
+    }
+  }
+  b->nparts = slot;
+  return HEAT1D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+heat1d_batch_t heat1d_batch_create(const heat1d_rod* rods, int64_t nrods, int dtype, const heat1d_opts* o) {
+  if ((!rods && nrods > 0) || nrods < 0) {
+    fail(HEAT1D_ERR_INVAL, "heat1d_batch_create: bad rod array");
+    return nullptr;
+  }
+  if (dtype != HEAT1D_F32 && dtype != HEAT1D_F64) {
+    fail(HEAT1D_ERR_INVAL, "heat1d_batch_create: dtype must be HEAT1D_F32 or HEAT1D_F64");
+    return nullptr;
+  }
+  heat1d_opts opts;
+  heat1d_default_opts(&opts);
+  if (o) opts = *o;
+  heat1d_batch* b = new heat1d_batch();
+  b->dtype = dtype;
+  b->esize = dtype == HEAT1D_F64 ? 8 : 4;
+  b->E = opts.elems_per_thread ? opts.elems_per_thread : (dtype == HEAT1D_F64 ? 8 : 16);
+  b->threads = opts.block_threads ? opts.block_threads : 256;
+  b->T = opts.halo_steps ? opts.halo_steps : (dtype == HEAT1D_F64 ? 16 : 32);
+  if (opts.spin_limit_ns > 0) b->spin_limit_ns = opts.spin_limit_ns;
+  if ((b->E != 4 && b->E != 8 && b->E != 16) || b->threads % 32 != 0 || b->threads < 32 ||
+      b->threads > heat1d_impl::max_tile_threads(static_cast<int>(b->esize), b->E) || b->T < 1) {
+    fail(HEAT1D_ERR_INVAL, "heat1d_batch_create: elems_per_thread must be 4, 8 or 16 and block_threads a multiple "
+                           "of 32 within the CTA limit");
+    delete b;
+    return nullptr;
+  }
+  b->cap = heat1d_impl::window_width(b->threads / 32, b->E,
+                                     heat1d_impl::sync_window_halo(static_cast<int>(b->esize), b->E));
+  if (b->cap - 2 * b->T < b->T) {
+    fail(HEAT1D_ERR_INVAL, "heat1d_batch_create: halo_steps too large for the CTA");
+    delete b;
+    return nullptr;
+  }
+  b->grid = heat1d_impl::max_resident_batched(dtype, b->E, b->threads);
+  if (b->grid <= 0) {
+    fail(HEAT1D_ERR_NOT_RESIDENT, "heat1d_batch_create: batched kernel cannot be resident");
+    delete b;
+    return nullptr;
+  }
+  std::vector<heat1d_impl::BatchRod> drods;
+  std::vector<int> warp_rods;
+  std::vector<heat1d_impl::BatchItem> items;
+  if (batch_plan(b, rods, nrods, drods, warp_rods, items) != HEAT1D_OK) {
+    delete b;
+    return nullptr;
+  }
+  b->nrods = nrods;
+  b->nitems = static_cast<int64_t>(items.size());
+  b->grid = static_cast<int>(std::min<int64_t>(b->grid, std::max<int64_t>(b->nitems, 1)));
+  // a rod's parts must all be resident at once
+  for (const auto& it : items)
+    if (it.kind == heat1d_impl::kBatchPart && it.nparts > b->grid) b->grid = it.nparts;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t n) {
+    if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(n, 16));
+  };
+  alloc(reinterpret_cast<void**>(&b->d_rods), sizeof(heat1d_impl::BatchRod) * drods.size());
+  alloc(reinterpret_cast<void**>(&b->d_warp_rods), sizeof(int) * warp_rods.size());
+  alloc(reinterpret_cast<void**>(&b->d_items), sizeof(heat1d_impl::BatchItem) * items.size());
+  alloc(&b->d_ctl, 256);
+  alloc(reinterpret_cast<void**>(&b->d_flags), sizeof(int) * b->nparts);
+  alloc(&b->d_edges, b->esize * 4 * b->T * std::max<int64_t>(b->nparts, 1));
+  if (e == cudaSuccess && !drods.empty())
+    e = cudaMemcpy(b->d_rods, drods.data(), sizeof(heat1d_impl::BatchRod) * drods.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !warp_rods.empty())
+    e = cudaMemcpy(b->d_warp_rods, warp_rods.data(), sizeof(int) * warp_rods.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(b->d_items, items.data(), sizeof(heat1d_impl::BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_ctl, 0, 256);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "heat1d_batch_create");
+    batch_free(b);
+    delete b;
+    return nullptr;
+  }
+  return b;
+}
+
+int heat1d_batch_run(heat1d_batch_t b, void* u_packed, void* stream) {
+  if (!b || !u_packed) return fail(HEAT1D_ERR_INVAL, "heat1d_batch_run: null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  b->last_stream = st;
+  if (b->nitems == 0) return HEAT1D_OK;
+  heat1d_impl::BatchRun a{};
+  a.rods = b->d_rods;
+  a.warp_rods = b->d_warp_rods;
+  a.items = b->d_items;
+  a.nitems = b->nitems;
+  a.u = u_packed;
+  a.counter = static_cast<unsigned*>(b->d_ctl);
+  a.flags = b->d_flags;
+  a.edges = b->d_edges;
+  a.Tmax = b->T;
+  a.status = static_cast<int*>(b->d_ctl) + 32;
+  a.spin_limit_ns = b->spin_limit_ns;
+  HEAT1D_CUDA(cudaMemsetAsync(b->d_ctl, 0, sizeof(unsigned), st));
+  if (b->nparts > 0) HEAT1D_CUDA(cudaMemsetAsync(b->d_flags, 0, sizeof(int) * b->nparts, st));
+  int rc = heat1d_impl::launch_batched(a, b->dtype, b->E, b->threads, b->grid, st);
+  if (rc == HEAT1D_ERR_NOT_RESIDENT) return fail(rc, "heat1d_batch_run: grid cannot be resident");
+  if (rc) return cuda_fail(cudaGetLastError(), "launch_batched");
+  return HEAT1D_OK;
+}
+
+int heat1d_batch_sync(heat1d_batch_t b) {
+  if (!b) return fail(HEAT1D_ERR_INVAL, "null batch");
+  HEAT1D_CUDA(cudaStreamSynchronize(b->last_stream));
+  int st = 0;
+  HEAT1D_CUDA(cudaMemcpy(&st, static_cast<int*>(b->d_ctl) + 32, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    HEAT1D_CUDA(cudaMemset(static_cast<int*>(b->d_ctl) + 32, 0, sizeof(int)));
+    return fail(st, st == HEAT1D_ERR_TIMEOUT ? "a device-side wait exceeded spin_limit_ns"
+                                             : "device status " + std::to_string(st));
+  }
+  return HEAT1D_OK;
+}
+
+int heat1d_batch_describe(heat1d_batch_t b, int64_t* info) {
+  if (!b || !info) return fail(HEAT1D_ERR_INVAL, "null argument");
+  info[0] = b->counts[heat1d_impl::kBatchWarps];
+  info[1] = b->counts[heat1d_impl::kBatchRod];
+  info[2] = b->counts[heat1d_impl::kBatchPart];
+  info[3] = b->grid;
+  info[4] = b->threads;
+  info[5] = b->E;
+  info[6] = b->T;
+  info[7] = b->cap;
+  return HEAT1D_OK;
+}
+
+void heat1d_batch_destroy(heat1d_batch_t b) {
+  if (!b) return;
+  batch_free(b);
+  delete b;
+}
+
+int heat1d_run_batched(const heat1d_rod* rods, int64_t nrods, void* u_packed, int dtype, const heat1d_opts* o,
+                       void* stream) {
+  heat1d_batch_t b = heat1d_batch_create(rods, nrods, dtype, o);
+  if (!b) return g_last_error.find("resident") != std::string::npos ? HEAT1D_ERR_NOT_RESIDENT : HEAT1D_ERR_INVAL;
+  int rc = heat1d_batch_run(b, u_packed, stream);
+  if (rc == HEAT1D_OK) rc = heat1d_batch_sync(b);
+  heat1d_batch_destroy(b);
+  return rc;
+}
+
+}  // extern "C"

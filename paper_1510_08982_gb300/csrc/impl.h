@@ -94,6 +94,49 @@ void set_last_error(const std::string& msg);
 int launch_stream(const StreamRun& a, int dtype, int E, int threads, int grid, cudaStream_t st);
 int max_resident_stream(int dtype, int E, int threads);
 
+// ------------------------------------------------------------ batched rods
+
+// One rod of a batch as the kernels see it.
+struct BatchRod {
+  int64_t offset;  // first point in the packed state
+  int64_t N;
+  int64_t K;
+  double r, c1, cN;
+};
+
+// One work item: what one CTA does between two grabs from the queue.
+enum BatchKind { kBatchWarps = 0, kBatchRod = 1, kBatchPart = 2 };
+struct BatchItem {
+  int kind;    // BatchKind
+  int rod;     // kBatchWarps: first entry in warp_rods; else the rod
+  int count;   // kBatchWarps: rods in the batch (one per warp)
+  int part;    // kBatchPart: index of the part in the rod, and of its parts
+  int nparts;
+  int T;       // kBatchPart: halo depth = steps between exchanges
+  int L;       // kBatchPart: points of the part
+  int slot;    // kBatchPart: index of the part's flag and edge buffers
+  int64_t a0;  // kBatchPart: first point of the part (rod-relative)
+};
+
+struct BatchRun {
+  const BatchRod* rods;
+  const int* warp_rods;   // rods of the warp batches, in batch order
+  const BatchItem* items;
+  int64_t nitems;
+  void* u;                // packed state, updated in place
+  unsigned* counter;      // queue position, zero at launch
+  int* flags;             // per part: 1 after loading, e+2 after publishing epoch e; zero at launch
+  void* edges;            // per part: [2 parities][2][Tmax] values
+  int Tmax;
+  int* status;
+  int64_t spin_limit_ns;
+};
+
+// Batched launch: `grid` CTAs (all resident) of `threads` threads, E points
+// per thread (4, 8 or 16).
+int launch_batched(const BatchRun& a, int dtype, int E, int threads, int grid, cudaStream_t st);
+int max_resident_batched(int dtype, int E, int threads);
+
 // Largest number of CTAs of these kernels that can be resident at once.
 int max_resident_sync(int dtype, int E, int threads);
 int max_resident_async(int dtype, int E, int threads);

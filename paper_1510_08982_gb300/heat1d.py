@@ -28,7 +28,8 @@ STATUS_NAMES = {OK: "HEAT1D_OK", ERR_INVAL: "HEAT1D_ERR_INVAL", ERR_CUDA: "HEAT1
 EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_last_error", "heat1d_set_stream",
            "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
            "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync",
-           "heat1d_run_sync_noalloc"]
+           "heat1d_batch_create", "heat1d_batch_run", "heat1d_batch_sync", "heat1d_batch_describe",
+           "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_run_sync_noalloc"]
 
 
 class Heat1dError(RuntimeError):
@@ -42,6 +43,12 @@ class Opts(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("elems_per_thread", ctypes.c_int32),
                 ("spin_limit_ns", ctypes.c_int64), ("stall_segment", ctypes.c_int32),
                 ("sync_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class RodSpec(ctypes.Structure):
+    """heat1d_rod: one rod of a batch (offset into the packed state, N, K, r, c1, cN)."""
+    _fields_ = [("offset", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64), ("r", ctypes.c_double),
+                ("c1", ctypes.c_double), ("cN", ctypes.c_double)]
 
 
 _lib = None
@@ -74,6 +81,12 @@ def load():
         "heat1d_replay": (i32, [vp, i64, vp, i32]),
         "heat1d_sync": (i32, [vp]),
         "heat1d_run_sync_noalloc": (i32, [vp, vp, i64, dbl, dbl, dbl, i32, i64, i64, vp, vp]),
+        "heat1d_batch_create": (vp, [ctypes.POINTER(RodSpec), i64, i32, ctypes.POINTER(Opts)]),
+        "heat1d_batch_run": (i32, [vp, vp, vp]),
+        "heat1d_batch_sync": (i32, [vp]),
+        "heat1d_batch_describe": (i32, [vp, vp]),
+        "heat1d_batch_destroy": (None, [vp]),
+        "heat1d_run_batched": (i32, [ctypes.POINTER(RodSpec), i64, vp, i32, ctypes.POINTER(Opts), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -272,3 +285,95 @@ def run_sync_noalloc(u_in, u_out, r, c1, cN, K, segments=0, status_out=None):
     _check(lib.heat1d_run_sync_noalloc(ctypes.c_void_p(u_in.data_ptr()), ctypes.c_void_p(u_out.data_ptr()),
                                        u_in.numel(), float(r), float(c1), float(cN), _dtype_code(u_in.dtype),
                                        int(K), int(segments), st, sp))
+
+
+# ---------------------------------------------------------------------------- batched rods
+
+
+def pack_offsets(Ns):
+    """Offsets of rods of lengths Ns laid out back to back (int64 array) and
+    the total length."""
+    Ns = np.asarray(Ns, dtype=np.int64)
+    off = np.zeros(Ns.size, dtype=np.int64)
+    if Ns.size:
+        off[1:] = np.cumsum(Ns)[:-1]
+    return off, int(Ns.sum())
+
+
+def _rod_array(specs):
+    arr = (RodSpec * len(specs))()
+    for i, sp in enumerate(specs):
+        off, N, K, r, c1, cN = sp
+        arr[i] = RodSpec(int(off), int(N), int(K), float(r), float(c1), float(cN))
+    return arr
+
+
+def _opts(kw):
+    o = default_opts()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError("unknown option %r" % k)
+        setattr(o, k, int(v))
+    return o
+
+
+class Batch:
+    """A planned batch of rods (heat1d_batch_*).  specs: sequence of
+    (offset, N, K, r, c1, cN).  run(u) advances every rod in the packed CUDA
+    tensor u in place on the current stream (capturable in a CUDA graph)."""
+
+    def __init__(self, specs, dtype="float64", **opts):
+        self.lib = load()
+        self.code = _dtype_code(dtype)
+        arr = _rod_array(specs)
+        o = _opts(opts)
+        b = self.lib.heat1d_batch_create(arr, len(specs), self.code, ctypes.byref(o))
+        if not b:
+            raise Heat1dError(ERR_INVAL, last_error())
+        self.b = ctypes.c_void_p(b)
+
+    def run(self, u):
+        torch = _torch()
+        if not u.is_cuda or not u.is_contiguous():
+            raise ValueError("u must be a contiguous CUDA tensor")
+        if _dtype_code(u.dtype) != self.code:
+            raise ValueError("u has the wrong dtype for this batch")
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        _check(self.lib.heat1d_batch_run(self.b, ctypes.c_void_p(u.data_ptr()), st))
+
+    def sync(self):
+        _check(self.lib.heat1d_batch_sync(self.b))
+
+    def describe(self) -> dict:
+        info = np.zeros(8, dtype=np.int64)
+        _check(self.lib.heat1d_batch_describe(self.b, info.ctypes.data_as(ctypes.c_void_p)))
+        keys = ["warp_batches", "cta_rods", "rod_parts", "ctas", "threads", "elems_per_thread", "halo_steps",
+                "points_per_cta"]
+        return dict(zip(keys, (int(x) for x in info)))
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.heat1d_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def run_batched(specs, u, dtype="float64", **opts):
+    """heat1d_run_batched: plan, run on the current stream, wait, free."""
+    torch = _torch()
+    arr = _rod_array(specs)
+    o = _opts(opts)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(load().heat1d_run_batched(arr, len(specs), ctypes.c_void_p(u.data_ptr()), _dtype_code(dtype),
+                                     ctypes.byref(o), st))
