@@ -56,6 +56,11 @@ def parse():
     p.add_argument("--K", type=int, default=K_DEFAULT)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="sine-mode-rod", choices=["sine-mode-rod", "streamed-rod", "uneven-rods"],
+                   help="sine-mode-rod (default): the sync vs async rod; streamed-rod: the 2^26-point "
+                        "temporal-blocking rod; uneven-rods: 4096 rods in one batched launch")
+    p.add_argument("--dtype", default=None, choices=["f32", "f64"], help="streamed-rod / uneven-rods precision")
+    p.add_argument("--halo", type=int, default=0, help="streamed-rod: steps per HBM pass (T)")
     return p.parse_args()
 
 
@@ -185,10 +190,194 @@ def workload_config(args, S):
             "l2": "flushed between timed steps (256 MB write); the rod itself stays on-chip for the whole run"}
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def _device_setup():
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1510_08982_gb300 import build
+    build.build()
+    return torch, rank, world, local
+
+
+def _max_over_ranks(torch, world, x, dev):
+    if world > 1:
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def run_streamed(args):
+    """The 2^26-point rod (c1 = cN = 0, u(0) ~ U[0,1), r = 0.25, K = 1e4)
+    advanced by the streamed synchronous run, T steps per HBM pass."""
+    torch, rank, world, local = _device_setup()
+    from paper_1510_08982_gb300 import heat1d, inputs
+    dev = torch.device("cuda", local)
+    dt = args.dtype or "f32"
+    esz = 4 if dt == "f32" else 8
+    K = args.K if args.K != K_DEFAULT else 10_000
+    N = args.N if args.N != N_DEFAULT else 1 << 26
+    T = args.halo or (64 if dt == "f32" else 32)
+    tdt = torch.float32 if dt == "f32" else torch.float64
+    g = torch.Generator(device=dev).manual_seed(1000 + rank)
+    u0 = torch.rand(N, dtype=tdt, device=dev, generator=g)
+    h = heat1d.Heat1d(N, 0.25, 0.0, 0.0, dtype="float32" if dt == "f32" else "float64", sync_mode=2, halo_steps=T)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        h.set_u(u0)
+        h.run_sync(K)
+    h.sync()
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    total = 0.0
+    for _ in range(args.steps):
+        h.set_u(u0)  # 2*N*esz bytes > L2: the rod itself flushes L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.run_sync(K)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    h.sync()
+    total = _max_over_ranks(torch, world, total, dev)
+    ms = total / args.steps
+    ups = world * (N - 2) * K / (ms * 1e-3)
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alg_bytes = 2.0 * esz * N * (K / T)  # each pass reads and writes the rod once
+    achieved_gbs = alg_bytes / (ms * 1e-3) / 1e9
+    # ALU roofline: FP32 128 FMA-pipe lanes/clk/SM, FP64 1.25 TFLOP/s nominal (2 per SM per clk); 3 ops per update
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_ups = (nsm * 128 * 2.07e9 if dt == "f32" else FP64_NOMINAL_TFLOPS * 1e12 / 2) / 3
+    hbm_ups = hbm * 1e9 / (2.0 * esz / T)
+    bound = "hbm" if hbm_ups < alu_ups else "alu"
+    roof = ({"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm}
+            if bound == "hbm" else
+            {"bound": "alu", "achieved": ups / 1e9, "peak": alu_ups / 1e9, "unit": "Gupdates/s",
+             "frac": ups / alu_ups})
+    roof.update({"kernel": "stream_kernel", "peak_source": src, "traffic": None,
+                 "hbm_roofline_updates_per_s": hbm_ups, "alu_roofline_updates_per_s": alu_ups,
+                 "algorithmic_bytes_per_update": 2.0 * esz / T, "achieved_algorithmic_GBs": achieved_gbs})
+    line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dt, "data": "synthetic",
+            "config": {"workload": "streamed rod: N=%d %s, r=0.25, c1=cN=0, u(0)~U[0,1), K=%d, T=%d steps per "
+                                   "HBM pass" % (N, dt.upper(), K, T), "N": N, "K": K, "T": T,
+                       "l2": "inputs larger than L2 (%d MB state)" % (N * esz >> 20)},
+            "roofline": roof, "clocks": clk, "gpu_launches": 2 * args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
+def run_uneven(args):
+    """4096 uneven rods in one batched persistent launch, replayed from a CUDA graph."""
+    torch, rank, world, local = _device_setup()
+    from paper_1510_08982_gb300 import heat1d, inputs
+    dev = torch.device("cuda", local)
+    dt = args.dtype or "f32"
+    esz = 4 if dt == "f32" else 8
+    tdt = torch.float32 if dt == "f32" else torch.float64
+    rods = inputs.uneven_rods(seed=1000 + rank)
+    off, total_n = heat1d.pack_offsets([r.N for r in rods])
+    host = np.zeros(total_n)
+    for o, r in zip(off, rods):
+        host[o:o + r.N] = r.u0
+    u0 = torch.tensor(host, dtype=tdt, device=dev)
+    u = u0.clone()
+    specs = [(int(o), r.N, r.K, r.r, r.c1, r.cN) for o, r in zip(off, rods)]
+    b = heat1d.Batch(specs, dtype="float32" if dt == "f32" else "float64")
+    info = b.describe()
+    updates = sum((r.N - 2) * r.K for r in rods)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            b.run(u)
+    torch.cuda.current_stream().wait_stream(s)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        u.copy_(u0)
+        graph.replay()
+    torch.cuda.synchronize()
+    b.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    total = 0.0
+    for _ in range(args.steps):
+        u.copy_(u0)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    b.sync()
+    total = _max_over_ranks(torch, world, total, dev)
+    ms = total / args.steps
+    ups = world * updates / (ms * 1e-3)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_ups = (nsm * 128 * 2.07e9 if dt == "f32" else FP64_NOMINAL_TFLOPS * 1e12 / 2) / 3
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(total_n, dtype=tdt).pin_memory()
+        pinned.copy_(torch.tensor(host, dtype=tdt))
+        out = torch.empty_like(pinned).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            u.copy_(pinned, non_blocking=True)
+            b.run(u)
+            out.copy_(u, non_blocking=True)
+            torch.cuda.synchronize()
+        dt_e2e = (time.perf_counter() - t0) / args.steps
+        b.sync()
+        e2e = {"value": world * updates / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": total_n * esz,
+               "d2h_bytes_per_step": total_n * esz, "path": "pinned host -> device, heat1d_batch_run, device -> host"}
+    line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dt, "data": "synthetic",
+            "config": {"workload": "uneven rods: 4096 rods, N log-U[256,65536], K log-U[1e3,1e5], r U[0.05,0.5], "
+                                   "8 sine modes; one batched persistent launch replayed from a CUDA graph",
+                       "rods": len(rods), "points": total_n, "updates": updates, "plan": info,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": {"bound": "alu", "kernel": "batched_kernel", "achieved": ups / 1e9, "peak": alu_ups / 1e9,
+                         "unit": "Gupdates/s", "frac": ups / alu_ups, "traffic": None},
+            "clocks": clk, "e2e": e2e, "gpu_launches": args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "streamed-rod":
+        return run_streamed(args)
+    if args.workload == "uneven-rods":
+        return run_uneven(args)
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)

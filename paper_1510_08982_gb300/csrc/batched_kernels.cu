@@ -64,9 +64,9 @@ __device__ void run_warp_rod(const BatchRod& rd, real* u, int lane) {
   }
   const int mode = tile_mode<E>(fixed);
   if (mode == kTileFree) {
-    for (int64_t k = 0; k < rd.K; ++k) warp_step<real, E, kTileFree>(v, fixed, coef);
+    warp_steps<real, E, kTileFree>(v, fixed, coef, rd.K);
   } else if (mode == kTileMasked) {
-    for (int64_t k = 0; k < rd.K; ++k) warp_step<real, E, kTileMasked>(v, fixed, coef);
+    warp_steps<real, E, kTileMasked>(v, fixed, coef, rd.K);
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) {

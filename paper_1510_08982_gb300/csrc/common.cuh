@@ -208,6 +208,41 @@ __device__ __forceinline__ void warp_step(real (&v)[E], unsigned fixed, Coef<rea
   }
 }
 
+// The same step from `in` to `out` (separate registers).
+template <typename real, int E, int kMode>
+__device__ __forceinline__ void warp_step_to(const real (&in)[E], real (&out)[E], unsigned fixed, Coef<real> c) {
+  const real left = __shfl_up_sync(kFullMask, in[E - 1], 1);
+  const real right = __shfl_down_sync(kFullMask, in[0], 1);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const real prev = e > 0 ? in[e - 1] : left;
+    const real nxt = (e + 1 < E) ? in[e + 1] : right;
+    const real nv = ftcs(c.r, c.one, prev, in[e], nxt);
+    if (kMode == kTileMasked) {
+      out[e] = ((fixed >> e) & 1u) ? in[e] : nv;
+    } else {
+      out[e] = nv;
+    }
+  }
+}
+
+// n steps of one warp, two at a time between two register arrays, so that
+// the loop carries no register moves.
+template <typename real, int E, int kMode>
+__device__ __forceinline__ void warp_steps(real (&v)[E], unsigned fixed, Coef<real> c, int64_t n) {
+  if (kMode == kTileIdle) {
+    for (int64_t j = 0; j < n; ++j) warp_step<real, E, kTileIdle>(v, fixed, c);
+    return;
+  }
+  real w[E];
+  int64_t j = 0;
+  for (; j + 1 < n; j += 2) {
+    warp_step_to<real, E, kMode>(v, w, fixed, c);
+    warp_step_to<real, E, kMode>(w, v, fixed, c);
+  }
+  if (j < n) warp_step<real, E, kMode>(v, fixed, c);
+}
+
 template <typename real, int E>
 __device__ __forceinline__ void warp_step_any(int mode, real (&v)[E], unsigned fixed, Coef<real> c) {
   if (mode == kTileFree)
@@ -254,9 +289,9 @@ __device__ __forceinline__ void warp_advance(int mode, real (&v)[E], unsigned fi
   for (int done = 0; done < steps;) {
     const int n = min(H, steps - done);
     if (mode == kTileFree) {
-      for (int j = 0; j < n; ++j) warp_step<real, E, kTileFree>(v, fixed, c);
+      warp_steps<real, E, kTileFree>(v, fixed, c, n);
     } else if (mode == kTileMasked) {
-      for (int j = 0; j < n; ++j) warp_step<real, E, kTileMasked>(v, fixed, c);
+      warp_steps<real, E, kTileMasked>(v, fixed, c, n);
     }
     warp_refresh<real, E, H>(v, sh, parity, warp, lane, nwarps, nthreads, false);
     parity ^= 1;
