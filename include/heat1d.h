@@ -194,6 +194,50 @@ void heat1d_batch_destroy(heat1d_batch_t b);
 int heat1d_run_batched(const heat1d_rod* rods, int64_t nrods, void* u_packed, int dtype, const heat1d_opts* o,
                        void* stream);
 
+/* ------------------------------------------------------------ adjoint
+ *
+ * Gradient of the terminal misfit L = 0.5 * sum_i (u_i(K) - u_obs_i)^2 with
+ * respect to u(0) and r.  The paper does not differentiate its scheme; the
+ * adjoint here is derived from Section 3, Eq. (eqn:async) (Section 2's
+ * Eq. (eqn:sync) when trace is NULL): lambda(K) = u(K) - u_obs on the
+ * interior, then backwards lambda_i(k) += (1-2r) lambda_i(k+1) and
+ * lambda_{i+-1}(k - d) += r lambda_i(k+1) for every read u_{i+-1}(k - d) the
+ * forward step made, and dL/dr = sum_k sum_i lambda_i(k+1) *
+ * ((u_{i+1}(k-dR) - 2 u_i(k)) + u_{i-1}(k-dL)).  The gradient at the two
+ * Dirichlet entries of u(0) is 0.
+ *
+ * The forward pass keeps a checkpoint every ckpt_every steps (0: 128): the
+ * state plus the last q values of every point next to a segment boundary.
+ * The backward pass recomputes each interval from its checkpoint and marches
+ * lambda back through it.  lambda and every reduction are FP64 (the forward
+ * states are in the handle's dtype); reductions are deterministic.  Scratch
+ * (checkpoints, one interval of states) is allocated per call and freed;
+ * HEAT1D_ERR_OOM if it does not fit.  The call waits for the stream.
+ */
+
+/* On the handle: u(0) is the current state; afterwards the state is u(K).
+ * trace: NULL for the synchronous run, else the replayed asynchronous run's
+ * delays (layout above; host or device per trace_on_device; every entry must
+ * be < q, else HEAT1D_ERR_TRACE).  u_obs and grad_u0 are device arrays of N
+ * doubles; grad_r and loss are host doubles (may be NULL). */
+int heat1d_adjoint(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device, const double* u_obs,
+                   int64_t ckpt_every, double* grad_u0, double* grad_r, double* loss);
+
+/* Vector-Jacobian product of the same map u(0), r -> u(K): grad_uK (device,
+ * N doubles) is dL/du(K) for any L; returns dL/du(0) and dL/dr. */
+int heat1d_vjp(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device, const double* grad_uK,
+               int64_t ckpt_every, double* grad_u0, double* grad_r);
+
+/* The same for nrods rods of equal N and K packed rod-major in device arrays
+ * (u0 and uK of `dtype`, u_obs and grad_u0 of doubles, nrods*N values each;
+ * uK may be NULL).  r, c1, cN, grad_r and loss are host arrays of nrods.
+ * cotangent = 1 makes u_obs the cotangent dL/du(K) (loss then 0).  trace
+ * (device, [rod][K][S-1][2], or NULL) with S = segments and q. */
+int heat1d_adjoint_batched(int64_t nrods, int64_t N, int64_t K, const double* r, const double* c1, const double* cN,
+                           int dtype, const void* u0, const double* u_obs, int cotangent, int64_t segments, int q,
+                           const uint8_t* trace, int64_t ckpt_every, void* uK, double* grad_u0, double* grad_r,
+                           double* loss, void* stream);
+
 /* Synchronous run that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- for example
  * code running inside a host callback or an allocator hook, a plug-in that may

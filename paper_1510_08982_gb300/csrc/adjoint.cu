@@ -1,0 +1,420 @@
+// adjoint.cu -- gradient of the terminal misfit L = 0.5 ||u(K) - u_obs||^2
+// with respect to u(0) and r, for the synchronous run (Section 2, Eq.
+// (eqn:sync)) and for a replayed asynchronous run (Section 3, Eq.
+// (eqn:async) driven by a recorded delay trace).
+//
+// Forward, per interior point and step (mathematically):
+//   u_i(k+1) = (1-2r) u_i(k) + r u_{i+1}(k - dR) + r u_{i-1}(k - dL)
+// where dR, dL are the trace's delays on reads that cross a segment boundary
+// (0 elsewhere, and clamped to k).  With lambda(k) = dL/du(k):
+//   lambda(K)            = u(K) - u_obs on the interior, 0 at the ends
+//   lambda_i(k)          += (1-2r) lambda_i(k+1)
+//   lambda_{i+1}(k - dR) += r lambda_i(k+1)
+//   lambda_{i-1}(k - dL) += r lambda_i(k+1)
+//   dL/dr                += lambda_i(k+1) ((u_{i+1}(k-dR) - 2 u_i(k)) + u_{i-1}(k-dL))
+// A read made with delay d > 0 becomes, in the backward march, a contribution
+// to an earlier time level that has not been reached yet: it is parked in a
+// ring of q+1 pending sums per boundary point and added when the march gets
+// there.  Contributions with d = 0 are gathered directly, so a backward step
+// is a gather like the forward stencil.
+//
+// Memory: the forward pass keeps a checkpoint every C steps (the full state
+// plus the last q values of every boundary point, which delayed reads may
+// need); the backward pass recomputes each interval from its checkpoint into
+// a workspace of C+1 states and then marches lambda back through it.
+//
+// Each step is one launch over all points of all rods (the backward march
+// needs every point of step k before any of step k-1).  Every reduction (loss,
+// dL/dr) is deterministic: fixed per-block partials with compensated sums,
+// added in a fixed order at the end.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "impl.h"
+
+namespace heat1d_impl {
+using namespace heat1d_dev;
+
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+struct AdjGeom {
+  int64_t nrods, N;
+  int S;          // segments per rod
+  int q, Q;       // delay window, pending ring length (q+1)
+  int64_t bpr;    // blocks per rod
+  const double* r;
+  const double* c1;
+  const double* cN;
+  const uint8_t* trace;  // [rod][K][S-1][2] or null (synchronous)
+  int64_t K;
+};
+
+__device__ __forceinline__ int seg_of(int64_t i, int64_t N, int S) {
+  const int64_t base = N / S, extra = N % S, big = extra * (base + 1);
+  return static_cast<int>(i < big ? i / (base + 1) : extra + (i - big) / base);
+}
+__device__ __forceinline__ int64_t seg_start(int s, int64_t N, int S) {
+  const int64_t base = N / S, extra = N % S;
+  return s * base + (s < extra ? s : extra);
+}
+
+__device__ __forceinline__ int delay_at(const AdjGeom& g, int64_t rod, int64_t k, int b, int side) {
+  const int d = g.trace[((rod * g.K + k) * (g.S - 1) + b) * 2 + side];
+  return static_cast<int>(d < k ? d : k);
+}
+
+// Edge history: for each time t of the current interval a row of
+// [rod][S-1][2] values: side 0 = first point of segment b+1, side 1 = last
+// point of segment b.  Row of time t is t - t0 (t0 = first time held).
+template <typename real>
+__device__ __forceinline__ real* eh_row(real* eh, const AdjGeom& g, int64_t row) {
+  return eh + row * g.nrods * (g.S - 1) * 2;
+}
+
+// Sets the Dirichlet ends of every rod of a state row.
+template <typename real>
+__global__ void adj_force_ends(AdjGeom g, real* u) {
+  const int64_t rod = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rod >= g.nrods) return;
+  u[rod * g.N] = static_cast<real>(g.c1[rod]);
+  u[rod * g.N + g.N - 1] = static_cast<real>(g.cN[rod]);
+}
+
+// Writes the boundary points of state row `u` (all rods) into history row.
+template <typename real>
+__global__ void adj_edge_gather(AdjGeom g, const real* u, real* eh_dst) {
+  const int64_t n = g.nrods * (g.S - 1);
+  for (int64_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    const int64_t rod = x / (g.S - 1);
+    const int b = static_cast<int>(x % (g.S - 1));
+    const int64_t first = seg_start(b + 1, g.N, g.S);
+    eh_dst[x * 2 + 0] = u[rod * g.N + first];
+    eh_dst[x * 2 + 1] = u[rod * g.N + first - 1];
+  }
+}
+
+// One forward step k -> k+1 for every point of every rod (same arithmetic as
+// the persistent kernels).  Delayed reads come from the edge history.
+template <typename real>
+__global__ void __launch_bounds__(kAdjThreads) adj_fwd_step(AdjGeom g, int64_t k, const real* __restrict__ u,
+                                                            real* __restrict__ out, real* eh, int64_t t0) {
+  const int64_t rod = blockIdx.x / g.bpr;
+  const int64_t i = (blockIdx.x % g.bpr) * kAdjThreads + threadIdx.x;
+  if (i >= g.N) return;
+  const real* ur = u + rod * g.N;
+  const real r = static_cast<real>(g.r[rod]);
+  const real one = static_cast<real>(g.N > 0);
+  real v;
+  if (i == 0) {
+    v = static_cast<real>(g.c1[rod]);
+  } else if (i == g.N - 1) {
+    v = static_cast<real>(g.cN[rod]);
+  } else {
+    real uL = ur[i - 1], uR = ur[i + 1];
+    if (g.trace) {
+      const int s = seg_of(i, g.N, g.S);
+      if (s > 0 && i == seg_start(s, g.N, g.S)) {
+        const int d = delay_at(g, rod, k, s - 1, 1);
+        if (d > 0) uL = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1];
+      }
+      if (s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1) {
+        const int d = delay_at(g, rod, k, s, 0);
+        if (d > 0) uR = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + s) * 2 + 0];
+      }
+    }
+    v = ftcs(r, one, uL, ur[i], uR);
+  }
+  out[rod * g.N + i] = v;
+  if (g.trace) {  // boundary points of time k+1 into the history
+    const int s = seg_of(i, g.N, g.S);
+    real* row = eh_row(eh, g, k + 1 - t0);
+    if (s > 0 && i == seg_start(s, g.N, g.S)) row[(rod * (g.S - 1) + (s - 1)) * 2 + 0] = v;
+    if (s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1) row[(rod * (g.S - 1) + s) * 2 + 1] = v;
+  }
+}
+
+// Block-wide sum of one double per thread (fixed order).
+__device__ double block_sum(double x, double* red) {
+  red[threadIdx.x] = x;
+  __syncthreads();
+  for (int w = kAdjThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// Compensated accumulation of one partial per block.
+__device__ void kahan_add(double* sum, double* comp, double x) {
+  const double y = x - *comp;
+  const double t = *sum + y;
+  *comp = (t - *sum) - y;
+  *sum = t;
+}
+
+// lambda(K) = u(K) - u_obs on the interior; per-block loss partials.
+// With `cotangent` set, uobs is dL/du(K) itself and the loss is reported 0.
+template <typename real>
+__global__ void __launch_bounds__(kAdjThreads) adj_init(AdjGeom g, const real* __restrict__ uK,
+                                                        const double* __restrict__ uobs, double* __restrict__ lam,
+                                                        double* loss_part, int cotangent) {
+  __shared__ double red[kAdjThreads];
+  const int64_t rod = blockIdx.x / g.bpr;
+  const int64_t i = (blockIdx.x % g.bpr) * kAdjThreads + threadIdx.x;
+  double e2 = 0.0;
+  if (i < g.N) {
+    const int64_t x = rod * g.N + i;
+    const double e = cotangent ? uobs[x] : static_cast<double>(uK[x]) - uobs[x];
+    e2 = cotangent ? 0.0 : 0.5 * e * e;
+    lam[x] = (i > 0 && i < g.N - 1) ? e : 0.0;
+  }
+  const double s = block_sum(e2, red);
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = s;
+}
+
+// One backward step: lambda(k) from lambda(k+1), with u(k) (row `u`) and the
+// edge history for delayed reads; dL/dr partials per block.
+template <typename real>
+__global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k, const double* __restrict__ lin,
+                                                            double* __restrict__ lout, const real* __restrict__ u,
+                                                            const real* eh, int64_t t0, double* pend,
+                                                            double* gr_sum, double* gr_comp) {
+  __shared__ double red[kAdjThreads];
+  const int64_t rod = blockIdx.x / g.bpr;
+  const int64_t i = (blockIdx.x % g.bpr) * kAdjThreads + threadIdx.x;
+  double contrib = 0.0;
+  if (i < g.N) {
+    const int64_t base = rod * g.N;
+    if (i == 0 || i == g.N - 1) {
+      lout[base + i] = 0.0;
+    } else {
+      const double r = g.r[rod];
+      const double gi = lin[base + i];
+      const real* ur = u + base;
+      double uL = static_cast<double>(ur[i - 1]), uR = static_cast<double>(ur[i + 1]);
+      int s = 0, dL = 0, dR = 0;
+      bool first = false, last = false;
+      double acc = 0.0;
+      if (g.trace) {
+        s = seg_of(i, g.N, g.S);
+        first = s > 0 && i == seg_start(s, g.N, g.S);
+        last = s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1;
+        const int64_t slot = k % g.Q;
+        double* prow = pend + slot * g.nrods * (g.S - 1) * 2;
+        // parked contributions to this point at time k
+        if (first) {
+          double* p = prow + (rod * (g.S - 1) + (s - 1)) * 2 + 0;
+          acc += *p;
+          *p = 0.0;
+        }
+        if (last) {
+          double* p = prow + (rod * (g.S - 1) + s) * 2 + 1;
+          acc += *p;
+          *p = 0.0;
+        }
+        if (first) {
+          dL = delay_at(g, rod, k, s - 1, 1);
+          if (dL > 0) uL = static_cast<double>(eh_row(eh, g, k - dL - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1]);
+        }
+        if (last) {
+          dR = delay_at(g, rod, k, s, 0);
+          if (dR > 0) uR = static_cast<double>(eh_row(eh, g, k - dR - t0)[(rod * (g.S - 1) + s) * 2 + 0]);
+        }
+      }
+      // direct (d = 0) contributions: from i-1 (it reads u_i as its right neighbour),
+      // from i itself, from i+1 (it reads u_i as its left neighbour)
+      if (i - 1 >= 1) {
+        bool direct = true;
+        if (first) direct = delay_at(g, rod, k, s - 1, 0) == 0;  // i-1 = last of segment s-1 reads right
+        if (direct) acc += r * lin[base + i - 1];
+      }
+      acc += (1.0 - 2.0 * r) * gi;
+      if (i + 1 <= g.N - 2) {
+        bool direct = true;
+        if (last) direct = delay_at(g, rod, k, s, 1) == 0;  // i+1 = first of segment s+1 reads left
+        if (direct) acc += r * lin[base + i + 1];
+      }
+      lout[base + i] = acc;
+      // this point's own delayed reads send r*lambda_i(k+1) to earlier levels
+      if (g.trace) {
+        if (first && dL > 0) {
+          double* p = pend + ((k - dL) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + (s - 1)) * 2 + 1;
+          *p += r * gi;
+        }
+        if (last && dR > 0) {
+          double* p = pend + ((k - dR) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + s) * 2 + 0;
+          *p += r * gi;
+        }
+      }
+      const double du = (uR - 2.0 * static_cast<double>(ur[i])) + uL;
+      contrib = gi * du;
+    }
+  }
+  const double bs = block_sum(contrib, red);
+  if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
+}
+
+// Per rod: sums of the block partials, in block order.
+__global__ void adj_finish(AdjGeom g, const double* loss_part, const double* gr_sum, double* loss_out,
+                           double* gr_out) {
+  const int64_t rod = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rod >= g.nrods) return;
+  double ls = 0.0, lc = 0.0, gs = 0.0, gc = 0.0;
+  for (int64_t b = 0; b < g.bpr; ++b) {
+    kahan_add(&ls, &lc, loss_part[rod * g.bpr + b]);
+    kahan_add(&gs, &gc, gr_sum[rod * g.bpr + b]);
+  }
+  loss_out[rod] = ls;
+  gr_out[rod] = gs;
+}
+
+template <typename real>
+int adjoint_t(const AdjointRun& a) {
+  cudaStream_t st = a.stream;
+  const int64_t nr = a.nrods, N = a.N, K = a.K, C = std::max<int64_t>(1, std::min<int64_t>(a.ckpt_every, K));
+  const int64_t npts = nr * N;
+  const bool async_run = a.trace != nullptr;
+  const int S = async_run ? a.S : 1;
+  const int q = async_run ? a.q : 1;
+  AdjGeom g{};
+  g.nrods = nr;
+  g.N = N;
+  g.S = S;
+  g.q = q;
+  g.Q = q + 1;
+  g.bpr = (N + kAdjThreads - 1) / kAdjThreads;
+  g.trace = a.trace;
+  g.K = K;
+  const int64_t nblocks = nr * g.bpr;
+  const int64_t nc = (K + C - 1) / C;  // intervals
+  const int64_t ehw = async_run ? nr * (S - 1) * 2 : 0;  // history row width
+  const int64_t eh_rows = C + q;                          // times [kc-q+1, kc+C]
+
+  // scratch
+  std::vector<void*> owned;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    owned.push_back(p);
+    return p;
+  };
+  auto cleanup = [&]() {
+    for (void* p : owned) cudaFree(p);
+  };
+  double* d_coef = static_cast<double*>(alloc(sizeof(double) * 3 * nr));
+  real* X = static_cast<real*>(alloc(sizeof(real) * (C + 1) * npts));       // interval workspace
+  real* ck = static_cast<real*>(alloc(sizeof(real) * nc * npts));           // checkpoints u(kc)
+  real* eh = static_cast<real*>(alloc(sizeof(real) * eh_rows * std::max<int64_t>(ehw, 1)));
+  real* ckeh = static_cast<real*>(alloc(sizeof(real) * nc * q * std::max<int64_t>(ehw, 1)));
+  double* lam = static_cast<double*>(alloc(sizeof(double) * 2 * npts));
+  double* pend = static_cast<double*>(alloc(sizeof(double) * g.Q * std::max<int64_t>(ehw, 1)));
+  double* parts = static_cast<double*>(alloc(sizeof(double) * 3 * nblocks));
+  double* outs = static_cast<double*>(alloc(sizeof(double) * 2 * nr));
+  if (!d_coef || !X || !ck || !eh || !ckeh || !lam || !pend || !parts || !outs) {
+    cleanup();
+    return HEAT1D_ERR_OOM;
+  }
+  std::vector<double> coef(3 * nr);
+  for (int64_t j = 0; j < nr; ++j) {
+    coef[j] = a.r[j];
+    coef[nr + j] = a.c1[j];
+    coef[2 * nr + j] = a.cN[j];
+  }
+  g.r = d_coef;
+  g.c1 = d_coef + nr;
+  g.cN = d_coef + 2 * nr;
+  cudaError_t e = cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pend, 0, sizeof(double) * g.Q * std::max<int64_t>(ehw, 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(parts, 0, sizeof(double) * 3 * nblocks, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(X, a.u0, sizeof(real) * npts, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return HEAT1D_ERR_CUDA;
+  }
+  const dim3 grid(static_cast<unsigned>(nblocks)), block(kAdjThreads);
+  const int gather_blocks = static_cast<int>(std::min<int64_t>(1024, (std::max<int64_t>(ehw / 2, 1) + 255) / 256));
+  adj_force_ends<real><<<static_cast<unsigned>((nr + 127) / 128), 128, 0, st>>>(g, X);  // u(0) with its ends set
+  // history rows for times <= 0 all hold u(0) (reads before 0 are clamped, so
+  // only the row of time 0 is ever read)
+  if (async_run) {
+    for (int64_t row = 0; row < q; ++row)
+      adj_edge_gather<real><<<gather_blocks, 256, 0, st>>>(g, X, eh + row * ehw);
+  }
+
+  // ---- forward with checkpoints
+  for (int64_t c = 0; c < nc; ++c) {
+    const int64_t kc = c * C, Cc = std::min<int64_t>(C, K - kc);
+    const int64_t t0 = kc - (q - 1);
+    if (c > 0) {  // the interval starts from the previous interval's last state and history
+      e = cudaMemcpyAsync(X, X + C * npts, sizeof(real) * npts, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess && async_run)
+        e = cudaMemcpyAsync(eh, eh + C * ehw, sizeof(real) * q * ehw, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) break;
+    }
+    e = cudaMemcpyAsync(ck + c * npts, X, sizeof(real) * npts, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && async_run)
+      e = cudaMemcpyAsync(ckeh + c * q * ehw, eh, sizeof(real) * q * ehw, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) break;
+    for (int64_t j = 0; j < Cc; ++j)
+      adj_fwd_step<real><<<grid, block, 0, st>>>(g, kc + j, X + j * npts, X + (j + 1) * npts, eh, t0);
+    if (c == nc - 1 && Cc != C)  // make the final state sit where the next interval would look
+      e = cudaMemcpyAsync(X + C * npts, X + Cc * npts, sizeof(real) * npts, cudaMemcpyDeviceToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess && a.uK)
+    e = cudaMemcpyAsync(a.uK, X + C * npts, sizeof(real) * npts, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return HEAT1D_ERR_CUDA;
+  }
+  double* lin = lam;
+  double* lout = lam + npts;
+  adj_init<real><<<grid, block, 0, st>>>(g, X + C * npts, a.u_obs, lin, parts, a.cotangent);
+
+  // ---- backward: recompute each interval, then march lambda back through it
+  for (int64_t c = nc - 1; c >= 0 && e == cudaSuccess; --c) {
+    const int64_t kc = c * C, Cc = std::min<int64_t>(C, K - kc);
+    const int64_t t0 = kc - (q - 1);
+    e = cudaMemcpyAsync(X, ck + c * npts, sizeof(real) * npts, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && async_run)
+      e = cudaMemcpyAsync(eh, ckeh + c * q * ehw, sizeof(real) * q * ehw, cudaMemcpyDeviceToDevice, st);
+    for (int64_t j = 0; j + 1 < Cc && e == cudaSuccess; ++j)  // states kc .. kc+Cc-1
+      adj_fwd_step<real><<<grid, block, 0, st>>>(g, kc + j, X + j * npts, X + (j + 1) * npts, eh, t0);
+    for (int64_t k = kc + Cc - 1; k >= kc; --k) {
+      adj_bwd_step<real><<<grid, block, 0, st>>>(g, k, lin, lout, X + (k - kc) * npts, eh, t0, pend,
+                                                 parts + nblocks, parts + 2 * nblocks);
+      std::swap(lin, lout);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    adj_finish<<<static_cast<unsigned>((nr + 127) / 128), 128, 0, st>>>(g, parts, parts + nblocks, outs, outs + nr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(a.grad_u0, lin, sizeof(double) * npts, cudaMemcpyDeviceToDevice, st);
+  std::vector<double> host(2 * nr);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), outs, sizeof(double) * 2 * nr, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return HEAT1D_ERR_CUDA;
+  for (int64_t j = 0; j < nr; ++j) {
+    if (a.loss) a.loss[j] = host[j];
+    if (a.grad_r) a.grad_r[j] = host[nr + j];
+  }
+  return HEAT1D_OK;
+}
+
+}  // namespace
+
+int run_adjoint(const AdjointRun& a, int dtype) {
+  return dtype == HEAT1D_F64 ? adjoint_t<double>(a) : adjoint_t<float>(a);
+}
+
+}  // namespace heat1d_impl

@@ -746,3 +746,106 @@ int heat1d_run_batched(const heat1d_rod* rods, int64_t nrods, void* u_packed, in
 }
 
 }  // extern "C"
+
+// ============================================================ adjoint
+
+extern "C" {
+
+static int adjoint_handle(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device, const double* u_obs,
+                          int cotangent, int64_t ckpt_every, double* grad_u0, double* grad_r, double* loss) {
+  if (!h || !u_obs || !grad_u0) return fail(HEAT1D_ERR_INVAL, "heat1d_adjoint: null argument");
+  if (K < 0) return fail(HEAT1D_ERR_INVAL, "heat1d_adjoint: K must be >= 0");
+  const bool async_run = trace != nullptr && h->S > 1;
+  const size_t tbytes = static_cast<size_t>(K) * (h->S - 1) * 2;
+  const uint8_t* dtrace = nullptr;
+  int rc;
+  if (async_run) {
+    if (trace_on_device) {
+      dtrace = trace;
+    } else {
+      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
+      HEAT1D_CUDA(cudaMemcpyAsync(h->d_trace, trace, tbytes, cudaMemcpyHostToDevice, h->stream));
+      dtrace = h->d_trace;
+    }
+  }
+  // host-side check of the trace window (the kernels assume every d < q)
+  if (async_run) {
+    std::vector<uint8_t> tr(tbytes);
+    HEAT1D_CUDA(cudaMemcpyAsync(tr.data(), dtrace, tbytes, cudaMemcpyDeviceToHost, h->stream));
+    HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
+    for (size_t j = 0; j < tbytes; ++j)
+      if (tr[j] >= h->q) return fail(HEAT1D_ERR_TRACE, "heat1d_adjoint: trace entry >= q");
+  }
+  heat1d_impl::AdjointRun a{};
+  a.nrods = 1;
+  a.N = h->N;
+  a.K = K;
+  a.r = &h->r;
+  a.c1 = &h->c1;
+  a.cN = &h->cN;
+  a.S = h->S;
+  a.q = h->q;
+  a.trace = dtrace;
+  a.u0 = h->u[h->cur];
+  a.u_obs = u_obs;
+  a.ckpt_every = ckpt_every > 0 ? ckpt_every : 128;
+  a.uK = h->u[1 - h->cur];
+  a.grad_u0 = grad_u0;
+  a.grad_r = grad_r;
+  a.loss = loss;
+  a.cotangent = cotangent;
+  a.stream = h->stream;
+  rc = heat1d_impl::run_adjoint(a, h->dtype);
+  if (rc == HEAT1D_ERR_OOM) return fail(rc, "heat1d_adjoint: out of device memory for checkpoints");
+  if (rc) return cuda_fail(cudaGetLastError(), "heat1d_adjoint");
+  h->cur = 1 - h->cur;  // the state is now u(K)
+  return HEAT1D_OK;
+}
+
+int heat1d_adjoint(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device, const double* u_obs,
+                   int64_t ckpt_every, double* grad_u0, double* grad_r, double* loss) {
+  return adjoint_handle(h, K, trace, trace_on_device, u_obs, 0, ckpt_every, grad_u0, grad_r, loss);
+}
+
+int heat1d_vjp(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device, const double* grad_uK,
+               int64_t ckpt_every, double* grad_u0, double* grad_r) {
+  return adjoint_handle(h, K, trace, trace_on_device, grad_uK, 1, ckpt_every, grad_u0, grad_r, nullptr);
+}
+
+int heat1d_adjoint_batched(int64_t nrods, int64_t N, int64_t K, const double* r, const double* c1, const double* cN,
+                           int dtype, const void* u0, const double* u_obs, int cotangent, int64_t segments, int q,
+                           const uint8_t* trace, int64_t ckpt_every, void* uK, double* grad_u0, double* grad_r,
+                           double* loss, void* stream) {
+  if (nrods < 1 || N < 3 || K < 0 || !r || !c1 || !cN || !u0 || !u_obs || !grad_u0)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_adjoint_batched: bad argument");
+  if (dtype != HEAT1D_F32 && dtype != HEAT1D_F64) return fail(HEAT1D_ERR_INVAL, "heat1d_adjoint_batched: dtype");
+  for (int64_t j = 0; j < nrods; ++j)
+    if (!(r[j] > 0.0 && r[j] <= 0.5)) return fail(HEAT1D_ERR_INVAL, "heat1d_adjoint_batched: r out of (0, 0.5]");
+  if (trace && (segments < 2 || segments > N || q < 1 || q > 255))
+    return fail(HEAT1D_ERR_INVAL, "heat1d_adjoint_batched: a trace needs 2 <= segments <= N and 1 <= q <= 255");
+  heat1d_impl::AdjointRun a{};
+  a.nrods = nrods;
+  a.N = N;
+  a.K = K;
+  a.r = r;
+  a.c1 = c1;
+  a.cN = cN;
+  a.S = trace ? static_cast<int>(segments) : 1;
+  a.q = trace ? q : 1;
+  a.trace = trace;
+  a.u0 = u0;
+  a.u_obs = u_obs;
+  a.ckpt_every = ckpt_every > 0 ? ckpt_every : 128;
+  a.uK = uK;
+  a.grad_u0 = grad_u0;
+  a.grad_r = grad_r;
+  a.loss = loss;
+  a.cotangent = cotangent;
+  a.stream = static_cast<cudaStream_t>(stream);
+  int rc = heat1d_impl::run_adjoint(a, dtype);
+  if (rc == HEAT1D_ERR_OOM) return fail(rc, "heat1d_adjoint_batched: out of device memory for checkpoints");
+  if (rc) return cuda_fail(cudaGetLastError(), "heat1d_adjoint_batched");
+  return HEAT1D_OK;
+}
+
+}  // extern "C"

@@ -137,6 +137,30 @@ struct BatchRun {
 int launch_batched(const BatchRun& a, int dtype, int E, int threads, int grid, cudaStream_t st);
 int max_resident_batched(int dtype, int E, int threads);
 
+// ------------------------------------------------------------ adjoint
+
+// nrods rods of the same N and K, packed rod-major.
+struct AdjointRun {
+  int64_t nrods, N, K;
+  const double* r;         // host, nrods
+  const double* c1;        // host, nrods
+  const double* cN;        // host, nrods
+  int S, q;                // segments per rod and delay window (used when trace != null)
+  const uint8_t* trace;    // device [rod][K][S-1][2], null: synchronous run
+  const void* u0;          // device, nrods*N values of the dtype
+  const double* u_obs;     // device, nrods*N
+  int64_t ckpt_every;      // C
+  void* uK;                // device, nrods*N values of the dtype, or null
+  double* grad_u0;         // device, nrods*N
+  double* grad_r;          // host, nrods (may be null)
+  double* loss;            // host, nrods (may be null)
+  int cotangent;           // 1: u_obs holds dL/du(K) itself (general vector-Jacobian product)
+  cudaStream_t stream;
+};
+// Runs the forward pass with checkpoints and the backward pass; waits for
+// the stream.  Returns a heat1d_status.
+int run_adjoint(const AdjointRun& a, int dtype);
+
 // Largest number of CTAs of these kernels that can be resident at once.
 int max_resident_sync(int dtype, int E, int threads);
 int max_resident_async(int dtype, int E, int threads);

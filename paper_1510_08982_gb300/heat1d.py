@@ -29,7 +29,8 @@ EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_las
            "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
            "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync",
            "heat1d_batch_create", "heat1d_batch_run", "heat1d_batch_sync", "heat1d_batch_describe",
-           "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_run_sync_noalloc"]
+           "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_adjoint", "heat1d_vjp",
+           "heat1d_adjoint_batched", "heat1d_run_sync_noalloc"]
 
 
 class Heat1dError(RuntimeError):
@@ -87,6 +88,10 @@ def load():
         "heat1d_batch_describe": (i32, [vp, vp]),
         "heat1d_batch_destroy": (None, [vp]),
         "heat1d_run_batched": (i32, [ctypes.POINTER(RodSpec), i64, vp, i32, ctypes.POINTER(Opts), vp]),
+        "heat1d_adjoint": (i32, [vp, i64, vp, i32, vp, i64, vp, vp, vp]),
+        "heat1d_vjp": (i32, [vp, i64, vp, i32, vp, i64, vp, vp]),
+        "heat1d_adjoint_batched": (i32, [i64, i64, i64, vp, vp, vp, i32, vp, vp, i32, i64, i32, vp, i64, vp, vp, vp,
+                                          vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -254,6 +259,32 @@ class Heat1d:
         """Waits for the stream; raises on a device-side failure."""
         _check(self.lib.heat1d_sync(self.h))
 
+    def adjoint(self, K, u_obs, trace=None, ckpt_every=0):
+        """heat1d_adjoint from the current state: returns (loss, grad_u0 as a
+        CUDA float64 tensor, grad_r).  Afterwards the state is u(K)."""
+        torch = _torch()
+        self._stream()
+        uo = u_obs.to(device="cuda", dtype=torch.float64).contiguous()
+        g = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        gr = ctypes.c_double(0.0)
+        ls = ctypes.c_double(0.0)
+        tp, on_dev = self._trace_ptr(trace, K) if trace is not None else (None, 0)
+        _check(self.lib.heat1d_adjoint(self.h, int(K), tp, on_dev, ctypes.c_void_p(uo.data_ptr()), int(ckpt_every),
+                                       ctypes.c_void_p(g.data_ptr()), ctypes.byref(gr), ctypes.byref(ls)))
+        return ls.value, g, gr.value
+
+    def vjp(self, K, grad_uK, trace=None, ckpt_every=0):
+        """heat1d_vjp from the current state: (grad_u0 float64 tensor, grad_r)."""
+        torch = _torch()
+        self._stream()
+        gk = grad_uK.to(device="cuda", dtype=torch.float64).contiguous()
+        g = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        gr = ctypes.c_double(0.0)
+        tp, on_dev = self._trace_ptr(trace, K) if trace is not None else (None, 0)
+        _check(self.lib.heat1d_vjp(self.h, int(K), tp, on_dev, ctypes.c_void_p(gk.data_ptr()), int(ckpt_every),
+                                   ctypes.c_void_p(g.data_ptr()), ctypes.byref(gr)))
+        return g, gr.value
+
     def _trace_ptr(self, t, K):
         torch = _torch()
         if t is None:
@@ -377,3 +408,32 @@ def run_batched(specs, u, dtype="float64", **opts):
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     _check(load().heat1d_run_batched(arr, len(specs), ctypes.c_void_p(u.data_ptr()), _dtype_code(dtype),
                                      ctypes.byref(o), st))
+
+
+def adjoint_batched(u0, u_obs, r, c1, cN, K, trace=None, segments=0, q=3, ckpt_every=0, cotangent=False):
+    """heat1d_adjoint_batched for u0 of shape (nrods, N) (CUDA, float32 or
+    float64).  Returns (uK, grad_u0 (float64), grad_r (numpy), loss (numpy))."""
+    torch = _torch()
+    nrods, N = u0.shape
+    u0 = u0.contiguous()
+    uo = u_obs.to(device="cuda", dtype=torch.float64).contiguous()
+    uK = torch.empty_like(u0)
+    g = torch.empty((nrods, N), dtype=torch.float64, device="cuda")
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    cc1 = np.ascontiguousarray(c1, dtype=np.float64)
+    ccN = np.ascontiguousarray(cN, dtype=np.float64)
+    gr = np.zeros(nrods)
+    ls = np.zeros(nrods)
+    tp = None
+    if trace is not None:
+        if not (isinstance(trace, torch.Tensor) and trace.is_cuda and trace.dtype == torch.uint8):
+            raise ValueError("trace must be a CUDA uint8 tensor of shape (nrods, K, segments-1, 2)")
+        tp = ctypes.c_void_p(trace.contiguous().data_ptr())
+    vp = ctypes.c_void_p
+    st = vp(torch.cuda.current_stream().cuda_stream)
+    _check(load().heat1d_adjoint_batched(nrods, N, int(K), rr.ctypes.data_as(vp), cc1.ctypes.data_as(vp),
+                                         ccN.ctypes.data_as(vp), _dtype_code(u0.dtype), vp(u0.data_ptr()),
+                                         vp(uo.data_ptr()), int(bool(cotangent)), int(segments), int(q), tp,
+                                         int(ckpt_every), vp(uK.data_ptr()), vp(g.data_ptr()),
+                                         gr.ctypes.data_as(vp), ls.ctypes.data_as(vp), st))
+    return uK, g, gr, ls
