@@ -56,11 +56,14 @@ def parse():
     p.add_argument("--K", type=int, default=K_DEFAULT)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="sine-mode-rod", choices=["sine-mode-rod", "streamed-rod", "uneven-rods"],
+    p.add_argument("--workload", default="sine-mode-rod",
+                   choices=["sine-mode-rod", "streamed-rod", "uneven-rods", "inverse-problem"],
                    help="sine-mode-rod (default): the sync vs async rod; streamed-rod: the 2^26-point "
                         "temporal-blocking rod; uneven-rods: 4096 rods in one batched launch")
     p.add_argument("--dtype", default=None, choices=["f32", "f64"], help="streamed-rod / uneven-rods precision")
     p.add_argument("--halo", type=int, default=0, help="streamed-rod: steps per HBM pass (T)")
+    p.add_argument("--rods", type=int, default=256, help="inverse-problem: rods in the batch")
+    p.add_argument("--async-trace", action="store_true", help="inverse-problem: replayed asynchronous run")
     return p.parse_args()
 
 
@@ -370,6 +373,80 @@ def run_uneven(args):
     return 0
 
 
+def run_inverse(args):
+    """Adjoint of the inverse problem: 256 rods of N = 65536, K = 2e4, smooth
+    u(0), r_true ~ U[0.1, 0.45], u_obs = u(K) + N(0, 1e-4); one step = the
+    forward pass with checkpoints every 128 steps + the backward pass
+    (recompute + transposed stencil), giving dL/du(0) and dL/dr per rod."""
+    torch, rank, world, local = _device_setup()
+    from paper_1510_08982_gb300 import heat1d, inputs
+    dev = torch.device("cuda", local)
+    dt = args.dtype or "f64"
+    tdt = torch.float32 if dt == "f32" else torch.float64
+    K = args.K if args.K != K_DEFAULT else 20_000
+    N = args.N if args.N != N_DEFAULT else 65536
+    nr = args.rods
+    rods = inputs.inverse_problem_rods(n_rods=nr, N=N, K=K, seed=1000 + rank)
+    u0 = torch.tensor(np.stack([r.u0 for r in rods]), dtype=tdt, device=dev)
+    r = np.array([x.r for x in rods])
+    c1 = np.array([x.c1 for x in rods])
+    cN = np.array([x.cN for x in rods])
+    S, q = 16, 3  # 4096 points per segment: one CTA each for the observation runs
+    trace = None
+    if args.async_trace:
+        trace = torch.tensor(np.stack([inputs.delay_trace(K, S, q, seed=j) for j in range(nr)]), device=dev)
+    # observations: u(K) at r_true plus noise; the gradient is taken at 0.9 r_true
+    uobs = torch.empty(nr, N, dtype=torch.float64, device=dev)
+    for j, x in enumerate(rods):
+        opts = {"segments": S, "q": q} if trace is not None else {}
+        with heat1d.Heat1d(N, x.r, x.c1, x.cN, dtype="float32" if dt == "f32" else "float64", **opts) as h:
+            h.set_u(u0[j])
+            if trace is None:
+                h.run_sync(K)
+            else:
+                h.replay(K, trace[j].contiguous())
+            h.sync()
+            uobs[j] = h.get_u().double()
+    uobs += torch.tensor(np.stack([inputs.observation_noise(N, seed=7000 + j) for j in range(nr)]), device=dev)
+    rg = 0.9 * r
+
+    def step():
+        return heat1d.adjoint_batched(u0, uobs, rg, c1, cN, K, trace=trace, segments=S if trace is not None else 0,
+                                      q=q, ckpt_every=128)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = step()
+    torch.cuda.synchronize()
+    dt_s = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    dt_s = _max_over_ranks(torch, world, dt_s, dev)
+    updates = nr * (N - 2) * K
+    ups = world * updates / dt_s
+    alu = (FP64_NOMINAL_TFLOPS * 1e12 / 2) / 3
+    line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dt, "data": "synthetic",
+            "config": {"workload": "inverse problem: %d rods x N=%d, K=%d, checkpoints every 128 steps, %s; one step = "
+                                   "forward with checkpoints + backward (recompute + adjoint); value counts forward "
+                                   "updates (rods x (N-2) x K) per second of the whole gradient computation"
+                                   % (nr, N, K, "replayed trace S=16 q=3" if trace is not None else "synchronous"),
+                       "rods": nr, "N": N, "K": K, "ckpt_every": 128},
+            "gradient": {"grad_r_first_rods": [float(x) for x in out[2][:4]], "loss_first_rods": [float(x) for x in out[3][:4]]},
+            "roofline": {"bound": "alu", "kernel": "adj_fwd_step / adj_bwd_step", "achieved": ups / 1e9,
+                         "peak": alu / 1e9, "unit": "Gupdates/s (forward-equivalent)", "frac": ups / alu,
+                         "note": "three passes (forward, recompute, backward) per forward update"},
+            "clocks": clk, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -378,6 +455,8 @@ def main():
         return run_streamed(args)
     if args.workload == "uneven-rods":
         return run_uneven(args)
+    if args.workload == "inverse-problem":
+        return run_inverse(args)
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)

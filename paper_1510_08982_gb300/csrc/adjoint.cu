@@ -41,12 +41,14 @@ using namespace heat1d_dev;
 namespace {
 
 constexpr int kAdjThreads = 256;
+constexpr int kAdjPointsPerThread = 16;  // a block walks kAdjThreads * 16 points of one rod
 
 struct AdjGeom {
   int64_t nrods, N;
   int S;          // segments per rod
   int q, Q;       // delay window, pending ring length (q+1)
   int64_t bpr;    // blocks per rod
+  int64_t span;   // points per block (a block never straddles two rods)
   const double* r;
   const double* c1;
   const double* cN;
@@ -104,51 +106,56 @@ template <typename real>
 __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step(AdjGeom g, int64_t k, const real* __restrict__ u,
                                                             real* __restrict__ out, real* eh, int64_t t0) {
   const int64_t rod = blockIdx.x / g.bpr;
-  const int64_t i = (blockIdx.x % g.bpr) * kAdjThreads + threadIdx.x;
-  if (i >= g.N) return;
+  const int64_t b0 = (blockIdx.x % g.bpr) * g.span;
+  const int64_t b1 = min(b0 + g.span, g.N);
   const real* ur = u + rod * g.N;
+  real* orow = out + rod * g.N;
   const real r = static_cast<real>(g.r[rod]);
   const real one = static_cast<real>(g.N > 0);
-  real v;
-  if (i == 0) {
-    v = static_cast<real>(g.c1[rod]);
-  } else if (i == g.N - 1) {
-    v = static_cast<real>(g.cN[rod]);
-  } else {
-    real uL = ur[i - 1], uR = ur[i + 1];
-    if (g.trace) {
-      const int s = seg_of(i, g.N, g.S);
-      if (s > 0 && i == seg_start(s, g.N, g.S)) {
-        const int d = delay_at(g, rod, k, s - 1, 1);
-        if (d > 0) uL = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1];
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += kAdjThreads) {
+    real v;
+    if (i == 0) {
+      v = static_cast<real>(g.c1[rod]);
+    } else if (i == g.N - 1) {
+      v = static_cast<real>(g.cN[rod]);
+    } else {
+      real uL = ur[i - 1], uR = ur[i + 1];
+      if (g.trace) {
+        const int s = seg_of(i, g.N, g.S);
+        if (s > 0 && i == seg_start(s, g.N, g.S)) {
+          const int d = delay_at(g, rod, k, s - 1, 1);
+          if (d > 0) uL = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1];
+        }
+        if (s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1) {
+          const int d = delay_at(g, rod, k, s, 0);
+          if (d > 0) uR = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + s) * 2 + 0];
+        }
       }
-      if (s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1) {
-        const int d = delay_at(g, rod, k, s, 0);
-        if (d > 0) uR = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + s) * 2 + 0];
-      }
+      v = ftcs(r, one, uL, ur[i], uR);
     }
-    v = ftcs(r, one, uL, ur[i], uR);
-  }
-  out[rod * g.N + i] = v;
-  if (g.trace) {  // boundary points of time k+1 into the history
-    const int s = seg_of(i, g.N, g.S);
-    real* row = eh_row(eh, g, k + 1 - t0);
-    if (s > 0 && i == seg_start(s, g.N, g.S)) row[(rod * (g.S - 1) + (s - 1)) * 2 + 0] = v;
-    if (s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1) row[(rod * (g.S - 1) + s) * 2 + 1] = v;
+    orow[i] = v;
+    if (g.trace) {  // boundary points of time k+1 into the history
+      const int s = seg_of(i, g.N, g.S);
+      real* row = eh_row(eh, g, k + 1 - t0);
+      if (s > 0 && i == seg_start(s, g.N, g.S)) row[(rod * (g.S - 1) + (s - 1)) * 2 + 0] = v;
+      if (s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1) row[(rod * (g.S - 1) + s) * 2 + 1] = v;
+    }
   }
 }
 
-// Block-wide sum of one double per thread (fixed order).
+// Block-wide sum of one double per thread in a fixed order: warp shuffles,
+// then the warps' sums in warp order.
 __device__ double block_sum(double x, double* red) {
-  red[threadIdx.x] = x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFullMask, x, o);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = x;
   __syncthreads();
-  for (int w = kAdjThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  const double s = red[0];
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int j = 0; j < kAdjThreads / 32; ++j) s += red[j];
   __syncthreads();
-  return s;
+  return s;  // valid in thread 0
 }
 
 // Compensated accumulation of one partial per block.
@@ -165,14 +172,15 @@ template <typename real>
 __global__ void __launch_bounds__(kAdjThreads) adj_init(AdjGeom g, const real* __restrict__ uK,
                                                         const double* __restrict__ uobs, double* __restrict__ lam,
                                                         double* loss_part, int cotangent) {
-  __shared__ double red[kAdjThreads];
+  __shared__ double red[kAdjThreads / 32];
   const int64_t rod = blockIdx.x / g.bpr;
-  const int64_t i = (blockIdx.x % g.bpr) * kAdjThreads + threadIdx.x;
+  const int64_t b0 = (blockIdx.x % g.bpr) * g.span;
+  const int64_t b1 = min(b0 + g.span, g.N);
   double e2 = 0.0;
-  if (i < g.N) {
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += kAdjThreads) {
     const int64_t x = rod * g.N + i;
     const double e = cotangent ? uobs[x] : static_cast<double>(uK[x]) - uobs[x];
-    e2 = cotangent ? 0.0 : 0.5 * e * e;
+    if (!cotangent) e2 += 0.5 * e * e;
     lam[x] = (i > 0 && i < g.N - 1) ? e : 0.0;
   }
   const double s = block_sum(e2, red);
@@ -181,80 +189,73 @@ __global__ void __launch_bounds__(kAdjThreads) adj_init(AdjGeom g, const real* _
 
 // One backward step: lambda(k) from lambda(k+1), with u(k) (row `u`) and the
 // edge history for delayed reads; dL/dr partials per block.
+//
+// With lambda extended by zeros beyond the interior, t_i = (lambda_{i+1} -
+// 2 lambda_i) + lambda_{i-1} serves both halves of the step:
+//   - lambda_i(k) = lambda_i(k+1) + r t_i, minus the terms of neighbours whose
+//     read of u_i was delayed (those arrive later through the pending ring);
+//   - by summation by parts, sum_{interior i} lambda_i ((u_{i+1} - 2u_i) +
+//     u_{i-1}) = sum_{all i} u_i t_i, so dL/dr gains u_i(k) t_i per point,
+//     plus lambda_i (u_{i+-1}(k-d) - u_{i+-1}(k)) where point i read a
+//     neighbour with delay d > 0.
 template <typename real>
 __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k, const double* __restrict__ lin,
                                                             double* __restrict__ lout, const real* __restrict__ u,
                                                             const real* eh, int64_t t0, double* pend,
                                                             double* gr_sum, double* gr_comp) {
-  __shared__ double red[kAdjThreads];
+  __shared__ double red[kAdjThreads / 32];
   const int64_t rod = blockIdx.x / g.bpr;
-  const int64_t i = (blockIdx.x % g.bpr) * kAdjThreads + threadIdx.x;
+  const int64_t b0 = (blockIdx.x % g.bpr) * g.span;
+  const int64_t b1 = min(b0 + g.span, g.N);
   double contrib = 0.0;
-  if (i < g.N) {
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += kAdjThreads) {
     const int64_t base = rod * g.N;
-    if (i == 0 || i == g.N - 1) {
+    const int64_t N = g.N;
+    const double lc = (i >= 1 && i <= N - 2) ? lin[base + i] : 0.0;
+    const double ll = (i - 1 >= 1 && i - 1 <= N - 2) ? lin[base + i - 1] : 0.0;
+    const double lr = (i + 1 >= 1 && i + 1 <= N - 2) ? lin[base + i + 1] : 0.0;
+    const real* ur = u + base;
+    const double t = __dadd_rn(__fma_rn(-2.0, lc, lr), ll);
+    contrib = __fma_rn(static_cast<double>(ur[i]), t, contrib);
+    if (i == 0 || i == N - 1) {
       lout[base + i] = 0.0;
     } else {
       const double r = g.r[rod];
-      const double gi = lin[base + i];
-      const real* ur = u + base;
-      double uL = static_cast<double>(ur[i - 1]), uR = static_cast<double>(ur[i + 1]);
-      int s = 0, dL = 0, dR = 0;
-      bool first = false, last = false;
-      double acc = 0.0;
+      double tl = t;      // t without the neighbour terms that arrive delayed
+      double pending = 0.0;
       if (g.trace) {
-        s = seg_of(i, g.N, g.S);
-        first = s > 0 && i == seg_start(s, g.N, g.S);
-        last = s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1;
-        const int64_t slot = k % g.Q;
-        double* prow = pend + slot * g.nrods * (g.S - 1) * 2;
-        // parked contributions to this point at time k
-        if (first) {
-          double* p = prow + (rod * (g.S - 1) + (s - 1)) * 2 + 0;
-          acc += *p;
-          *p = 0.0;
-        }
-        if (last) {
-          double* p = prow + (rod * (g.S - 1) + s) * 2 + 1;
-          acc += *p;
-          *p = 0.0;
-        }
-        if (first) {
-          dL = delay_at(g, rod, k, s - 1, 1);
-          if (dL > 0) uL = static_cast<double>(eh_row(eh, g, k - dL - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1]);
-        }
-        if (last) {
-          dR = delay_at(g, rod, k, s, 0);
-          if (dR > 0) uR = static_cast<double>(eh_row(eh, g, k - dR - t0)[(rod * (g.S - 1) + s) * 2 + 0]);
-        }
-      }
-      // direct (d = 0) contributions: from i-1 (it reads u_i as its right neighbour),
-      // from i itself, from i+1 (it reads u_i as its left neighbour)
-      if (i - 1 >= 1) {
-        bool direct = true;
-        if (first) direct = delay_at(g, rod, k, s - 1, 0) == 0;  // i-1 = last of segment s-1 reads right
-        if (direct) acc += r * lin[base + i - 1];
-      }
-      acc += (1.0 - 2.0 * r) * gi;
-      if (i + 1 <= g.N - 2) {
-        bool direct = true;
-        if (last) direct = delay_at(g, rod, k, s, 1) == 0;  // i+1 = first of segment s+1 reads left
-        if (direct) acc += r * lin[base + i + 1];
-      }
-      lout[base + i] = acc;
-      // this point's own delayed reads send r*lambda_i(k+1) to earlier levels
-      if (g.trace) {
-        if (first && dL > 0) {
-          double* p = pend + ((k - dL) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + (s - 1)) * 2 + 1;
-          *p += r * gi;
-        }
-        if (last && dR > 0) {
-          double* p = pend + ((k - dR) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + s) * 2 + 0;
-          *p += r * gi;
+        const int s = seg_of(i, N, g.S);
+        const bool first = s > 0 && i == seg_start(s, N, g.S);
+        const bool last = s + 1 < g.S && i == seg_start(s + 1, N, g.S) - 1;
+        if (first || last) {
+          double* prow = pend + (k % g.Q) * g.nrods * (g.S - 1) * 2;
+          if (first) {
+            double* p = prow + (rod * (g.S - 1) + (s - 1)) * 2 + 0;  // parked from i-1's delayed right reads
+            pending += *p;
+            *p = 0.0;
+            if (delay_at(g, rod, k, s - 1, 0) > 0) tl -= ll;  // i-1 read u_i late: its term is parked
+            const int dL = delay_at(g, rod, k, s - 1, 1);   // this point's own left read
+            if (dL > 0) {
+              const double uLd = static_cast<double>(eh_row(eh, g, k - dL - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1]);
+              contrib += lc * (uLd - static_cast<double>(ur[i - 1]));
+              pend[((k - dL) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + (s - 1)) * 2 + 1] += r * lc;
+            }
+          }
+          if (last) {
+            double* p = prow + (rod * (g.S - 1) + s) * 2 + 1;  // parked from i+1's delayed left reads
+            pending += *p;
+            *p = 0.0;
+            if (delay_at(g, rod, k, s, 1) > 0) tl -= lr;    // i+1 read u_i late
+            const int dR = delay_at(g, rod, k, s, 0);       // this point's own right read
+            if (dR > 0) {
+              const double uRd = static_cast<double>(eh_row(eh, g, k - dR - t0)[(rod * (g.S - 1) + s) * 2 + 0]);
+              contrib += lc * (uRd - static_cast<double>(ur[i + 1]));
+              pend[((k - dR) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + s) * 2 + 0] += r * lc;
+            }
+          }
         }
       }
-      const double du = (uR - 2.0 * static_cast<double>(ur[i])) + uL;
-      contrib = gi * du;
+      lout[base + i] = __fma_rn(r, tl, lc) + pending;
     }
   }
   const double bs = block_sum(contrib, red);
@@ -289,7 +290,8 @@ int adjoint_t(const AdjointRun& a) {
   g.S = S;
   g.q = q;
   g.Q = q + 1;
-  g.bpr = (N + kAdjThreads - 1) / kAdjThreads;
+  g.span = static_cast<int64_t>(kAdjThreads) * kAdjPointsPerThread;
+  g.bpr = (N + g.span - 1) / g.span;
   g.trace = a.trace;
   g.K = K;
   const int64_t nblocks = nr * g.bpr;
