@@ -44,6 +44,9 @@ Q = 3
 FP64_NOMINAL_TFLOPS = 1.25
 FP64_INSTR_PER_UPDATE = 3
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one launch of the asynchronous kernel on the
+# 2^20-point rod, from the committed ncu summary of that kernel.
+ASYNC_KERNEL_DRAM_BYTES = 8_463_104 + 2_816
 
 
 def parse():
@@ -603,7 +606,10 @@ def main():
                 "frac": achieved / peak_upd,
                 "peak_source": "recipe nominal FP64 1.25 TFLOP/s at 2070 MHz = 6.25e11 FP64-pipe instr/s, "
                                "3 per update (2 DFMA + 1 DADD)",
-                "traffic": None,
+                # dram__bytes_read.sum + dram__bytes_write.sum of one async launch (ncu, K = 2000; the rod is
+                # loaded once and the per-step exchange stays in L2, so the figure does not grow with K)
+                "traffic": ASYNC_KERNEL_DRAM_BYTES,
+                "traffic_source": "ncu capture of async_persistent_kernel<double,8>, K=2000 (profiles/)",
                 "per_kernel": {k: {"Gupdates_per_s": v / 1e9, "frac": v / peak_upd} for k, v in per.items()}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
