@@ -71,10 +71,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1510_08982_gb300 import dist as hd
+    return hd.env()
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -196,6 +194,11 @@ def workload_config(args, S):
             "l2": "flushed between timed steps (256 MB write); the rod itself stays on-chip for the whole run"}
 
 
+def hd_seed(rank):
+    from paper_1510_08982_gb300 import dist as hd
+    return hd.rod_seed(rank)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -217,11 +220,8 @@ def _device_setup():
 
 
 def _max_over_ranks(torch, world, x, dev):
-    if world > 1:
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-    return x
+    from paper_1510_08982_gb300 import dist as hd
+    return hd.max_over_ranks(x, world, dev)
 
 
 def run_streamed(args):
@@ -236,7 +236,7 @@ def run_streamed(args):
     N = args.N if args.N != N_DEFAULT else 1 << 26
     T = args.halo or (64 if dt == "f32" else 32)
     tdt = torch.float32 if dt == "f32" else torch.float64
-    g = torch.Generator(device=dev).manual_seed(1000 + rank)
+    g = torch.Generator(device=dev).manual_seed(hd_seed(rank))
     u0 = torch.rand(N, dtype=tdt, device=dev, generator=g)
     h = heat1d.Heat1d(N, 0.25, 0.0, 0.0, dtype="float32" if dt == "f32" else "float64", sync_mode=2, halo_steps=T)
     stream = torch.cuda.current_stream()
@@ -299,7 +299,7 @@ def run_uneven(args):
     dt = args.dtype or "f32"
     esz = 4 if dt == "f32" else 8
     tdt = torch.float32 if dt == "f32" else torch.float64
-    rods = inputs.uneven_rods(seed=1000 + rank)
+    rods = inputs.uneven_rods(seed=hd_seed(rank))
     off, total_n = heat1d.pack_offsets([r.N for r in rods])
     host = np.zeros(total_n)
     for o, r in zip(off, rods):
@@ -392,7 +392,7 @@ def run_inverse(args):
     K = args.K if args.K != K_DEFAULT else 20_000
     N = args.N if args.N != N_DEFAULT else 65536
     nr = args.rods
-    rods = inputs.inverse_problem_rods(n_rods=nr, N=N, K=K, seed=1000 + rank)
+    rods = inputs.inverse_problem_rods(n_rods=nr, N=N, K=K, seed=hd_seed(rank))
     u0 = torch.tensor(np.stack([r.u0 for r in rods]), dtype=tdt, device=dev)
     r = np.array([x.r for x in rods])
     c1 = np.array([x.c1 for x in rods])
@@ -473,7 +473,8 @@ def main():
     build.build()
     dev = torch.device("cuda", local)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    rod = inputs.sine_mode_rod(N=args.N, K=args.K, seed=1000 + rank)
+    from paper_1510_08982_gb300 import dist as hd
+    rod = inputs.sine_mode_rod(N=args.N, K=args.K, seed=hd.rod_seed(rank))
     N, K = rod.N, rod.K
     M = N - 2
     h = heat1d.Heat1d(N, rod.r, rod.c1, rod.cN, dtype="float64", segments=nsm, q=Q)
@@ -530,13 +531,10 @@ def main():
     barrier()
     clk = clocks.stop()
     h.sync()
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = hd.max_over_ranks(total, world, dev)
     ms_per_step = total / args.steps
     updates_per_step = 3 * M * K
-    value = world * updates_per_step / (ms_per_step * 1e-3)
+    value = hd.whole_job_rate(updates_per_step, ms_per_step * 1e-3, world)
     per = {name: M * K / (t / args.steps * 1e-3) for name, t in
            (("sync", t_sync), ("async", t_async), ("replay", t_replay))}
 
@@ -592,10 +590,7 @@ def main():
             e2e_step()
         barrier()
         dt = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = hd.max_over_ranks(dt, world, dev)
         tb = trace.numel()
         e2e = {"value": world * updates_per_step / dt, "unit": UNIT,
                "h2d_bytes_per_step": 3 * 8 * N + tb, "d2h_bytes_per_step": 3 * 8 * N + tb,
