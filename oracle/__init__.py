@@ -18,6 +18,9 @@ non-zero status from C):
   the switched system driven by a given delay trace.
 * ``adjoint(u0, r, c1, cN, K, u_obs, S, q, trace)`` -- FP64 gradient of
   0.5*||u(K) - u_obs||^2 with respect to u(0) and r.
+* ``sync_periodic(u0, r, K, dtype)``, ``async_periodic(u0, r, S, q, K, trace, dtype)``
+  -- Section 5.3's periodic boundary (both ends coupled), synchronous and
+  asynchronous (trace uint8[K][S][2]: S boundaries on the ring).
 * ``segments(N, S)`` -- the contiguous split of the N points into S segments.
 """
 from __future__ import annotations
@@ -67,8 +70,13 @@ def _load():
         lib.oracle_async_f64.argtypes = [i64, dbl, dbl, dbl, i64, i32, vp, i64, vp, vp]
         lib.oracle_async_f32.argtypes = [i64, flt, flt, flt, i64, i32, vp, i64, vp, vp]
         lib.oracle_adjoint_f64.argtypes = [i64, dbl, dbl, dbl, i64, i32, vp, i64, vp, vp, vp, vp, vp]
+        lib.oracle_sync_periodic_f64.argtypes = [i64, dbl, vp, i64, vp]
+        lib.oracle_sync_periodic_f32.argtypes = [i64, flt, vp, i64, vp]
+        lib.oracle_async_periodic_f64.argtypes = [i64, dbl, i64, i32, vp, i64, vp, vp]
+        lib.oracle_async_periodic_f32.argtypes = [i64, flt, i64, i32, vp, i64, vp, vp]
         for f in (lib.oracle_segments, lib.oracle_sync_f64, lib.oracle_sync_f32, lib.oracle_async_f64,
-                  lib.oracle_async_f32, lib.oracle_adjoint_f64):
+                  lib.oracle_async_f32, lib.oracle_adjoint_f64, lib.oracle_sync_periodic_f64,
+                  lib.oracle_sync_periodic_f32, lib.oracle_async_periodic_f64, lib.oracle_async_periodic_f32):
             f.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -144,3 +152,29 @@ def adjoint(u0, r, c1, cN, K, u_obs, S=1, q=1, trace=None):
                                       _ptr(tr), _ptr(u_obs), _ptr(g), ctypes.byref(gr), ctypes.byref(ls)),
            "oracle_adjoint")
     return ls.value, g, gr.value
+
+
+def sync_periodic(u0, r, K, dtype=np.float64) -> np.ndarray:
+    """u(K) of the periodic synchronous update (Section 5.3)."""
+    dt = _np_dtype(dtype)
+    u0 = np.ascontiguousarray(u0, dtype=dt)
+    out = np.empty_like(u0)
+    lib = _load()
+    fn = lib.oracle_sync_periodic_f64 if dt == np.float64 else lib.oracle_sync_periodic_f32
+    _check(fn(u0.size, float(r), _ptr(u0), int(K), _ptr(out)), "oracle_sync_periodic")
+    return out
+
+
+def async_periodic(u0, r, S, q, K, trace, dtype=np.float64) -> np.ndarray:
+    """u(K) of the periodic asynchronous update driven by ``trace``
+    (uint8, shape (K, S, 2) or flat)."""
+    dt = _np_dtype(dtype)
+    u0 = np.ascontiguousarray(u0, dtype=dt)
+    out = np.empty_like(u0)
+    tr = np.ascontiguousarray(trace, dtype=np.uint8).reshape(-1)
+    if tr.size != int(K) * int(S) * 2:
+        raise ValueError("trace has %d entries, expected K*S*2 = %d" % (tr.size, int(K) * int(S) * 2))
+    lib = _load()
+    fn = lib.oracle_async_periodic_f64 if dt == np.float64 else lib.oracle_async_periodic_f32
+    _check(fn(u0.size, float(r), int(S), int(q), _ptr(u0), int(K), _ptr(tr), _ptr(out)), "oracle_async_periodic")
+    return out

@@ -82,3 +82,71 @@ int SUF(oracle_async)(int64_t N, REAL r, REAL c1, REAL cN, int64_t S, int q, con
   free(hist);
   return ORACLE_OK;
 }
+
+/* Periodic boundary, Section 5.3: the two end points are updated too, each
+ * with the other as its outer neighbour (u_1 uses u_N, u_N uses u_1), so
+ * every point i uses (i-1) mod N and (i+1) mod N.  Synchronous form. */
+int SUF(oracle_sync_periodic)(int64_t N, REAL r, const REAL* u0, int64_t K, REAL* out) {
+  if (N < 3 || K < 0 || !u0 || !out) return ORACLE_EINVAL;
+  REAL* a = (REAL*)malloc(sizeof(REAL) * (size_t)N);
+  REAL* b = (REAL*)malloc(sizeof(REAL) * (size_t)N);
+  if (!a || !b) { free(a); free(b); return ORACLE_ENOMEM; }
+  memcpy(a, u0, sizeof(REAL) * (size_t)N);
+  for (int64_t k = 0; k < K; ++k) {
+    for (int64_t i = 0; i < N; ++i) {
+      REAL uL = a[(i + N - 1) % N], u = a[i], uR = a[(i + 1) % N];
+      b[i] = FMA(r, (uR - (REAL)2 * u) + uL, u);
+    }
+    REAL* t = a; a = b; b = t;
+  }
+  memcpy(out, a, sizeof(REAL) * (size_t)N);
+  free(a);
+  free(b);
+  return ORACLE_OK;
+}
+
+/* Periodic boundary, asynchronous form (Section 5.3 with Section 3's
+ * Eq. (eqn:async)): S >= 2 segments on a ring; boundary b joins segment b and
+ * segment (b+1) mod S, so there are S boundaries and the trace is
+ * uint8[K][S][2] (side 0: segment b reads its right neighbour, side 1:
+ * segment (b+1) mod S reads its left neighbour).  Same history scheme as
+ * oracle_async. */
+int SUF(oracle_async_periodic)(int64_t N, REAL r, int64_t S, int q, const REAL* u0, int64_t K,
+                               const uint8_t* trace, REAL* out) {
+  if (N < 3 || K < 0 || S < 2 || S > N || q < 1 || q > 255 || !u0 || !out || (K > 0 && !trace))
+    return ORACLE_EINVAL;
+  for (int64_t j = 0; j < K * S * 2; ++j)
+    if (trace[j] >= q) return ORACLE_ETRACE;
+  int64_t Q = (int64_t)q + 1;
+  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S + 1));
+  int64_t* seg = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+  REAL* hist = (REAL*)malloc(sizeof(REAL) * (size_t)N * (size_t)Q);
+  if (!off || !seg || !hist) { free(off); free(seg); free(hist); return ORACLE_ENOMEM; }
+  oracle_segments(N, S, off);
+  for (int64_t s = 0; s < S; ++s)
+    for (int64_t i = off[s]; i < off[s + 1]; ++i) seg[i] = s;
+#define H(t, i) hist[(size_t)((t) % Q) * (size_t)N + (size_t)(i)]
+  for (int64_t i = 0; i < N; ++i) H(0, i) = u0[i];
+  for (int64_t k = 0; k < K; ++k) {
+    for (int64_t i = 0; i < N; ++i) {
+      int64_t il = (i + N - 1) % N, ir = (i + 1) % N;
+      int64_t tL = k, tR = k;
+      if (seg[il] != seg[i]) { /* left read crosses boundary seg[il] (side 1) */
+        int64_t d = trace[(k * S + seg[il]) * 2 + 1];
+        tL = k - (d < k ? d : k);
+      }
+      if (seg[ir] != seg[i]) { /* right read crosses boundary seg[i] (side 0) */
+        int64_t d = trace[(k * S + seg[i]) * 2 + 0];
+        tR = k - (d < k ? d : k);
+      }
+      REAL uL = H(tL, il), u = H(k, i), uR = H(tR, ir);
+      H(k + 1, i) = FMA(r, (uR - (REAL)2 * u) + uL, u);
+    }
+  }
+  for (int64_t i = 0; i < N; ++i) out[i] = H(K, i);
+#undef H
+  free(off);
+  free(seg);
+  free(hist);
+  return ORACLE_OK;
+}

@@ -56,6 +56,14 @@ def delay_trace(K: int, S: int, q: int, seed: int = 0) -> np.ndarray:
     return d.astype(np.uint8).reshape(K, S - 1, 2)
 
 
+def periodic_delay_trace(K: int, S: int, q: int, seed: int = 0) -> np.ndarray:
+    """Delays for the periodic ring of S segments (S boundaries): shape
+    (K, S, 2), the j-th SplitMix64 output with j = (k*S + b)*2 + s, mod q."""
+    j = np.arange(K * S * 2, dtype=np.uint64)
+    d = splitmix64(seed, j) % np.uint64(q)
+    return d.astype(np.uint8).reshape(K, S, 2)
+
+
 def sine_sum(N: int, modes, amps) -> np.ndarray:
     """sum_j amps[j] * sin(modes[j] * pi * x_i), float64."""
     x = grid_x(N)

@@ -158,3 +158,53 @@ def brute_adjoint_float(u0, r, c1, cN, S, q, trace, u_obs):
     g[0] = 0.0
     g[-1] = 0.0
     return loss, g, gr
+
+
+# ----------------------------------------------------------------------------- periodic boundary
+
+
+def periodic_matrix_fraction(N, r):
+    """Circulant matrix of the periodic update (Section 5.3)."""
+    r = _frac(r)
+    A = [[Fraction(0)] * N for _ in range(N)]
+    for i in range(N):
+        A[i][i] += 1 - 2 * r
+        A[i][(i - 1) % N] += r
+        A[i][(i + 1) % N] += r
+    return A
+
+
+def brute_sync_periodic_fraction(u0, r, K):
+    u = [_frac(v) for v in u0]
+    A = periodic_matrix_fraction(len(u), r)
+    for _ in range(K):
+        u = matvec(A, u)
+    return u
+
+
+def async_periodic_step_matrix(N, r, S, q, dk):
+    """Block matrix for one periodic asynchronous step; dk has shape (S, 2):
+    boundary b joins segment b and (b+1) mod S."""
+    r = _frac(r)
+    seg = segment_of(N, S)
+    M = [[Fraction(0)] * (q * N) for _ in range(q * N)]
+    for i in range(N):
+        il, ir = (i - 1) % N, (i + 1) % N
+        jl = int(dk[seg[il]][1]) if seg[il] != seg[i] else 0
+        jr = int(dk[seg[i]][0]) if seg[ir] != seg[i] else 0
+        M[i][i] += 1 - 2 * r
+        M[i][jl * N + il] += r
+        M[i][jr * N + ir] += r
+    for j in range(1, q):
+        for i in range(N):
+            M[j * N + i][(j - 1) * N + i] = Fraction(1)
+    return M
+
+
+def brute_async_periodic_fraction(u0, r, S, q, trace):
+    N = len(u0)
+    z = [_frac(v) for v in u0] * q
+    trace = np.asarray(trace)
+    for k in range(trace.shape[0]):
+        z = matvec(async_periodic_step_matrix(N, r, S, q, trace[k]), z)
+    return z[:N]
