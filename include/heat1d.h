@@ -76,7 +76,12 @@ typedef struct heat1d_opts {
                             segment in registers), 2 streamed (temporal blocking through HBM:
                             tiles of block_threads * elems_per_thread points, halo_steps steps
                             per pass).  Automatic picks on-chip when every segment fits one CTA. */
-  int32_t reserved[6];
+  int32_t boundary;      /* 0: Dirichlet ends (Section 2).  1: periodic (Section 5.3): the two end
+                            points are updated too, each with the other as its outer neighbour;
+                            c1 and cN are then unused.  Periodic runs are on-chip synchronous runs
+                            and asynchronous runs with S >= 2 (the ring has S boundaries, so a
+                            periodic trace is uint8[K][S][2]). */
+  int32_t reserved[5];
 } heat1d_opts;
 
 /* Fills *o with the defaults (every field 0 except stall_segment = -1). */
@@ -135,7 +140,7 @@ int heat1d_run_sync(heat1d_t h, int64_t K);
  * complete when heat1d_sync() returns. */
 int heat1d_run_async(heat1d_t h, int64_t K, uint8_t* trace_out, int trace_on_device);
 
-/* Size in bytes of a trace of K steps: K * (S-1) * 2. */
+/* Size in bytes of a trace of K steps: K * (S-1) * 2 (K * S * 2 when periodic). */
 int64_t heat1d_trace_bytes(heat1d_t h, int64_t K);
 
 /* Replay of an asynchronous run, Section 3 Eq. (eqn:async) with the delays

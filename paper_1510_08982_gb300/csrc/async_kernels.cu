@@ -179,16 +179,19 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
   if (warp >= nwc) {
     if (lane == 0) {
       real* rings = static_cast<real*>(a.rings);
+      const int sl = s > 0 ? s - 1 : (a.periodic ? a.S - 1 : -1);  // neighbours (ring when periodic)
+      const int sr = s + 1 < a.S ? s + 1 : (a.periodic ? 0 : -1);
       if (warp == nwc) {
         publish_loop<real, E>(a, sh, s);
-      } else if (warp == nwc + 1) {
-        if (s > 0)  // left neighbour's right edge
-          pull_loop<real, E>(a, sh, a.prog + static_cast<size_t>(s - 1) * kProgStride,
-                             rings + (static_cast<size_t>(s - 1) * 2 + 1) * a.R, sh.lring, &sh.lavail);
       } else {
-        if (s + 1 < a.S)  // right neighbour's left edge
-          pull_loop<real, E>(a, sh, a.prog + static_cast<size_t>(s + 1) * kProgStride,
-                             rings + (static_cast<size_t>(s + 1) * 2 + 0) * a.R, sh.rring, &sh.ravail);
+        // warp nwc+1 pulls the left neighbour's right edge, warp nwc+2 the
+        // right neighbour's left edge
+        const bool from_left = warp == nwc + 1;
+        const int nb = from_left ? sl : sr;
+        if (nb >= 0)
+          pull_loop<real, E>(a, sh, a.prog + static_cast<size_t>(nb) * kProgStride,
+                             rings + (static_cast<size_t>(nb) * 2 + (from_left ? 1 : 0)) * a.R,
+                             from_left ? sh.lring : sh.rring, from_left ? &sh.lavail : &sh.ravail);
       }
     }
     return;
@@ -203,10 +206,14 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
   const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};  // one = 1 at run time
   const real* __restrict__ uin = static_cast<const real*>(a.u_in);
   real* __restrict__ uout = static_cast<real*>(a.u_out);
-  const bool has_left = s > 0, has_right = s + 1 < S;
+  const bool periodic = a.periodic != 0;
+  const bool has_left = s > 0 || periodic, has_right = s + 1 < S || periodic;
 
   // Position p holds global point a0 - 1 + p: positions 0 and L+1 are the
-  // halos, written from the neighbours' versions before every step.
+  // halos, written from the neighbours' versions before every step.  The
+  // Dirichlet ends are points end_lo and end_hi; on the periodic ring they are
+  // moved out of reach (every point is updated).
+  const int64_t end_lo = periodic ? -2 : 0, end_hi = periodic ? N + 1 : N - 1;
   real v[E];
   unsigned fixed = 0;
   int e_first = -1, e_last = -1, e_rh = -1;  // slots of this thread holding positions 1, L (owners) and L+1
@@ -216,10 +223,10 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
     const int64_t g = a0 - 1 + p;
     real x = static_cast<real>(0);
     if (p >= 1 && p <= L) x = uin[g];
-    if (g == 0) x = c1;
-    if (g == N - 1) x = cN;
+    if (g == end_lo) x = c1;
+    if (g == end_hi) x = cN;
     v[e] = x;
-    if (p == 0 || p >= L + 1 || g <= 0 || g >= N - 1) fixed |= 1u << e;
+    if (p == 0 || p >= L + 1 || g <= end_lo || g >= end_hi) fixed |= 1u << e;
     const bool own = Win::owner(warp, lane, e, nwc);
     if (p == 1 && own) e_first = e;
     if (p == L && own) e_last = e;
@@ -248,9 +255,10 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
 
   const uint8_t* trace_in = a.trace_in;
   uint8_t* trace_out = a.trace_out;
-  const size_t tstride = static_cast<size_t>(S - 1) * 2;
-  const size_t tl = has_left ? static_cast<size_t>(s - 1) * 2 + 1 : 0;  // side 1 of boundary s-1
-  const size_t tr = static_cast<size_t>(s) * 2 + 0;                     // side 0 of boundary s
+  // S-1 boundaries (S on the periodic ring, boundary b joining b and b+1 mod S)
+  const size_t tstride = static_cast<size_t>(periodic ? S : S - 1) * 2;
+  const size_t tl = has_left ? static_cast<size_t>((s + S - 1) % S) * 2 + 1 : 0;  // side 1 of boundary s-1
+  const size_t tr = static_cast<size_t>(s) * 2 + 0;                               // side 0 of boundary s
   int dl_next = 0, dr_next = 0;
   if (trace_in && K > 0) {
     if (left_reader) dl_next = __ldg(trace_in + tl);

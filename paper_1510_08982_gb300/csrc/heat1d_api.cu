@@ -136,6 +136,9 @@ int configure(heat1d* h, const heat1d_opts& o) {
   }
   if (T < 1) T = 1;
   if (o.sync_mode < 0 || o.sync_mode > 2) return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: sync_mode must be 0, 1 or 2");
+  if (o.boundary < 0 || o.boundary > 1) return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: boundary must be 0 or 1");
+  if (o.boundary == 1 && o.sync_mode == 2)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: periodic runs are on-chip only (sync_mode 0 or 1)");
 
   // Streamed shape: 16-byte vectors, so E and the halo are multiples of
   // 16 / sizeof(real) points and every tile starts on a 16-byte boundary.
@@ -258,6 +261,7 @@ SegmentRun base_run(heat1d* h, int64_t K) {
   a.prog = h->prog;
   a.rings = h->rings;
   a.stall_segment = h->opts.stall_segment;
+  a.periodic = h->opts.boundary == 1;
   return a;
 }
 
@@ -279,7 +283,9 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   int E = 0, threads = 0;
   int rc = pick_shape(h, h->Lmax + 2, 32 * heat1d_impl::kCommWarps, true, &E, &threads);
   if (rc) return rc;
-  const size_t tbytes = static_cast<size_t>(K) * (h->S - 1) * 2;
+  const bool periodic = h->opts.boundary == 1;
+  if (periodic && h->S < 2) return fail(HEAT1D_ERR_INVAL, "periodic asynchronous runs need at least 2 segments");
+  const size_t tbytes = static_cast<size_t>(K) * (periodic ? h->S : h->S - 1) * 2;
   SegmentRun a = base_run(h, K);
   uint8_t* out_dev = nullptr;
   if (trace_out && tbytes) {
@@ -419,6 +425,10 @@ int heat1d_set_u(heat1d_t h, const void* u, int on_device) {
   if (!h || !u) return fail(HEAT1D_ERR_INVAL, "null argument");
   HEAT1D_CUDA(cudaMemcpyAsync(h->u[h->cur], u, h->esize * h->N,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  if (h->opts.boundary == 1) {  // periodic: no Dirichlet ends to force
+    if (!on_device) HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
+    return HEAT1D_OK;
+  }
   if (h->dtype == HEAT1D_F64)
     set_ends_kernel<double><<<1, 32, 0, h->stream>>>(static_cast<double*>(h->u[h->cur]), h->N, h->c1, h->cN);
   else
@@ -443,7 +453,7 @@ int heat1d_run_sync(heat1d_t h, int64_t K) {
   int E = 0, threads = 0;
   int rc = h->opts.sync_mode == 2 ? HEAT1D_ERR_INVAL : pick_shape(h, h->Lmax + 2 * h->T, 0, false, &E, &threads);
   if (rc) {
-    if (h->opts.sync_mode == 1) return rc;
+    if (h->opts.sync_mode == 1 || h->opts.boundary == 1) return rc;
     return run_streamed(h, K);
   }
   SegmentRun a = base_run(h, K);
@@ -463,7 +473,7 @@ int heat1d_run_async(heat1d_t h, int64_t K, uint8_t* trace_out, int trace_on_dev
 
 int64_t heat1d_trace_bytes(heat1d_t h, int64_t K) {
   if (!h || K < 0) return fail(HEAT1D_ERR_INVAL, "bad argument");
-  return K * (h->S - 1) * 2;
+  return K * (h->opts.boundary == 1 ? h->S : h->S - 1) * 2;
 }
 
 int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device) {
@@ -754,6 +764,7 @@ extern "C" {
 static int adjoint_handle(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device, const double* u_obs,
                           int cotangent, int64_t ckpt_every, double* grad_u0, double* grad_r, double* loss) {
   if (!h || !u_obs || !grad_u0) return fail(HEAT1D_ERR_INVAL, "heat1d_adjoint: null argument");
+  if (h->opts.boundary == 1) return fail(HEAT1D_ERR_INVAL, "heat1d_adjoint: Dirichlet ends only");
   if (K < 0) return fail(HEAT1D_ERR_INVAL, "heat1d_adjoint: K must be >= 0");
   const bool async_run = trace != nullptr && h->S > 1;
   const size_t tbytes = static_cast<size_t>(K) * (h->S - 1) * 2;

@@ -28,6 +28,7 @@ struct SegmentRun {
   double r, c1, cN;
   int* status;             // device status word (0 = healthy)
   int64_t spin_limit_ns;
+  int periodic;            // 1: periodic ring (Section 5.3), no Dirichlet ends
 
   // synchronous run
   int T;                   // halo width = steps between exchanges

@@ -71,12 +71,19 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
     const int p = Win::pos(warp, lane, e);
     const int64_t g = a0 - T + p;
     real x = static_cast<real>(0);
-    if (p < Lh && g >= 0 && g < N) x = uin[g];
-    if (g == 0) x = c1;
-    if (g == N - 1) x = cN;
+    if (a.periodic) {  // halos wrap around the ring
+      if (p < Lh) x = uin[((g % N) + N) % N];
+      if (p >= Lh) fixed |= 1u << e;
+    } else {
+      if (p < Lh && g >= 0 && g < N) x = uin[g];
+      if (g == 0) x = c1;
+      if (g == N - 1) x = cN;
+      if (p >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
+    }
     v[e] = x;
-    if (p >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
   }
+  const int sl = s > 0 ? s - 1 : (a.periodic ? a.S - 1 : -1);      // left neighbour segment
+  const int sr = s + 1 < a.S ? s + 1 : (a.periodic ? 0 : -1);       // right neighbour segment
   const int mode = tile_mode<E>(fixed);
 
   int parity = 0;
@@ -104,16 +111,16 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 
     // Reload the halos (every copy): the left neighbour's last T points, the
     // right neighbour's first T points.
-    if (s > 0) {
-      const real* left = edges + (static_cast<size_t>(epoch & 1u) * a.S + (s - 1)) * 2 * T;
+    if (sl >= 0) {
+      const real* left = edges + (static_cast<size_t>(epoch & 1u) * a.S + sl) * 2 * T;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
         if (p < T) v[e] = ld_cg(left + T + p);
       }
     }
-    if (s + 1 < a.S) {
-      const real* right = edges + (static_cast<size_t>(epoch & 1u) * a.S + (s + 1)) * 2 * T;
+    if (sr >= 0) {
+      const real* right = edges + (static_cast<size_t>(epoch & 1u) * a.S + sr) * 2 * T;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);

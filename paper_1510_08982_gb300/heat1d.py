@@ -43,7 +43,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("segments", ctypes.c_int64), ("q", ctypes.c_int32), ("halo_steps", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("elems_per_thread", ctypes.c_int32),
                 ("spin_limit_ns", ctypes.c_int64), ("stall_segment", ctypes.c_int32),
-                ("sync_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("sync_mode", ctypes.c_int32), ("boundary", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class RodSpec(ctypes.Structure):
@@ -135,7 +135,8 @@ class Heat1d:
     """One rod of N points: state, options and scratch on the current device.
 
     ``opts`` keywords: segments, q, halo_steps, block_threads,
-    elems_per_thread, spin_limit_ns, stall_segment, sync_mode (see heat1d_opts)."""
+    elems_per_thread, spin_limit_ns, stall_segment, sync_mode, boundary (see
+    heat1d_opts; boundary=1 is the periodic ring of Section 5.3)."""
 
     def __init__(self, N, r, c1, cN, dtype="float64", **opts):
         torch = _torch()
@@ -234,7 +235,8 @@ class Heat1d:
 
     def new_trace(self, K, device=True):
         torch = _torch()
-        shape = (int(K), max(self.S - 1, 0), 2)
+        periodic = self.get_opts().get("boundary", 0) == 1
+        shape = (int(K), self.S if periodic else max(self.S - 1, 0), 2)
         if device:
             return torch.empty(shape, dtype=torch.uint8, device="cuda")
         return np.empty(shape, dtype=np.uint8)
