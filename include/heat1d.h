@@ -102,6 +102,16 @@ const char* heat1d_last_error(void);
 /* Sets the CUDA stream (a cudaStream_t; NULL is the legacy default stream). */
 int heat1d_set_stream(heat1d_t h, void* stream);
 
+/* Records snapshots of the state during the next runs (the paper keeps the
+ * whole history in its array v, Section 4; here it is optional and strided):
+ * row j of buf (device, rows x N values of the handle's dtype) receives the
+ * state at step j*every of each run, row 0 the state the run starts from.
+ * A run of K steps needs K/every + 1 <= rows (else HEAT1D_ERR_INVAL).
+ * Synchronous runs need every to be a multiple of the halo depth and must be
+ * on-chip.  buf = NULL stops recording.  The buffer stays owned by the
+ * caller. */
+int heat1d_set_snapshots(heat1d_t h, void* buf, int64_t every, int64_t rows);
+
 /* Replaces the options.  Validates them against N; the segment split and the
  * scratch buffers are rebuilt.  HEAT1D_ERR_INVAL if out of range. */
 int heat1d_set_opts(heat1d_t h, const heat1d_opts* o);

@@ -236,6 +236,14 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
       e_rh = e;
   }
   const int mode = tile_mode<E>(fixed);
+  real* snap = static_cast<real*>(a.snap);
+  if (snap) {  // row 0: the state at step 0
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = Win::pos(warp, lane, e);
+      if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) snap[a0 - 1 + p] = v[e];
+    }
+  }
   const bool left_reader = has_left && warp == 0 && lane == 0;  // position 0 is (warp 0, lane 0, slot 0)
   const bool right_reader = has_right && e_rh >= 0;
 
@@ -294,6 +302,14 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
     }
     warp_step_any<real, E>(mode, v, fixed, coef);
     const int ver = k + 1, j = ver & (a.R - 1);
+    if (snap && ver % a.snap_every == 0) {  // owners record the state at step ver
+      real* row = snap + static_cast<size_t>(ver / a.snap_every) * N;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) row[a0 - 1 + p] = v[e];
+      }
+    }
     if (e_first >= 0) {
 #pragma unroll
       for (int e = 0; e < E; ++e)

@@ -77,6 +77,8 @@ struct heat1d {
   void* ctl = nullptr;  // [0]: grid barrier counter, [32]: status word (separate lines)
   uint8_t* d_trace = nullptr;
   size_t d_trace_bytes = 0;
+  void* snap = nullptr;  // caller's snapshot buffer (device) or null
+  int64_t snap_every = 0, snap_rows = 0;
 
   unsigned* barrier() { return static_cast<unsigned*>(ctl); }
   int* status() { return static_cast<int*>(ctl) + 32; }
@@ -262,6 +264,10 @@ SegmentRun base_run(heat1d* h, int64_t K) {
   a.rings = h->rings;
   a.stall_segment = h->opts.stall_segment;
   a.periodic = h->opts.boundary == 1;
+  if (h->snap && h->snap_every > 0 && K / h->snap_every + 1 <= h->snap_rows) {
+    a.snap = h->snap;
+    a.snap_every = h->snap_every;
+  }
   return a;
 }
 
@@ -283,6 +289,8 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   int E = 0, threads = 0;
   int rc = pick_shape(h, h->Lmax + 2, 32 * heat1d_impl::kCommWarps, true, &E, &threads);
   if (rc) return rc;
+  if (h->snap && K / h->snap_every + 1 > h->snap_rows)
+    return fail(HEAT1D_ERR_INVAL, "snapshot buffer holds fewer rows than K/every + 1");
   const bool periodic = h->opts.boundary == 1;
   if (periodic && h->S < 2) return fail(HEAT1D_ERR_INVAL, "periodic asynchronous runs need at least 2 segments");
   const size_t tbytes = static_cast<size_t>(K) * (periodic ? h->S : h->S - 1) * 2;
@@ -394,6 +402,15 @@ void heat1d_destroy(heat1d_t h) {
   delete h;
 }
 
+int heat1d_set_snapshots(heat1d_t h, void* buf, int64_t every, int64_t rows) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  if (buf && (every < 1 || rows < 1)) return fail(HEAT1D_ERR_INVAL, "heat1d_set_snapshots: every and rows must be >= 1");
+  h->snap = buf;
+  h->snap_every = buf ? every : 0;
+  h->snap_rows = buf ? rows : 0;
+  return HEAT1D_OK;
+}
+
 int heat1d_set_stream(heat1d_t h, void* stream) {
   if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
   h->stream = static_cast<cudaStream_t>(stream);
@@ -454,7 +471,14 @@ int heat1d_run_sync(heat1d_t h, int64_t K) {
   int rc = h->opts.sync_mode == 2 ? HEAT1D_ERR_INVAL : pick_shape(h, h->Lmax + 2 * h->T, 0, false, &E, &threads);
   if (rc) {
     if (h->opts.sync_mode == 1 || h->opts.boundary == 1) return rc;
+    if (h->snap) return fail(HEAT1D_ERR_INVAL, "snapshots are recorded by on-chip runs only");
     return run_streamed(h, K);
+  }
+  if (h->snap) {
+    if (K / h->snap_every + 1 > h->snap_rows)
+      return fail(HEAT1D_ERR_INVAL, "snapshot buffer holds fewer rows than K/every + 1");
+    if (h->snap_every % h->T != 0)
+      return fail(HEAT1D_ERR_INVAL, "synchronous snapshots need every to be a multiple of the halo depth");
   }
   SegmentRun a = base_run(h, K);
   HEAT1D_CUDA(cudaMemsetAsync(h->barrier(), 0, sizeof(unsigned), h->stream));

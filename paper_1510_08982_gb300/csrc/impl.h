@@ -29,6 +29,8 @@ struct SegmentRun {
   int* status;             // device status word (0 = healthy)
   int64_t spin_limit_ns;
   int periodic;            // 1: periodic ring (Section 5.3), no Dirichlet ends
+  void* snap;              // device [K/snap_every + 1][N] states at steps j*snap_every, or null
+  int64_t snap_every;
 
   // synchronous run
   int T;                   // halo width = steps between exchanges

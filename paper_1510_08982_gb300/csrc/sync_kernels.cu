@@ -86,11 +86,26 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
   const int sr = s + 1 < a.S ? s + 1 : (a.periodic ? 0 : -1);       // right neighbour segment
   const int mode = tile_mode<E>(fixed);
 
+  if (a.snap) {  // row 0: the state at step 0
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = Win::pos(warp, lane, e);
+      if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) static_cast<real*>(a.snap)[a0 + (p - T)] = v[e];
+    }
+  }
   int parity = 0;
   unsigned epoch = 0;
   for (int64_t k0 = 0; k0 < a.K; k0 += T) {
     const int tb = static_cast<int>(std::min<int64_t>(T, a.K - k0));
     warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
+    if (a.snap && (k0 + tb) % a.snap_every == 0) {  // owners record the state at step k0+tb
+      real* row = static_cast<real*>(a.snap) + static_cast<size_t>((k0 + tb) / a.snap_every) * N;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) row[a0 + (p - T)] = v[e];
+      }
+    }
     if (k0 + tb >= a.K) break;
 
     // Publish the first T and the last T points of the segment.

@@ -26,7 +26,7 @@ STATUS_NAMES = {OK: "HEAT1D_OK", ERR_INVAL: "HEAT1D_ERR_INVAL", ERR_CUDA: "HEAT1
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_last_error", "heat1d_set_stream",
-           "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
+           "heat1d_set_snapshots", "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
            "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync",
            "heat1d_batch_create", "heat1d_batch_run", "heat1d_batch_sync", "heat1d_batch_describe",
            "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_adjoint", "heat1d_vjp",
@@ -71,6 +71,7 @@ def load():
         "heat1d_destroy": (None, [vp]),
         "heat1d_last_error": (ctypes.c_char_p, []),
         "heat1d_set_stream": (i32, [vp, vp]),
+        "heat1d_set_snapshots": (i32, [vp, vp, i64, i64]),
         "heat1d_set_opts": (i32, [vp, ctypes.POINTER(Opts)]),
         "heat1d_get_opts": (i32, [vp, ctypes.POINTER(Opts)]),
         "heat1d_num_segments": (i64, [vp, vp]),
@@ -182,6 +183,18 @@ class Heat1d:
                 raise TypeError("unknown option %r" % k)
             setattr(o, k, int(v))
         _check(self.lib.heat1d_set_opts(self.h, ctypes.byref(o)))
+
+    def set_snapshots(self, buf=None, every=1):
+        """Record the state every `every` steps of the following runs into
+        buf (CUDA tensor of shape (rows, N), the handle's dtype); None stops."""
+        if buf is None:
+            _check(self.lib.heat1d_set_snapshots(self.h, None, 0, 0))
+            self._snap = None
+            return
+        if not buf.is_cuda or buf.dtype != self.torch_dtype or buf.dim() != 2 or buf.shape[1] != self.N:
+            raise ValueError("snapshot buffer must be a CUDA tensor (rows, N) of the handle's dtype")
+        _check(self.lib.heat1d_set_snapshots(self.h, ctypes.c_void_p(buf.data_ptr()), int(every), buf.shape[0]))
+        self._snap = buf
 
     def get_opts(self) -> dict:
         o = Opts()

@@ -1,0 +1,55 @@
+"""The paper's run (Section 5) through the library: snapshots bit for bit
+against the oracle's replay of each recorded trace, the ensemble statistics of
+Fig. 3 / Fig. 6 (stable, converging to the unique Dirichlet steady state;
+spreading on the periodic ring)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_08982_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    import torch  # noqa: F401
+    from paper_1510_08982_gb300 import build, experiments
+    build.build()
+    return experiments
+
+
+def test_spatio_temporal_snapshots_match_oracle(X):
+    K = 300
+    a, s, tr = X.spatio_temporal(K=K)
+    rod = inputs.paper_rod(N=100, K=K)
+    for k in (0, 1, 7, 150, 300):
+        assert np.array_equal(a[k], oracle.async_replay(rod.u0, 0.5, 1.0, 0.0, 100, 3, k, tr[:k]))
+        assert np.array_equal(s[k], oracle.sync(rod.u0, 0.5, 1.0, 0.0, k))
+
+
+def test_dirichlet_ensemble_is_stable_and_converges(X):
+    """Fig. 3: every trajectory stays bounded; far enough out all reach the
+    unique steady state (the line from 1 to 0)."""
+    K = 100000
+    ens = X.ensemble(runs=4, K=K, keep_traces=True)
+    x = inputs.grid_x(100)
+    target = np.linalg.norm(1.0 - x)
+    assert np.all(ens["norms"] <= ens["norms"][:, :1] + 1e-12)   # max principle: ||u|| never grows past u(0)'s bound
+    assert np.abs(ens["norms"][:, -1] - target).max() < 1e-9
+    assert abs(ens["sync_norm"][-1] - target) < 1e-9
+    assert ens["delay_histogram"].sum() == 4 * K * 99 * 2
+
+
+def test_periodic_ensemble_spreads(X):
+    """Fig. 6: on the periodic ring the asynchronous runs do not share one
+    limit (the sum drifts with the delays), while the synchronous run keeps
+    the mean."""
+    K = 5000
+    ens = X.ensemble(runs=3, K=K, periodic=True)
+    rod = inputs.paper_rod(N=100)
+    assert abs(np.linalg.norm(np.full(100, rod.u0.mean())) - ens["sync_norm"][-1]) < 0.06
+    if ens["delay_histogram"][1:].sum() > 0:
+        assert np.ptp(ens["norms"][:, -1]) > 0
