@@ -11,6 +11,13 @@ paper does not state the number of steps; 1000 is used by default.
   step of 300 independent free-running asynchronous runs, their mean, the
   synchronous trajectory, and the histogram of the delays the GPU recorded.
 
+* ``delay_statistics`` / ``decay_rates`` -- the delays the GPU recorded
+  (overall and per boundary side, mean, lag-1 autocorrelation) and the
+  decay rate of ||u(k) - u_ss|| from the fundamental mode, asynchronous runs
+  next to the synchronous spectral radius 1 - 4 r sin^2(pi/(2(N-1))).  The companion
+  paper's theory of these rates is not available here, so nothing is
+  compared against a predicted value.
+
 ``python -m paper_1510_08982_gb300.experiments --out run.npz [--periodic]``
 writes the arrays to an .npz file.  Every run is a run of the library (no
 CPU path); each asynchronous run's trace is kept so that it can be replayed.
@@ -86,6 +93,61 @@ def ensemble(runs: int = 300, K: int = 1000, q: int = 3, periodic: bool = False,
     return out
 
 
+def delay_statistics(trace, q: int):
+    """trace: uint8 (K, B, 2).  Histogram, mean, per-side histograms and the
+    lag-1 autocorrelation of each boundary side's delay sequence (averaged)."""
+    t = np.asarray(trace, dtype=np.float64)
+    hist = np.bincount(np.asarray(trace).reshape(-1), minlength=q)[:q]
+    per_side = [np.bincount(np.asarray(trace)[:, :, s].reshape(-1), minlength=q)[:q] for s in (0, 1)]
+    x = t - t.mean(axis=0, keepdims=True)
+    num = (x[1:] * x[:-1]).sum(axis=0)
+    den = (x * x).sum(axis=0)
+    ac = float(np.mean(num[den > 0] / den[den > 0])) if np.any(den > 0) else 0.0
+    return {"histogram": hist, "mean": float(t.mean()), "per_side": np.stack(per_side), "lag1_autocorrelation": ac}
+
+
+def decay_rates(K: int = 20000, runs: int = 4, q: int = 3, dtype: str = "float64"):
+    """Per-step decay factor of ||u(k) - u_ss||_2 (fitted on the last half of
+    the run) for `runs` asynchronous runs and the synchronous run, from the
+    fundamental mode u(0) = u_ss + sin(pi x) on the Section 5 rod.  The
+    synchronous factor is then lambda_1 = 1 - 4 r sin^2(pi / (2 (N - 1)))
+    from the first step (the paper's own u(0) has no fundamental component,
+    so its error decays through a mix of modes instead)."""
+    import torch
+    x = inputs.grid_x(N_PAPER)
+    uss_np = 1.0 - x
+    u0 = uss_np + np.sin(np.pi * x)
+    uss = torch.tensor(uss_np, dtype=torch.float64, device="cuda")
+    tdt = torch.float64 if dtype == "float64" else torch.float32
+    every = max(1, K // 2000)
+    rows = K // every + 1
+
+    def rate(snaps):
+        e = torch.linalg.vector_norm(snaps.double() - uss, dim=1).cpu().numpy()
+        k = np.arange(rows) * every
+        half = rows // 2
+        good = e[half:] > 0
+        slope = np.polyfit(k[half:][good], np.log(e[half:][good]), 1)[0]
+        return float(np.exp(slope))
+
+    rates = []
+    with _handle(False, q, dtype) as h:
+        snaps = torch.empty((rows, N_PAPER), dtype=tdt, device="cuda")
+        h.set_snapshots(snaps, every=every)
+        for _ in range(runs):
+            h.set_u(u0)
+            h.run_async(K)
+            h.sync()
+            rates.append(rate(snaps))
+        h.set_u(u0)
+        h.run_sync(K)
+        h.sync()
+        sync_rate = rate(snaps)
+        h.set_snapshots(None)
+    lam1 = 1.0 - 4.0 * R_PAPER * np.sin(np.pi / (2.0 * (N_PAPER - 1))) ** 2
+    return {"async_rates": np.array(rates), "sync_rate": sync_rate, "sync_spectral_radius": lam1}
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     p.add_argument("--out", required=True)
@@ -96,9 +158,21 @@ def main(argv=None):
     args = p.parse_args(argv)
     a, s, tr = spatio_temporal(args.K, args.q, args.periodic)
     ens = ensemble(args.runs, args.K, args.q, args.periodic)
-    np.savez_compressed(args.out, async_states=a, sync_states=s, async_trace=tr, **ens)
-    print("wrote %s: %d runs x %d steps, delay histogram %s" % (args.out, args.runs, args.K,
-                                                                ens["delay_histogram"].tolist()))
+    stats = delay_statistics(tr, args.q)
+    extra = {}
+    if not args.periodic:
+        dr = decay_rates(q=args.q)
+        extra = {"async_decay_rates": dr["async_rates"], "sync_decay_rate": dr["sync_rate"],
+                 "sync_spectral_radius": dr["sync_spectral_radius"]}
+    np.savez_compressed(args.out, async_states=a, sync_states=s, async_trace=tr,
+                        delay_mean=stats["mean"], delay_per_side=stats["per_side"],
+                        delay_lag1_autocorrelation=stats["lag1_autocorrelation"], **ens, **extra)
+    print("wrote %s: %d runs x %d steps, delay histogram %s, mean delay %.3f, lag-1 autocorrelation %.3f%s"
+          % (args.out, args.runs, args.K, ens["delay_histogram"].tolist(), stats["mean"],
+             stats["lag1_autocorrelation"],
+             "" if args.periodic else ", decay per step: sync %.6f (lambda_1 %.6f), async %s"
+             % (extra["sync_decay_rate"], extra["sync_spectral_radius"],
+                np.round(extra["async_decay_rates"], 6).tolist())))
 
 
 if __name__ == "__main__":

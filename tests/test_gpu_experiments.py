@@ -53,3 +53,14 @@ def test_periodic_ensemble_spreads(X):
     assert abs(np.linalg.norm(np.full(100, rod.u0.mean())) - ens["sync_norm"][-1]) < 0.06
     if ens["delay_histogram"][1:].sum() > 0:
         assert np.ptp(ens["norms"][:, -1]) > 0
+
+
+def test_decay_rates_and_delay_statistics(X):
+    """From the fundamental mode the synchronous decay factor is the spectral
+    radius lambda_1 (closed form); the asynchronous runs still decay (< 1).  Their value
+    against the companion paper's theory is not pinned here."""
+    dr = X.decay_rates(K=20000, runs=2)
+    assert abs(dr["sync_rate"] - dr["sync_spectral_radius"]) < 1e-9
+    assert np.all(dr["async_rates"] < 1.0)
+    st = X.delay_statistics(np.array([[[0, 2]], [[1, 2]], [[2, 0]]], dtype=np.uint8), 3)
+    assert st["histogram"].tolist() == [2, 1, 3] and abs(st["mean"] - 7 / 6) < 1e-12
