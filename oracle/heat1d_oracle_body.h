@@ -150,3 +150,86 @@ int SUF(oracle_async_periodic)(int64_t N, REAL r, int64_t S, int q, const REAL* 
   free(hist);
   return ORACLE_OK;
 }
+
+/* Asynchronous run with temporal blocking: the bounded-delay model of
+ * Section 3 applied to blocks of T steps instead of single steps (the paper's
+ * PE exchanges one value per step; here a PE exchanges a strip of T edge
+ * values once per T steps).  This is a different switched system from
+ * Eq. (eqn:async); it is defined as follows.
+ *
+ *  - Time is cut into blocks of T steps; block b runs from step bT to step
+ *    bT + tb, tb = min(T, K - bT).  W_b denotes the full state at step bT.
+ *  - Segment s = [lo, hi) starts block b from a tile covering
+ *    [lo - T, hi + T) clipped to [0, N): its own points from W_b, the T points
+ *    left of lo from W_{b - dL}, the T points right of hi from W_{b - dR},
+ *    where dL = trace[(b(S-1) + s-1)*2 + 1] and dR = trace[(b(S-1) + s)*2 + 0]
+ *    (the same sides as Eq. (eqn:async)'s trace), each clamped to b.
+ *  - It sweeps the tile tb times with the Section 2 update (the tile's two
+ *    outermost points and the Dirichlet ends are held), and its own points
+ *    after the last sweep are its part of W_{b+1}.  Own points lie at least
+ *    T >= tb points inside the tile, so no held tile edge reaches them.
+ *  - A halo must lie within the adjacent segment: T may not exceed the
+ *    shortest segment when S > 1.
+ *
+ * With every delay 0 this is the synchronous run; with T = 1 it is
+ * Eq. (eqn:async) with the same trace.  The last q+1 block states are kept
+ * (block b reads W_{b-q+1} .. W_b and writes W_{b+1} into the slot of
+ * W_{b-q}).  trace holds ceil(K/T)*(S-1)*2 entries. */
+int SUF(oracle_async_blocked)(int64_t N, REAL r, REAL c1, REAL cN, int64_t S, int q, int64_t T,
+                              const REAL* u0, int64_t K, const uint8_t* trace, REAL* out) {
+  if (N < 3 || K < 0 || S < 1 || S > N || q < 1 || q > 255 || T < 1 || !u0 || !out) return ORACLE_EINVAL;
+  int64_t nb = (K + T - 1) / T;
+  if (S > 1 && T > N / S) return ORACLE_EINVAL; /* N / S is the shortest segment */
+  if (S > 1 && nb > 0 && !trace) return ORACLE_EINVAL;
+  for (int64_t j = 0; S > 1 && j < nb * (S - 1) * 2; ++j)
+    if (trace[j] >= q) return ORACLE_ETRACE;
+  int64_t Q = (int64_t)q + 1;
+  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S + 1));
+  REAL* W = (REAL*)malloc(sizeof(REAL) * (size_t)N * (size_t)Q);
+  REAL* ta = (REAL*)malloc(sizeof(REAL) * (size_t)N);
+  REAL* tb_ = (REAL*)malloc(sizeof(REAL) * (size_t)N);
+  if (!off || !W || !ta || !tb_) { free(off); free(W); free(ta); free(tb_); return ORACLE_ENOMEM; }
+  oracle_segments(N, S, off);
+#define WB(b, i) W[(size_t)((b) % Q) * (size_t)N + (size_t)(i)]
+  for (int64_t i = 0; i < N; ++i) WB(0, i) = u0[i];
+  WB(0, 0) = c1;
+  WB(0, N - 1) = cN;
+  for (int64_t b = 0; b < nb; ++b) {
+    int64_t steps = K - b * T < T ? K - b * T : T;
+    for (int64_t s = 0; s < S; ++s) {
+      int64_t lo = off[s], hi = off[s + 1];
+      int64_t tlo = lo - T > 0 ? lo - T : 0, thi = hi + T < N ? hi + T : N; /* tile [tlo, thi) */
+      int64_t bl = b, br = b;
+      if (s > 0) {
+        int64_t d = trace[(b * (S - 1) + (s - 1)) * 2 + 1];
+        bl = b - (d < b ? d : b);
+      }
+      if (s + 1 < S) {
+        int64_t d = trace[(b * (S - 1) + s) * 2 + 0];
+        br = b - (d < b ? d : b);
+      }
+      for (int64_t i = tlo; i < thi; ++i) ta[i] = i < lo ? WB(bl, i) : (i >= hi ? WB(br, i) : WB(b, i));
+      REAL* x = ta;
+      REAL* y = tb_;
+      for (int64_t j = 0; j < steps; ++j) {
+        for (int64_t i = tlo; i < thi; ++i) {
+          if (i == tlo || i == thi - 1 || i == 0 || i == N - 1) {
+            y[i] = x[i]; /* held: a tile edge or a Dirichlet end */
+          } else {
+            REAL uL = x[i - 1], u = x[i], uR = x[i + 1];
+            y[i] = FMA(r, (uR - (REAL)2 * u) + uL, u);
+          }
+        }
+        REAL* t = x; x = y; y = t;
+      }
+      for (int64_t i = lo; i < hi; ++i) WB(b + 1, i) = x[i];
+    }
+  }
+  for (int64_t i = 0; i < N; ++i) out[i] = WB(nb, i);
+#undef WB
+  free(off);
+  free(W);
+  free(ta);
+  free(tb_);
+  return ORACLE_OK;
+}

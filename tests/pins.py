@@ -208,3 +208,48 @@ def brute_async_periodic_fraction(u0, r, S, q, trace):
     for k in range(trace.shape[0]):
         z = matvec(async_periodic_step_matrix(N, r, S, q, trace[k]), z)
     return z[:N]
+
+
+# ----------------------------------------------------------------------------- asynchronous, temporally blocked
+
+
+def brute_async_blocked_fraction(u0, r, c1, cN, S, q, T, K, trace):
+    """Exact state after K steps of the blocked asynchronous run, written as
+    matrix powers on whole vectors: for block b and segment s the composite
+    vector z = W_b, with the T points left of the segment taken from W_{b-dL}
+    and the T points right of it from W_{b-dR}, is multiplied by the
+    synchronous matrix tb times; the segment's own entries of the product are
+    its part of W_{b+1}.  A's rows for the segment's own points reach at most
+    tb <= T points out, so the whole-vector product needs no tile edges.
+    trace: (ceil(K/T), S-1, 2), delays already clamped to b."""
+    N = len(u0)
+    u = [_frac(v) for v in u0]
+    u[0] = _frac(c1)
+    u[-1] = _frac(cN)
+    A = sync_matrix_fraction(N, r)
+    off = [0]
+    base, extra = divmod(N, S)
+    for s in range(S):
+        off.append(off[-1] + base + (1 if s < extra else 0))
+    W = [u]
+    trace = np.asarray(trace)
+    nb = (K + T - 1) // T
+    for b in range(nb):
+        tb = min(T, K - b * T)
+        new = list(W[b])
+        for s in range(S):
+            lo, hi = off[s], off[s + 1]
+            z = list(W[b])
+            if s > 0:
+                bl = b - int(trace[b][s - 1][1])
+                for i in range(max(lo - T, 0), lo):
+                    z[i] = W[bl][i]
+            if s + 1 < S:
+                br = b - int(trace[b][s][0])
+                for i in range(hi, min(hi + T, N)):
+                    z[i] = W[br][i]
+            for _ in range(tb):
+                z = matvec(A, z)
+            new[lo:hi] = z[lo:hi]
+        W.append(new)
+    return W[nb]

@@ -1,0 +1,113 @@
+"""Pins of the oracle's asynchronous run with temporal blocking.
+
+The model (blocks of T steps; each segment advances a block on its own points
+plus T-wide halo strips taken from its neighbours up to q-1 blocks old) is
+defined in oracle/heat1d_oracle_body.h.  It is checked here against what fixes
+it independently: the synchronous run (all delays 0), Eq. (eqn:async) (T = 1),
+an exact rational restatement as whole-vector matrix powers (tests/pins.py),
+the maximum principle and the unique steady state.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_08982_gb300 import inputs
+from tests import pins
+
+
+def nblocks(K, T):
+    return (K + T - 1) // T
+
+
+@pytest.mark.parametrize("T,K", [(1, 300), (4, 300), (7, 300), (64, 1000), (128, 1000), (5, 3)])
+def test_blocked_zero_trace_equals_sync_bitwise(T, K):
+    """All strips current (d = 0) is the synchronous run, bit for bit, in both
+    precisions and for a ragged last block."""
+    rod = inputs.small_rod(K=K)
+    tr = np.zeros((nblocks(K, T), 7, 2), dtype=np.uint8)
+    for dt in (np.float64, np.float32):
+        a = oracle.async_blocked(rod.u0, rod.r, rod.c1, rod.cN, 8, 3, T, K, tr, dtype=dt)
+        b = oracle.sync(rod.u0, rod.r, rod.c1, rod.cN, K, dtype=dt)
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_blocked_T1_is_eqn_async(seed):
+    """Blocks of one step are Eq. (eqn:async) with the same trace."""
+    rod = inputs.small_rod(K=500)
+    tr = inputs.delay_trace(rod.K, 8, 3, seed=seed)
+    for dt in (np.float64, np.float32):
+        a = oracle.async_blocked(rod.u0, rod.r, rod.c1, rod.cN, 8, 3, 1, rod.K, tr, dtype=dt)
+        b = oracle.async_replay(rod.u0, rod.r, rod.c1, rod.cN, 8, 3, rod.K, tr, dtype=dt)
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("N,S,q,T,K,seed", [(12, 3, 2, 2, 9, 0), (13, 3, 3, 3, 11, 1), (16, 4, 3, 4, 12, 2),
+                                            (10, 2, 4, 5, 14, 3), (15, 5, 2, 3, 10, 4), (9, 3, 1, 3, 7, 5)])
+def test_blocked_brute_force_exact(N, S, q, T, K, seed):
+    """Exact rational whole-vector matrix powers against the oracle bit for bit
+    (dyadic data, r = 1/4)."""
+    rng = np.random.default_rng(seed)
+    u0 = rng.integers(-16, 17, size=N) / 16.0
+    nb = nblocks(K, T)
+    tr = rng.integers(0, q, size=(nb, S - 1, 2)).astype(np.uint8)
+    trc = np.minimum(tr, np.arange(nb)[:, None, None]).astype(np.uint8)
+    exact = pins.brute_async_blocked_fraction(u0, Fraction(1, 4), 0.25, -0.75, S, q, T, K, trc)
+    got = oracle.async_blocked(u0, 0.25, 0.25, -0.75, S, q, T, K, tr)
+    assert [Fraction(v) for v in got] == exact
+
+
+def test_blocked_stale_strip_and_sides_matter():
+    """One stale strip changes the result, and swapping the trace's sides
+    changes it again: the brute-force pin would see a side or block mix-up."""
+    rng = np.random.default_rng(5)
+    N, S, q, T, K = 24, 3, 3, 4, 24
+    u0 = rng.integers(-16, 17, size=N) / 16.0
+    nb = nblocks(K, T)
+    z = np.zeros((nb, S - 1, 2), dtype=np.uint8)
+    tr = z.copy()
+    tr[3, 0, 0] = 2
+    tr[4, 1, 1] = 1
+    base = oracle.async_blocked(u0, 0.25, 0.0, 0.0, S, q, T, K, z)
+    a = oracle.async_blocked(u0, 0.25, 0.0, 0.0, S, q, T, K, tr)
+    b = oracle.async_blocked(u0, 0.25, 0.0, 0.0, S, q, T, K, tr[:, :, ::-1].copy())
+    assert not np.array_equal(a, base) and not np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("r", [0.1, 0.5])
+def test_blocked_maximum_principle(r):
+    rng = np.random.default_rng(4)
+    N, S, q, T, K = 300, 6, 3, 16, 400
+    u0 = rng.uniform(-1, 1, size=N)
+    tr = inputs.delay_trace(nblocks(K, T), S, q, seed=7)
+    u = oracle.async_blocked(u0, r, 0.2, -0.3, S, q, T, K, tr)
+    lo, hi = min(u0[1:-1].min(), 0.2, -0.3), max(u0[1:-1].max(), 0.2, -0.3)
+    assert u.min() >= lo - 1e-13 and u.max() <= hi + 1e-13
+
+
+def test_blocked_unique_steady_state():
+    """With Dirichlet ends the blocked asynchronous run reaches the linear
+    steady state whatever the (bounded) strip delays."""
+    N, S, q, T, K = 24, 3, 3, 4, 30000
+    u0 = inputs.paper_rod(N=N).u0
+    x = inputs.grid_x(N)
+    for seed in (0, 1):
+        tr = inputs.delay_trace(nblocks(K, T), S, q, seed=seed)
+        u = oracle.async_blocked(u0, 0.5, 1.0, 0.0, S, q, T, K, tr)
+        assert np.abs(u - (1.0 - x)).max() < 1e-12
+
+
+def test_blocked_rejects_bad_arguments():
+    rod = inputs.small_rod(K=10)
+    tr = np.zeros((nblocks(10, 4), 7, 2), dtype=np.uint8)
+    tr[1, 2, 1] = 3
+    with pytest.raises(oracle.OracleError):  # delay outside the window
+        oracle.async_blocked(rod.u0, rod.r, rod.c1, rod.cN, 8, 3, 4, 10, tr)
+    with pytest.raises(oracle.OracleError):  # halo wider than the shortest segment (128 points)
+        oracle.async_blocked(rod.u0, rod.r, rod.c1, rod.cN, 8, 3, 129, 10, np.zeros((1, 7, 2), np.uint8))
+    with pytest.raises(ValueError):
+        oracle.async_blocked(rod.u0, rod.r, rod.c1, rod.cN, 8, 3, 4, 10, np.zeros((2, 7, 2), np.uint8))
