@@ -297,9 +297,10 @@ def run_small(args):
     """The small rod (N = 1024 FP64, r = 0.4, c1 = 0, cN = 1, u(0) = sin(pi x) +
     0.5 sin(7 pi x) + x, S = 8, q = 3): latency-bound.  Per-step device times
     of the persistent synchronous run, the free asynchronous run, its replay,
-    and a synchronous run relaunched once per step (the paper's structure
-    without its host copies); then async vs sync at equal error: the steps
-    and the time to ||u(k) - u_ss||_inf <= 1e-6."""
+    the asynchronous run with temporal blocking (T = 64 steps per block), and a
+    synchronous run relaunched once per step (the paper's structure without its
+    host copies); then async vs sync at equal error: the steps and the time to
+    ||u(k) - u_ss||_inf <= 1e-6."""
     torch, rank, world, local = _device_setup()
     from paper_1510_08982_gb300 import heat1d, inputs
     dev = torch.device("cuda", local)
@@ -330,8 +331,9 @@ def run_small(args):
         e1.synchronize()
         return e0.elapsed_time(e1) * 1e-3
 
+    btr = h.new_blocked_trace(K)
     runs = {"sync": lambda: h.run_sync(K), "async": lambda: h.run_async(K, tr), "replay": lambda: h.replay(K, tr),
-            "sync_relaunch_per_step": lambda: relaunch(K)}
+            "async_blocked": lambda: h.run_async_blocked(K, btr), "sync_relaunch_per_step": lambda: relaunch(K)}
     for _ in range(args.warmup):
         for f in runs.values():
             timed(f)
@@ -351,7 +353,7 @@ def run_small(args):
     snaps = torch.empty((kmax // every + 1, N), dtype=torch.float64, device=dev)
     eq = {"eps": eps, "norm": "max abs of u(k) - u_ss", "snapshot_every": every,
           "closed_form_sync_steps": k_est}
-    for kind, fn in (("sync", h.run_sync), ("async", h.run_async)):
+    for kind, fn in (("sync", h.run_sync), ("async", h.run_async), ("async_blocked", h.run_async_blocked)):
         h.set_snapshots(snaps, every=every)
         h.set_u(u0)
         fn(kmax)
@@ -386,7 +388,9 @@ def run_small(args):
                        "N": N, "K": K, "segments": S, "q": Q,
                        "l2": "the 8 KB rod stays on-chip; latency-bound, L2 state does not matter"},
             "us_per_step": us, "updates_per_s": ups,
+            "blocked_delay_histogram": np.bincount(btr.cpu().numpy().reshape(-1), minlength=Q).tolist(),
             "speedup": {"async_vs_relaunch_per_step": us["sync_relaunch_per_step"] / us["async"],
+                        "async_blocked_vs_relaunch_per_step": us["sync_relaunch_per_step"] / us["async_blocked"],
                         "persistent_sync_vs_relaunch_per_step": us["sync_relaunch_per_step"] / us["sync"]},
             "equal_error": eq,
             "roofline": {"bound": "alu", "kernel": "async_persistent_kernel<double,8>",
@@ -394,7 +398,7 @@ def run_small(args):
                          "frac": ups["async"] / peak_upd, "traffic": None,
                          "note": "8 CTAs on a 1024-point rod: bound by exchange latency, the ALU fraction is "
                                  "reported but not meaningful"},
-            "clocks": clk, "gpu_launches": args.steps * (3 + K)}
+            "clocks": clk, "gpu_launches": args.steps * (4 + K)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         trn = tr.cpu().numpy()

@@ -160,6 +160,39 @@ int64_t heat1d_trace_bytes(heat1d_t h, int64_t K);
  * unspecified. */
 int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device);
 
+/* ------------------------------------------------------------ asynchronous run, temporally blocked
+ *
+ * The bounded-delay model of Section 3 (Eq. (eqn:async)) applied to blocks of
+ * T steps instead of single steps; the paper has no such run (its PEs exchange
+ * one value per step), so the model is defined here.  T is the handle's halo
+ * depth (heat1d_opts.halo_steps, default 64, at most the shortest segment;
+ * heat1d_get_opts reports the value in use).  Time is cut into blocks of T
+ * steps; in block b (steps bT .. bT+tb-1, tb = min(T, K-bT)) every segment
+ * advances tb steps on its own points at step bT plus two T-wide halo strips:
+ * its left neighbour's last T points at step (b-dL)T and its right
+ * neighbour's first T points at step (b-dR)T, d < q, d <= b.  Its own points
+ * after the block are its part of the state at step bT+tb.  With every delay 0
+ * this is heat1d_run_sync bit for bit; with T = 1 it is Eq. (eqn:async).
+ *
+ * Trace layout: uint8 trace[b][boundary][side], ceil(K/T) blocks, S-1
+ * boundaries, the sides as in heat1d_run_async (side 0: segment b's read of
+ * its right neighbour; side 1: segment b+1's read of its left neighbour).
+ * Dirichlet ends only (boundary = 1 is rejected with HEAT1D_ERR_INVAL). */
+
+/* Free-running blocked run of K steps: each segment publishes its two edge
+ * strips once per block and starts the next block with its neighbours'
+ * newest strips not newer than that block, waiting only while one is more
+ * than q-1 blocks old.  trace_out (may be NULL; device or host per
+ * trace_on_device) receives heat1d_blocked_trace_bytes(h, K) bytes of delays. */
+int heat1d_run_async_blocked(heat1d_t h, int64_t K, uint8_t* trace_out, int trace_on_device);
+
+/* Replay of a blocked run with the strip delays given (entries >= q: the run
+ * returns HEAT1D_ERR_TRACE from heat1d_sync() and the state is unspecified). */
+int heat1d_replay_blocked(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device);
+
+/* Size in bytes of a blocked trace of K steps: ceil(K/T) * (S-1) * 2. */
+int64_t heat1d_blocked_trace_bytes(heat1d_t h, int64_t K);
+
 /* Waits for the handle's stream and returns the device-side status of the
  * runs enqueued since the previous heat1d_sync(): HEAT1D_OK,
  * HEAT1D_ERR_TIMEOUT or HEAT1D_ERR_TRACE (HEAT1D_ERR_CUDA on a CUDA error). */

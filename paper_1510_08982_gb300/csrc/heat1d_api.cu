@@ -79,6 +79,8 @@ struct heat1d {
   size_t d_trace_bytes = 0;
   void* snap = nullptr;  // caller's snapshot buffer (device) or null
   int64_t snap_every = 0, snap_rows = 0;
+  void* strips = nullptr;  // blocked asynchronous run: [S][R][2T] strips, allocated on first use
+  size_t strips_bytes = 0;
 
   unsigned* barrier() { return static_cast<unsigned*>(ctl); }
   int* status() { return static_cast<int*>(ctl) + 32; }
@@ -92,6 +94,9 @@ void free_scratch(heat1d* h) {
   cudaFree(h->rings);
   cudaFree(h->prog);
   cudaFree(h->done);
+  cudaFree(h->strips);
+  h->strips = nullptr;
+  h->strips_bytes = 0;
   h->d_off = nullptr;
   h->edges = nullptr;
   h->rings = nullptr;
@@ -330,6 +335,66 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   return HEAT1D_OK;
 }
 
+// The asynchronous run with temporal blocking (blocks of T = h->T steps).
+int run_blocked_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device, const uint8_t* trace_in,
+                       int in_on_device) {
+  if (K < 0 || K >= INT_MAX) return fail(HEAT1D_ERR_INVAL, "K out of range");
+  if (K == 0) return HEAT1D_OK;
+  if (h->opts.boundary == 1) return fail(HEAT1D_ERR_INVAL, "blocked asynchronous runs have Dirichlet ends only");
+  int E = 0, threads = 0;
+  int rc = pick_shape(h, h->Lmax + 2 * h->T, 0, false, &E, &threads);
+  if (rc) return rc;
+  if (h->snap) {
+    if (K / h->snap_every + 1 > h->snap_rows)
+      return fail(HEAT1D_ERR_INVAL, "snapshot buffer holds fewer rows than K/every + 1");
+    if (h->snap_every % h->T != 0)
+      return fail(HEAT1D_ERR_INVAL, "blocked snapshots need every to be a multiple of the block length");
+  }
+  const size_t sbytes = h->esize * static_cast<size_t>(h->S) * h->R * 2 * h->T;
+  if (sbytes > h->strips_bytes) {
+    cudaFree(h->strips);
+    h->strips = nullptr;
+    h->strips_bytes = 0;
+    HEAT1D_CUDA(cudaMalloc(&h->strips, sbytes));
+    h->strips_bytes = sbytes;
+  }
+  const int64_t nb = (K + h->T - 1) / h->T;
+  const size_t tbytes = static_cast<size_t>(nb) * (h->S - 1) * 2;
+  SegmentRun a = base_run(h, K);
+  a.rings = h->strips;
+  uint8_t* out_dev = nullptr;
+  if (trace_out && tbytes) {
+    if (out_on_device) {
+      out_dev = trace_out;
+    } else {
+      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
+      out_dev = h->d_trace;
+    }
+  }
+  const uint8_t* in_dev = nullptr;
+  if (trace_in && tbytes) {
+    if (in_on_device) {
+      in_dev = trace_in;
+    } else {
+      if (out_dev && out_dev == h->d_trace) return fail(HEAT1D_ERR_INVAL, "host trace in and out at once");
+      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
+      HEAT1D_CUDA(cudaMemcpyAsync(h->d_trace, trace_in, tbytes, cudaMemcpyHostToDevice, h->stream));
+      in_dev = h->d_trace;
+    }
+  }
+  a.trace_out = out_dev;
+  a.trace_in = in_dev;
+  HEAT1D_CUDA(cudaMemsetAsync(h->prog, 0xff, sizeof(int) * h->S * heat1d_impl::kProgStride, h->stream));
+  rc = heat1d_impl::launch_async_blocked(a, h->dtype, E, threads, h->stream);
+  if (rc == HEAT1D_ERR_NOT_RESIDENT)
+    return fail(rc, "blocked asynchronous run: " + std::to_string(h->S) + " CTAs cannot all be resident");
+  if (rc) return cuda_fail(cudaGetLastError(), "launch_async_blocked");
+  h->cur = 1 - h->cur;
+  if (out_dev && !out_on_device)
+    HEAT1D_CUDA(cudaMemcpyAsync(trace_out, out_dev, tbytes, cudaMemcpyDeviceToHost, h->stream));
+  return HEAT1D_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -493,6 +558,23 @@ int heat1d_run_sync(heat1d_t h, int64_t K) {
 int heat1d_run_async(heat1d_t h, int64_t K, uint8_t* trace_out, int trace_on_device) {
   if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
   return run_async_common(h, K, trace_out, trace_on_device, nullptr, 0);
+}
+
+int heat1d_run_async_blocked(heat1d_t h, int64_t K, uint8_t* trace_out, int trace_on_device) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  return run_blocked_common(h, K, trace_out, trace_on_device, nullptr, 0);
+}
+
+int heat1d_replay_blocked(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  if (!trace && h->S > 1 && K > 0) return fail(HEAT1D_ERR_INVAL, "heat1d_replay_blocked: trace is NULL");
+  static const uint8_t dummy = 0;
+  return run_blocked_common(h, K, nullptr, 0, trace ? trace : &dummy, trace ? trace_on_device : 0);
+}
+
+int64_t heat1d_blocked_trace_bytes(heat1d_t h, int64_t K) {
+  if (!h || K < 0) return fail(HEAT1D_ERR_INVAL, "bad argument");
+  return (K + h->T - 1) / h->T * (h->S - 1) * 2;
 }
 
 int64_t heat1d_trace_bytes(heat1d_t h, int64_t K) {

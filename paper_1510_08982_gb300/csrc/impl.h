@@ -88,6 +88,9 @@ constexpr int64_t window_warps(int64_t positions, int E, int H) {
 // threads per CTA (a multiple of 32).  Return a heat1d_status code.
 int launch_sync_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
 int launch_async_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
+// Asynchronous run with temporal blocking: a.T steps per block, a.rings holds
+// [S][R][2T] strips, a.prog the per-segment strip versions (-1 at launch).
+int launch_async_blocked(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
 
 // Sets the message returned by heat1d_last_error() on this host thread.
 void set_last_error(const std::string& msg);

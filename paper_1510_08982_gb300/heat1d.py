@@ -28,6 +28,7 @@ STATUS_NAMES = {OK: "HEAT1D_OK", ERR_INVAL: "HEAT1D_ERR_INVAL", ERR_CUDA: "HEAT1
 EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_last_error", "heat1d_set_stream",
            "heat1d_set_snapshots", "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
            "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync",
+           "heat1d_run_async_blocked", "heat1d_replay_blocked", "heat1d_blocked_trace_bytes",
            "heat1d_batch_create", "heat1d_batch_run", "heat1d_batch_sync", "heat1d_batch_describe",
            "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_adjoint", "heat1d_vjp",
            "heat1d_adjoint_batched", "heat1d_run_sync_noalloc"]
@@ -82,6 +83,9 @@ def load():
         "heat1d_trace_bytes": (i64, [vp, i64]),
         "heat1d_replay": (i32, [vp, i64, vp, i32]),
         "heat1d_sync": (i32, [vp]),
+        "heat1d_run_async_blocked": (i32, [vp, i64, vp, i32]),
+        "heat1d_replay_blocked": (i32, [vp, i64, vp, i32]),
+        "heat1d_blocked_trace_bytes": (i64, [vp, i64]),
         "heat1d_run_sync_noalloc": (i32, [vp, vp, i64, dbl, dbl, dbl, i32, i64, i64, vp, vp]),
         "heat1d_batch_create": (vp, [ctypes.POINTER(RodSpec), i64, i32, ctypes.POINTER(Opts)]),
         "heat1d_batch_run": (i32, [vp, vp, vp]),
@@ -270,6 +274,30 @@ class Heat1d:
         ptr, on_dev = self._trace_ptr(trace, K)
         _check(self.lib.heat1d_replay(self.h, int(K), ptr, on_dev))
 
+    def blocked_trace_bytes(self, K) -> int:
+        return int(self.lib.heat1d_blocked_trace_bytes(self.h, int(K)))
+
+    def new_blocked_trace(self, K, device=True):
+        """A trace buffer for a blocked run of K steps: (ceil(K/T), S-1, 2) uint8."""
+        torch = _torch()
+        T = self.get_opts()["halo_steps"]
+        shape = ((int(K) + T - 1) // T, max(self.S - 1, 0), 2)
+        if device:
+            return torch.empty(shape, dtype=torch.uint8, device="cuda")
+        return np.empty(shape, dtype=np.uint8)
+
+    def run_async_blocked(self, K, trace_out=None):
+        """Asynchronous run with temporal blocking (blocks of halo_steps steps);
+        trace_out as for run_async, blocked_trace_bytes(K) bytes."""
+        self._stream()
+        ptr, on_dev = self._trace_ptr(trace_out, K, self.blocked_trace_bytes(K))
+        _check(self.lib.heat1d_run_async_blocked(self.h, int(K), ptr, on_dev))
+
+    def replay_blocked(self, K, trace):
+        self._stream()
+        ptr, on_dev = self._trace_ptr(trace, K, self.blocked_trace_bytes(K))
+        _check(self.lib.heat1d_replay_blocked(self.h, int(K), ptr, on_dev))
+
     def sync(self):
         """Waits for the stream; raises on a device-side failure."""
         _check(self.lib.heat1d_sync(self.h))
@@ -300,11 +328,12 @@ class Heat1d:
                                    ctypes.c_void_p(g.data_ptr()), ctypes.byref(gr)))
         return g, gr.value
 
-    def _trace_ptr(self, t, K):
+    def _trace_ptr(self, t, K, n=None):
         torch = _torch()
         if t is None:
             return None, 0
-        n = self.trace_bytes(K)
+        if n is None:
+            n = self.trace_bytes(K)
         if isinstance(t, torch.Tensor):
             if t.dtype != torch.uint8 or not t.is_contiguous() or t.numel() != n:
                 raise ValueError("trace must be a contiguous uint8 tensor of %d bytes" % n)
