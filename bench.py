@@ -236,7 +236,7 @@ def run_streamed(args):
     esz = 4 if dt == "f32" else 8
     K = args.K if args.K != K_DEFAULT else 10_000
     N = args.N if args.N != N_DEFAULT else 1 << 26
-    T = args.halo or (64 if dt == "f32" else 32)
+    T = args.halo or (128 if dt == "f32" else 32)
     tdt = torch.float32 if dt == "f32" else torch.float64
     g = torch.Generator(device=dev).manual_seed(hd_seed(rank))
     u0 = torch.rand(N, dtype=tdt, device=dev, generator=g)

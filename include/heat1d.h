@@ -64,8 +64,11 @@ typedef struct heat1d_opts {
   int32_t q;             /* delay window of the asynchronous run, 1..255 (Section 3's buffer
                             length q).  0: 3. */
   int32_t halo_steps;    /* T, steps advanced between two exchanges in the synchronous run
-                            (overlapped halos of width T).  0: automatic.  1: exchange and
-                            grid barrier after every step, as in Section 2. */
+                            (overlapped halos of width T) and the block length of the blocked
+                            asynchronous run.  0: automatic (on-chip runs 64 in FP64, 128 in
+                            FP32, at most the shortest segment; streamed runs 32 in FP64, 128
+                            in FP32).  1: exchange and grid barrier after every step, as in
+                            Section 2. */
   int32_t block_threads; /* threads per CTA for the compute warps.  0: automatic. */
   int32_t elems_per_thread; /* points held in registers per thread (2, 4, 8 or 16).  0: automatic. */
   int64_t spin_limit_ns; /* bound on every device-side wait.  0: 2e9 (2 s). */

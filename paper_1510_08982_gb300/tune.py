@@ -71,7 +71,7 @@ def batched_candidates(dtype: str):
         return [dict(elems_per_thread=e, block_threads=t, halo_steps=T)
                 for e in (4, 8) for t in (128, 256) for T in (8, 16, 32)]
     return [dict(elems_per_thread=e, block_threads=t, halo_steps=T)
-            for e in (8, 16) for t in (128, 256, 512) for T in (16, 32, 64)]
+            for e in (8, 16) for t in (128, 256, 512) for T in (32, 64, 128)]
 
 
 def stream_candidates(dtype: str):
@@ -79,7 +79,7 @@ def stream_candidates(dtype: str):
         return [dict(elems_per_thread=e, block_threads=t, halo_steps=T)
                 for e in (4, 8) for t in (128, 256) for T in (8, 16, 32, 64)]
     return [dict(elems_per_thread=e, block_threads=t, halo_steps=T)
-            for e in (8, 16) for t in (128, 256) for T in (8, 16, 32, 64)]
+            for e in (8, 16) for t in (128, 256) for T in (16, 64, 128, 192)]
 
 
 def _gpu_name() -> str:
