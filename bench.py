@@ -48,7 +48,7 @@ FP64_INSTR_PER_UPDATE = 3
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the asynchronous kernel on the
 # 2^20-point rod, from the committed ncu summary of that kernel.
-ASYNC_KERNEL_DRAM_BYTES = 8_466_688 + 1_792
+ASYNC_KERNEL_DRAM_BYTES = 8_486_656 + 2_560
 
 
 def parse():

@@ -128,33 +128,47 @@ __device__ void publish_loop(const SegmentRun& a, AsyncShared<real, E>& sh, int 
   }
 }
 
-// Puller: copies each new version of one neighbour's facing edge value from
-// its global ring into the local ring, then release-stores the newest version
-// held (the buffer of Section 3 that keeps the most recent received values).
+// Puller (a whole warp): copies each new version of one neighbour's facing
+// edge value from its global ring into the local ring, then release-stores
+// the newest version held (the buffer of Section 3 that keeps the most recent
+// received values).  Lane 0 acquires the neighbour's version counter; after a
+// warp barrier (which orders that acquire before the other lanes' loads) the
+// lanes copy the new versions in parallel, so one pass costs two L2 round
+// trips however many versions arrived.
 template <typename real, int E>
 __device__ void pull_loop(const SegmentRun& a, AsyncShared<real, E>& sh, const int* nprog, const real* nring,
-                          real* lring, int* avail) {
+                          real* lring, int* avail, int lane) {
   const int R = a.R;
   int seen = -1;
   uint64_t t_idle = global_timer_ns();
   unsigned spins = 0;
   while (true) {
-    const int P = ld_acquire_gpu(nprog);
+    int P = 0;
+    if (lane == 0) P = ld_acquire_gpu(nprog);
+    __syncwarp();
+    P = __shfl_sync(kFullMask, P, 0);
     if (P > seen) {
-      for (int x = max(seen + 1, P - R + 1); x <= P; ++x) lring[x & (R - 1)] = ld_cg(nring + (x & (R - 1)));
-      st_release_cta_shared(avail, P);
+      for (int x = max(seen + 1, P - R + 1) + lane; x <= P; x += 32) lring[x & (R - 1)] = ld_cg(nring + (x & (R - 1)));
+      __syncwarp();
+      if (lane == 0) st_release_cta_shared(avail, P);
       seen = P;
       t_idle = global_timer_ns();
       continue;
     }
-    if (ld_acquire_cta_shared(&sh.compute_done)) break;  // no more reads needed
-    if ((++spins & 63u) == 0) {
-      if (status_failed(a.status)) break;
-      if (static_cast<int64_t>(global_timer_ns() - t_idle) > a.spin_limit_ns) {
-        raise_status(a.status, HEAT1D_ERR_TIMEOUT);
-        break;
+    int stop = 0;
+    if (lane == 0) {
+      if (ld_acquire_cta_shared(&sh.compute_done)) {
+        stop = 1;  // no more reads needed
+      } else if ((++spins & 63u) == 0) {
+        if (status_failed(a.status)) {
+          stop = 1;
+        } else if (static_cast<int64_t>(global_timer_ns() - t_idle) > a.spin_limit_ns) {
+          raise_status(a.status, HEAT1D_ERR_TIMEOUT);
+          stop = 1;
+        }
       }
     }
+    if (__shfl_sync(kFullMask, stop, 0)) break;
   }
 }
 
@@ -177,22 +191,20 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
   __syncthreads();
 
   if (warp >= nwc) {
-    if (lane == 0) {
-      real* rings = static_cast<real*>(a.rings);
-      const int sl = s > 0 ? s - 1 : (a.periodic ? a.S - 1 : -1);  // neighbours (ring when periodic)
-      const int sr = s + 1 < a.S ? s + 1 : (a.periodic ? 0 : -1);
-      if (warp == nwc) {
-        publish_loop<real, E>(a, sh, s);
-      } else {
-        // warp nwc+1 pulls the left neighbour's right edge, warp nwc+2 the
-        // right neighbour's left edge
-        const bool from_left = warp == nwc + 1;
-        const int nb = from_left ? sl : sr;
-        if (nb >= 0)
-          pull_loop<real, E>(a, sh, a.prog + static_cast<size_t>(nb) * kProgStride,
-                             rings + (static_cast<size_t>(nb) * 2 + (from_left ? 1 : 0)) * a.R,
-                             from_left ? sh.lring : sh.rring, from_left ? &sh.lavail : &sh.ravail);
-      }
+    real* rings = static_cast<real*>(a.rings);
+    const int sl = s > 0 ? s - 1 : (a.periodic ? a.S - 1 : -1);  // neighbours (ring when periodic)
+    const int sr = s + 1 < a.S ? s + 1 : (a.periodic ? 0 : -1);
+    if (warp == nwc) {
+      if (lane == 0) publish_loop<real, E>(a, sh, s);
+    } else {
+      // warp nwc+1 pulls the left neighbour's right edge, warp nwc+2 the
+      // right neighbour's left edge
+      const bool from_left = warp == nwc + 1;
+      const int nb = from_left ? sl : sr;
+      if (nb >= 0)
+        pull_loop<real, E>(a, sh, a.prog + static_cast<size_t>(nb) * kProgStride,
+                           rings + (static_cast<size_t>(nb) * 2 + (from_left ? 1 : 0)) * a.R,
+                           from_left ? sh.lring : sh.rring, from_left ? &sh.lavail : &sh.ravail, lane);
     }
     return;
   }
@@ -273,64 +285,80 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_pe
     if (right_reader) dr_next = __ldg(trace_in + tr);
   }
 
+  // Only the warps that read a halo or hand an edge to the publisher need to
+  // stop after every step.  The others advance each run of kRefresh steps
+  // with the two-array step (no per-step checks, no register rotation); the
+  // arithmetic is the same.  While snapshots are recorded every warp steps
+  // one at a time, so that it can store the state of any step.
+  const bool edge_warp = __any_sync(kFullMask, left_reader || right_reader || e_first >= 0 || e_last >= 0);
+  const bool per_step = edge_warp || snap != nullptr;
   bool failed = false;   // a wait of this thread gave up: no more waits until the CTA leaves
   bool aborted = false;
   int parity = 0;
-  for (int k = 0; k < K; ++k) {
-    if (left_reader && !failed) {
-      const int d = dl_next;
-      if (trace_in && k + 1 < K) dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
-      real val;
-      if (fetch_halo<real>(a, &sh.lavail, sh.lring, k, trace_in, trace_out, static_cast<size_t>(k) * tstride + tl, d,
-                           val))
-        v[0] = val;
-      else
-        failed = true;
-    }
-    if (right_reader && !failed) {
-      const int d = dr_next;
-      if (trace_in && k + 1 < K) dr_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tr);
-      real val;
-      if (fetch_halo<real>(a, &sh.ravail, sh.rring, k, trace_in, trace_out, static_cast<size_t>(k) * tstride + tr, d,
-                           val)) {
+  for (int k0 = 0; k0 < K; k0 += kRefresh) {
+    const int n = min(kRefresh, K - k0);
+    if (!per_step) {
+      if (mode == kTileFree)
+        warp_steps<real, E, kTileFree>(v, fixed, coef, n);
+      else if (mode == kTileMasked)
+        warp_steps<real, E, kTileMasked>(v, fixed, coef, n);
+    } else {
+      for (int k = k0; k < k0 + n; ++k) {
+        if (left_reader && !failed) {
+          const int d = dl_next;
+          if (trace_in && k + 1 < K) dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
+          real val;
+          if (fetch_halo<real>(a, &sh.lavail, sh.lring, k, trace_in, trace_out, static_cast<size_t>(k) * tstride + tl,
+                               d, val))
+            v[0] = val;
+          else
+            failed = true;
+        }
+        if (right_reader && !failed) {
+          const int d = dr_next;
+          if (trace_in && k + 1 < K) dr_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tr);
+          real val;
+          if (fetch_halo<real>(a, &sh.ravail, sh.rring, k, trace_in, trace_out, static_cast<size_t>(k) * tstride + tr,
+                               d, val)) {
 #pragma unroll
-        for (int e = 0; e < E; ++e)
-          if (e == e_rh) v[e] = val;
-      } else {
-        failed = true;
+            for (int e = 0; e < E; ++e)
+              if (e == e_rh) v[e] = val;
+          } else {
+            failed = true;
+          }
+        }
+        warp_step_any<real, E>(mode, v, fixed, coef);
+        const int ver = k + 1, j = ver & (a.R - 1);
+        if (snap && ver % a.snap_every == 0) {  // owners record the state at step ver
+          real* row = snap + static_cast<size_t>(ver / a.snap_every) * N;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int p = Win::pos(warp, lane, e);
+            if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) row[a0 - 1 + p] = v[e];
+          }
+        }
+        if (e_first >= 0) {
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+            if (e == e_first) sh.own_l[j] = v[e];
+          st_release_cta_shared(&sh.own_l_ver, ver);
+        }
+        if (e_last >= 0) {
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+            if (e == e_last) sh.own_r[j] = v[e];
+          st_release_cta_shared(&sh.own_r_ver, ver);
+        }
       }
     }
-    warp_step_any<real, E>(mode, v, fixed, coef);
-    const int ver = k + 1, j = ver & (a.R - 1);
-    if (snap && ver % a.snap_every == 0) {  // owners record the state at step ver
-      real* row = snap + static_cast<size_t>(ver / a.snap_every) * N;
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int p = Win::pos(warp, lane, e);
-        if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) row[a0 - 1 + p] = v[e];
-      }
-    }
-    if (e_first >= 0) {
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (e == e_first) sh.own_l[j] = v[e];
-      st_release_cta_shared(&sh.own_l_ver, ver);
-    }
-    if (e_last >= 0) {
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (e == e_last) sh.own_r[j] = v[e];
-      st_release_cta_shared(&sh.own_r_ver, ver);
-    }
-    // Refresh the warp halos every kRefresh steps (and after the last step);
-    // the refresh barrier also tells every warp whether a wait gave up.
-    if (ver % kRefresh == 0 || ver == K) {
-      const bool any_failed = warp_refresh<real, E, Win::H>(v, sh.win, parity, warp, lane, nwc, nthreads_c, failed);
-      parity ^= 1;
-      if (any_failed) {
-        aborted = true;
-        break;
-      }
+    // Refresh the warp halos after every run of kRefresh steps (and after the
+    // last step); the refresh barrier also tells every warp whether a wait
+    // gave up.
+    const bool any_failed = warp_refresh<real, E, Win::H>(v, sh.win, parity, warp, lane, nwc, nthreads_c, failed);
+    parity ^= 1;
+    if (any_failed) {
+      aborted = true;
+      break;
     }
   }
 
