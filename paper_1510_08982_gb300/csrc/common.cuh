@@ -281,11 +281,15 @@ __device__ __forceinline__ bool warp_refresh(real (&v)[E], WindowShared<real, H>
 }
 
 // Advances the CTA `steps` steps: runs of at most H warp steps, each followed
-// by a refresh, so the windows are fully valid again when it returns.
+// by a refresh, so the windows are fully valid again when it returns.  With
+// final_refresh = false the refresh after the last run is left out: every
+// warp's own positions are valid after at most H steps, and a caller that
+// only stores those (and then discards the tile) saves a barrier; with
+// steps <= H no barrier is met at all.
 template <typename real, int E, int H>
 __device__ __forceinline__ void warp_advance(int mode, real (&v)[E], unsigned fixed, Coef<real> c,
                                              WindowShared<real, H>& sh, int& parity, int warp, int lane, int nwarps,
-                                             unsigned nthreads, int steps) {
+                                             unsigned nthreads, int steps, bool final_refresh = true) {
   for (int done = 0; done < steps;) {
     const int n = min(H, steps - done);
     if (mode == kTileFree) {
@@ -293,9 +297,11 @@ __device__ __forceinline__ void warp_advance(int mode, real (&v)[E], unsigned fi
     } else if (mode == kTileMasked) {
       warp_steps<real, E, kTileMasked>(v, fixed, c, n);
     }
-    warp_refresh<real, E, H>(v, sh, parity, warp, lane, nwarps, nthreads, false);
-    parity ^= 1;
     done += n;
+    if (done < steps || final_refresh) {
+      warp_refresh<real, E, H>(v, sh, parity, warp, lane, nwarps, nthreads, false);
+      parity ^= 1;
+    }
   }
 }
 

@@ -161,7 +161,8 @@ int configure(heat1d* h, const heat1d_opts& o) {
     return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: streamed runs need elems_per_thread a multiple of 16 bytes");
   const int64_t W =
       heat1d_impl::window_width(sthreads / 32, sE, heat1d_impl::sync_window_halo(static_cast<int>(h->esize), sE)) - 2 * Th;
-  if (o.sync_mode == 2 && (W < vn || sthreads > heat1d_impl::max_tile_threads(static_cast<int>(h->esize), sE)))
+  // (the streamed kernel adds one producer warp to the compute threads)
+  if (o.sync_mode == 2 && (W < vn || sthreads > heat1d_impl::kStreamMaxThreads))
     return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: streamed tile too small for halo_steps, or too many threads");
   const int64_t ntiles = W >= vn ? (h->N + W - 1) / W : 0;
 
@@ -192,8 +193,10 @@ int configure(heat1d* h, const heat1d_opts& o) {
 
 // The streamed synchronous run (temporal blocking through HBM).
 int run_streamed(heat1d* h, int64_t K) {
-  if (h->ntiles <= 0 || (h->sE != 4 && h->sE != 8 && h->sE != 16))
-    return fail(HEAT1D_ERR_INVAL, "streamed run: invalid tile shape (elems_per_thread must be 4, 8 or 16)");
+  if (h->ntiles <= 0 || (h->sE != 4 && h->sE != 8 && h->sE != 16) ||
+      h->sthreads > heat1d_impl::kStreamMaxThreads)
+    return fail(HEAT1D_ERR_INVAL,
+                "streamed run: invalid tile shape (elems_per_thread must be 4, 8 or 16; block_threads at most 512)");
   heat1d_impl::StreamRun a{};
   a.N = h->N;
   a.K = K;
@@ -209,13 +212,14 @@ int run_streamed(heat1d* h, int64_t K) {
   a.done = h->done;
   a.status = h->status();
   a.spin_limit_ns = h->opts.spin_limit_ns;
-  const int resident = heat1d_impl::max_resident_stream(h->dtype, h->sE, h->sthreads);
+  // Pipelined kernel: tile loads by bulk copies from one extra producer warp.
+  const int resident = heat1d_impl::max_resident_stream_tma(h->dtype, h->sE, h->sthreads, h->W + 2 * h->Th);
   if (resident <= 0) return fail(HEAT1D_ERR_NOT_RESIDENT, "streamed run: kernel cannot be resident");
   const int grid = static_cast<int>(std::min<int64_t>(h->ntiles, resident));
   HEAT1D_CUDA(cudaMemsetAsync(h->done, 0, sizeof(int) * h->ntiles, h->stream));
-  int rc = heat1d_impl::launch_stream(a, h->dtype, h->sE, h->sthreads, grid, h->stream);
+  int rc = heat1d_impl::launch_stream_tma(a, h->dtype, h->sE, h->sthreads, grid, h->stream);
   if (rc == HEAT1D_ERR_NOT_RESIDENT) return fail(rc, "streamed run: grid cannot be resident");
-  if (rc) return cuda_fail(cudaGetLastError(), "launch_stream");
+  if (rc) return cuda_fail(cudaGetLastError(), "launch_stream_tma");
   const int64_t npass = (K + h->Ts - 1) / h->Ts;
   if (npass & 1) h->cur = 1 - h->cur;
   return HEAT1D_OK;

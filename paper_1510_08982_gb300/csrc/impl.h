@@ -96,9 +96,12 @@ int launch_async_blocked(const SegmentRun& a, int dtype, int E, int threads, cud
 void set_last_error(const std::string& msg);
 
 // Streamed synchronous run: one cooperative launch of `grid` CTAs of `threads`
-// threads, E points per thread (4, 8 or 16); tiles of threads*E slots.
-int launch_stream(const StreamRun& a, int dtype, int E, int threads, int grid, cudaStream_t st);
-int max_resident_stream(int dtype, int E, int threads);
+// compute threads (at most kStreamMaxThreads) plus a loader and a releaser
+// warp, E points per thread (4, 8 or 16); tile loads by bulk copies into
+// shared memory.
+constexpr int kStreamMaxThreads = 512;
+int launch_stream_tma(const StreamRun& a, int dtype, int E, int threads, int grid, cudaStream_t st);
+int max_resident_stream_tma(int dtype, int E, int threads, int Wt);
 
 // ------------------------------------------------------------ batched rods
 

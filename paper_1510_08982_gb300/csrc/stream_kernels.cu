@@ -16,8 +16,9 @@
 // about to overwrite, and what tile j reads is complete).  Waits only point to
 // earlier passes, so the launch cannot deadlock while all CTAs are resident.
 //
-// Loads and stores move 16 bytes per thread per instruction where a thread's
-// run of E points lies inside the rod (tile starts are 16-byte aligned).
+// A tile and its halos arrive in shared memory by one bulk copy (tile starts
+// are 16-byte aligned); stores move 16 bytes per thread per instruction where
+// a thread's run of E points lies inside the rod.
 #include <algorithm>
 
 #include "common.cuh"
@@ -59,60 +60,234 @@ __device__ bool wait_tile(const int* done, int want, int* status, int64_t limit_
   return true;
 }
 
+// ------------------------------------------------------------ the pipeline
+//
+// Tile loads and pass-counter releases are taken off the compute warps' path
+// by two extra warps:
+//  - the loader (one thread) waits for a tile's previous pass and its
+//    neighbours', then copies the tile and its halos from HBM into one of
+//    kStages shared-memory stages with a single bulk copy (cp.async.bulk, the
+//    1D form of TMA) whose completion lands on the stage's "full" mbarrier;
+//  - the compute warps read the stage into registers, advance the tile, store
+//    it and arrive on the stage's "stored" mbarrier;
+//  - the releaser (one thread) waits on "stored", makes the tile's stores
+//    visible GPU-wide, release-stores the tile's pass counter and hands the
+//    stage back to the loader ("free").
+// Tiles whose halos reach past either end of the rod are loaded by the
+// compute warps with plain loads (the stage is then only a signal).  Every
+// wait is bounded; on a failure the loader waits for its own copies before it
+// returns.
+
+constexpr int kStages = 4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of `bar` with the given parity to complete.  Gives up
+// after limit_ns (raising a timeout) or, when `watch` is set, as soon as the
+// run has failed elsewhere.
+__device__ bool mbar_wait(uint64_t* bar, unsigned parity, int* status, int64_t limit_ns, bool watch) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (!mbar_test(bar, parity)) {
+    if ((++spins & 15u) == 0) {
+      if (watch && status_failed(status)) return false;
+      if (static_cast<int64_t>(global_timer_ns() - t0) > limit_ns) {
+        raise_status(status, HEAT1D_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_copy_to_shared(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 template <typename real, int E>
-__global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) stream_kernel(StreamRun a) {
+__global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_tma_kernel(StreamRun a) {
   using V = typename Vec16<real>::type;
   using Win = Window<E, sync_window_halo(sizeof(real), E)>;
   constexpr int VN = Vec16<real>::n;
   static_assert(E % VN == 0, "E must be a multiple of the 16-byte vector width");
+  extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ WindowShared<real, Win::H> sh;
-  __shared__ int sh_ok;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-
+  __shared__ __align__(8) uint64_t full[kStages], stored[kStages], freed[kStages];
+  __shared__ int stage_plain[kStages];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwc = (blockDim.x >> 5) - 2;  // compute warps; then the loader and the releaser warp
+  const unsigned nthreads_c = static_cast<unsigned>(nwc) * 32u;
   const int64_t N = a.N;
-  const int Th = a.Th, W = a.W;
-  const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
-  const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};
+  const int Th = a.Th, W = a.W, Wt = a.W + 2 * a.Th;
+  real* stage0 = reinterpret_cast<real*>(dyn);
   real* buf[2] = {static_cast<real*>(a.u_a), static_cast<real*>(a.u_b)};
   const int npass = static_cast<int>((a.K + a.T - 1) / a.T);
-  const int p0 = Win::pos(warp, lane, 0);  // this thread's first position
-  // lanes 1..30 own all their positions; lanes 0 and 31 may hold halo copies
-  const bool owns_all = Win::owner(warp, lane, 0, nwarps) && Win::owner(warp, lane, E - 1, nwarps);
-  int parity = 0;
+  const int64_t my_tiles = a.ntiles > blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // Items in order: every pass, this CTA's tiles blockIdx.x, blockIdx.x + G, ...
+  const int64_t items = my_tiles * npass;
 
-  for (int p = 0; p < npass; ++p) {
+  if (tid == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&stored[st], static_cast<unsigned>(nwc));
+      mbar_init(&freed[st], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == nwc) {  // ------------------------------------------------ loader
+    if (lane != 0) return;
+    int64_t issued = 0;
+    bool ok = true;
+    int p = 0, st = 0;
+    unsigned round = 0;
+    int64_t j = blockIdx.x;
+    for (int64_t i = 0; i < items && ok; ++i) {
+      if (round > 0 && !mbar_wait(&freed[st], (round - 1) & 1u, a.status, a.spin_limit_ns, true)) break;
+      if (p > 0) {
+        // The tile's previous pass and its neighbours'.  The tile's own pass
+        // was stored by this CTA's compute warps, which the copies run ahead
+        // of; when the CTA has at least kStages tiles, the wait on "freed"
+        // above already covers it (the releaser works in item order).
+        // Acquire loads, not relaxed loads and a GPU-scope fence: measured
+        // faster, as such a fence also waits for this thread's copies in
+        // flight.
+        if (my_tiles < kStages) ok = wait_tile(a.done + j, p, a.status, a.spin_limit_ns);
+        if (ok && j > 0) ok = wait_tile(a.done + (j - 1), p, a.status, a.spin_limit_ns);
+        if (ok && j + 1 < a.ntiles) ok = wait_tile(a.done + (j + 1), p, a.status, a.spin_limit_ns);
+        if (!ok) break;
+      }
+      const int64_t g0 = j * W - Th;
+      const bool plain = g0 < 0 || g0 + Wt > N;
+      stage_plain[st] = plain;
+      if (plain) {
+        mbar_arrive(&full[st]);  // release: the waits above happen before the compute warps' loads
+      } else {
+        // The neighbours' stores were made through the generic proxy; the copy
+        // reads through the async proxy, and the stage's previous contents
+        // were read through the generic proxy.
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const unsigned bytes = static_cast<unsigned>(Wt) * sizeof(real);
+        mbar_arrive_expect_tx(&full[st], bytes);
+        bulk_copy_to_shared(stage0 + static_cast<size_t>(st) * Wt, buf[p & 1] + g0, bytes, &full[st]);
+      }
+      issued = i + 1;
+      j += gridDim.x;
+      if (j >= a.ntiles) {
+        j = blockIdx.x;
+        ++p;
+      }
+      if (++st == kStages) {
+        st = 0;
+        ++round;
+      }
+    }
+    // Copies still in flight (only after a failure) must land before the CTA leaves.
+    for (int64_t i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
+      mbar_wait(&full[i % kStages], static_cast<unsigned>(i / kStages) & 1u, a.status, a.spin_limit_ns, false);
+    return;
+  }
+
+  if (warp == nwc + 1) {  // -------------------------------------------- releaser
+    if (lane != 0) return;
+    int p = 0, st = 0;
+    unsigned round = 0;
+    int64_t j = blockIdx.x;
+    for (int64_t i = 0; i < items; ++i) {
+      if (!mbar_wait(&stored[st], round & 1u, a.status, a.spin_limit_ns, true)) break;
+      // The compute warps' stores, ordered before their arrivals (release at
+      // CTA scope, acquired by the wait above), are ordered before the
+      // counter by this release at GPU scope (cumulativity).  No separate
+      // fence: it would wait a second time for the same stores.
+      st_release_gpu(a.done + j, p + 1);
+      mbar_arrive(&freed[st]);
+      j += gridDim.x;
+      if (j >= a.ntiles) {
+        j = blockIdx.x;
+        ++p;
+      }
+      if (++st == kStages) {
+        st = 0;
+        ++round;
+      }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------ compute warps
+  const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};
+  const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
+  const int p0 = Win::pos(warp, lane, 0);
+  const bool owns_all = Win::owner(warp, lane, 0, nwc) && Win::owner(warp, lane, E - 1, nwc);
+  int parity = 0;
+  int p = 0, st = 0;
+  unsigned round = 0;
+  int64_t j = blockIdx.x;
+  for (int64_t i = 0; i < items; ++i) {
     const real* __restrict__ src = buf[p & 1];
     real* __restrict__ dst = buf[(p + 1) & 1];
     const int tb = static_cast<int>(std::min<int64_t>(a.T, a.K - static_cast<int64_t>(p) * a.T));
-    for (int64_t j = blockIdx.x; j < a.ntiles; j += gridDim.x) {
-      if (p > 0) {
-        if (tid == 0) {
-          bool ok = true;
-          if (j > 0) ok = wait_tile(a.done + (j - 1), p, a.status, a.spin_limit_ns);
-          if (ok && j + 1 < a.ntiles) ok = wait_tile(a.done + (j + 1), p, a.status, a.spin_limit_ns);
-          sh_ok = ok;
-        }
-        __syncthreads();
-        if (!sh_ok) return;
+    bool failed = !mbar_wait(&full[st], round & 1u, a.status, a.spin_limit_ns, true);
+    const int64_t g0 = j * W - Th;
+    const int64_t gt = g0 + p0;
+    // A tile clear of both ends of the rod (the common case) has no fixed
+    // point, every window position inside the rod and an in-range store.
+    const bool inner = g0 > 0 && g0 + Wt < N;
+    real v[E];
+    if (!failed && !stage_plain[st]) {
+      const real* sp = stage0 + static_cast<size_t>(st) * Wt + p0;
+#pragma unroll
+      for (int q = 0; q < E / VN; ++q) {
+        const V x = reinterpret_cast<const V*>(sp)[q];
+        const real* xs = reinterpret_cast<const real*>(&x);
+#pragma unroll
+        for (int t = 0; t < VN; ++t) v[q * VN + t] = xs[t];
       }
-      // Load: position q holds global point g0 + q, g0 = j*W - Th.
-      const int64_t gt = j * W - Th + p0;
-      real v[E];
-      if (gt >= 0 && gt + E <= N) {
+    } else {
 #pragma unroll
-        for (int i = 0; i < E / VN; ++i) {
-          const V x = __ldcg(reinterpret_cast<const V*>(src + gt) + i);
-          const real* xs = reinterpret_cast<const real*>(&x);
-#pragma unroll
-          for (int q = 0; q < VN; ++q) v[i * VN + q] = xs[q];
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int64_t g = gt + e;
-          v[e] = (g >= 0 && g < N) ? __ldcg(src + g) : static_cast<real>(0);
-        }
+      for (int e = 0; e < E; ++e) {
+        const int64_t g = gt + e;
+        v[e] = (!failed && g >= 0 && g < N) ? __ldcg(src + g) : static_cast<real>(0);
       }
+    }
+    // A failed wait ends the run for every compute warp.  Passes longer than
+    // H steps meet halo-refresh barriers, so there the warps leave together;
+    // shorter passes meet none (the last refresh of a pass is left out) and
+    // each warp may leave on its own.
+    if (a.T > Win::H) {
+      if (named_barrier_or(2, nthreads_c, failed)) return;
+    } else if (failed) {
+      return;
+    }
+    if (inner) {
+      warp_advance<real, E, Win::H>(kTileFree, v, 0u, coef, sh, parity, warp, lane, nwc, nthreads_c, tb, false);
+    } else {
       unsigned fixed = 0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -122,41 +297,54 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) stream_k
         if (g <= 0 || g >= N - 1) fixed |= 1u << e;
       }
       const int mode = tile_mode<E>(fixed);
-      warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
-
-      // Store the W own points (positions Th .. Th+W-1) inside the rod.
-      if (owns_all && p0 >= Th && p0 + E <= Th + W && gt >= 0 && gt + E <= N) {
+      warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwc, nthreads_c, tb, false);
+    }
+    if (owns_all && p0 >= Th && p0 + E <= Th + W && (inner || (gt >= 0 && gt + E <= N))) {
 #pragma unroll
-        for (int i = 0; i < E / VN; ++i) {
-          V x;
-          real* xs = reinterpret_cast<real*>(&x);
+      for (int q = 0; q < E / VN; ++q) {
+        V x;
+        real* xs = reinterpret_cast<real*>(&x);
 #pragma unroll
-          for (int q = 0; q < VN; ++q) xs[q] = v[i * VN + q];
-          __stcg(reinterpret_cast<V*>(dst + gt) + i, x);
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int q = p0 + e;
-          const int64_t g = gt + e;
-          if (q >= Th && q < Th + W && g >= 0 && g < N && Win::owner(warp, lane, e, nwarps)) __stcg(dst + g, v[e]);
-        }
+        for (int t = 0; t < VN; ++t) xs[t] = v[q * VN + t];
+        __stcg(reinterpret_cast<V*>(dst + gt) + q, x);
       }
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release_gpu(a.done + j, p + 1);
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int qq = p0 + e;
+        const int64_t g = gt + e;
+        if (qq >= Th && qq < Th + W && g >= 0 && g < N && Win::owner(warp, lane, e, nwc)) __stcg(dst + g, v[e]);
       }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&stored[st]);  // release: this warp's stores come first
+    j += gridDim.x;
+    if (j >= a.ntiles) {
+      j = blockIdx.x;
+      ++p;
+    }
+    if (++st == kStages) {
+      st = 0;
+      ++round;
     }
   }
 }
 
 template <typename real, int E>
-int launch_stream_t(const StreamRun& a, int threads, int grid, cudaStream_t st) {
+size_t tma_smem_bytes(int Wt) {
+  return static_cast<size_t>(kStages) * Wt * sizeof(real);
+}
+
+template <typename real, int E>
+int launch_stream_tma_t(const StreamRun& a, int threads, int grid, cudaStream_t st) {
   StreamRun args = a;
   void* params[] = {&args};
-  cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(stream_kernel<real, E>), dim3(grid),
-                                              dim3(threads), params, 0, st);
+  const size_t smem = tma_smem_bytes<real, E>(a.W + 2 * a.Th);
+  if (cudaFuncSetAttribute(stream_tma_kernel<real, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return HEAT1D_ERR_CUDA;
+  cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(stream_tma_kernel<real, E>), dim3(grid),
+                                              dim3(threads + 64), params, smem, st);
   if (e == cudaErrorCooperativeLaunchTooLarge) {
     cudaGetLastError();
     return HEAT1D_ERR_NOT_RESIDENT;
@@ -165,9 +353,14 @@ int launch_stream_t(const StreamRun& a, int threads, int grid, cudaStream_t st) 
 }
 
 template <typename real, int E>
-int resident_stream_t(int threads) {
+int resident_stream_tma_t(int threads, int Wt) {
   int per_sm = 0, dev = 0, nsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_kernel<real, E>, threads, 0) != cudaSuccess)
+  const size_t smem = tma_smem_bytes<real, E>(Wt);
+  if (cudaFuncSetAttribute(stream_tma_kernel<real, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_tma_kernel<real, E>, threads + 64, smem) !=
+      cudaSuccess)
     return 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -176,22 +369,22 @@ int resident_stream_t(int threads) {
 
 }  // namespace
 
-int launch_stream(const StreamRun& a, int dtype, int E, int threads, int grid, cudaStream_t st) {
+int launch_stream_tma(const StreamRun& a, int dtype, int E, int threads, int grid, cudaStream_t st) {
   const bool f64 = dtype == HEAT1D_F64;
   switch (E) {
-    case 4: return f64 ? launch_stream_t<double, 4>(a, threads, grid, st) : launch_stream_t<float, 4>(a, threads, grid, st);
-    case 8: return f64 ? launch_stream_t<double, 8>(a, threads, grid, st) : launch_stream_t<float, 8>(a, threads, grid, st);
-    case 16: return f64 ? launch_stream_t<double, 16>(a, threads, grid, st) : launch_stream_t<float, 16>(a, threads, grid, st);
+    case 4: return f64 ? launch_stream_tma_t<double, 4>(a, threads, grid, st) : launch_stream_tma_t<float, 4>(a, threads, grid, st);
+    case 8: return f64 ? launch_stream_tma_t<double, 8>(a, threads, grid, st) : launch_stream_tma_t<float, 8>(a, threads, grid, st);
+    case 16: return f64 ? launch_stream_tma_t<double, 16>(a, threads, grid, st) : launch_stream_tma_t<float, 16>(a, threads, grid, st);
     default: return HEAT1D_ERR_INVAL;
   }
 }
 
-int max_resident_stream(int dtype, int E, int threads) {
+int max_resident_stream_tma(int dtype, int E, int threads, int Wt) {
   const bool f64 = dtype == HEAT1D_F64;
   switch (E) {
-    case 4: return f64 ? resident_stream_t<double, 4>(threads) : resident_stream_t<float, 4>(threads);
-    case 8: return f64 ? resident_stream_t<double, 8>(threads) : resident_stream_t<float, 8>(threads);
-    case 16: return f64 ? resident_stream_t<double, 16>(threads) : resident_stream_t<float, 16>(threads);
+    case 4: return f64 ? resident_stream_tma_t<double, 4>(threads, Wt) : resident_stream_tma_t<float, 4>(threads, Wt);
+    case 8: return f64 ? resident_stream_tma_t<double, 8>(threads, Wt) : resident_stream_tma_t<float, 8>(threads, Wt);
+    case 16: return f64 ? resident_stream_tma_t<double, 16>(threads, Wt) : resident_stream_tma_t<float, 16>(threads, Wt);
     default: return 0;
   }
 }
