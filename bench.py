@@ -49,6 +49,10 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the asynchronous kernel on the
 # 2^20-point rod, from the committed ncu summary of that kernel.
 ASYNC_KERNEL_DRAM_BYTES = 8_486_656 + 2_560
+# DRAM bytes (read + write) per pass of the streamed kernel on the 2^26-point
+# FP32 rod, from the committed ncu summary (T = 1: 4 passes, T = 128: 2
+# passes); a launch makes ceil(K/T) passes of the same traffic.
+STREAM_F32_DRAM_BYTES_PER_PASS = {1: (1_077_127_000 + 1_026_632_000) / 4, 128: (539_179_008 + 487_579_136) / 2}
 
 
 def parse():
@@ -277,7 +281,11 @@ def run_streamed(args):
             if bound == "hbm" else
             {"bound": "alu", "achieved": ups / 1e9, "peak": alu_ups / 1e9, "unit": "Gupdates/s",
              "frac": ups / alu_ups})
-    roof.update({"kernel": "stream_kernel", "peak_source": src, "traffic": None,
+    per_pass = STREAM_F32_DRAM_BYTES_PER_PASS.get(T) if dt == "f32" and N == 1 << 26 else None
+    traffic = None if per_pass is None else per_pass * math.ceil(K / T)
+    roof.update({"kernel": "stream_tma_kernel", "peak_source": src, "traffic": traffic,
+                 "traffic_source": None if traffic is None else
+                 "ncu dram__bytes_read+write of this kernel on this rod, per pass x passes (profiles/)",
                  "hbm_roofline_updates_per_s": hbm_ups, "alu_roofline_updates_per_s": alu_ups,
                  "algorithmic_bytes_per_update": 2.0 * esz / T, "achieved_algorithmic_GBs": achieved_gbs})
     line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
