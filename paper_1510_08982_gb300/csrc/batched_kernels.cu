@@ -149,10 +149,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
       }
       const int mode = tile_mode<E>(fixed);
       __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release_gpu(myflag, 1);  // loaded: neighbours may now overwrite their own points
-      }
+      if (tid == 0) st_release_gpu(myflag, 1);  // loaded: neighbours may now overwrite their own points
       bool ok = true;
       int epoch = 0;
       for (int64_t k0 = 0; k0 < rd.K; k0 += T) {
@@ -169,7 +166,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         }
         __syncthreads();
         if (tid == 0) {
-          __threadfence();
+          // A release at GPU scope after the CTA barrier orders every thread's
+          // edge stores before the flag (cumulativity); no separate fence.
           st_release_gpu(myflag, epoch + 2);
           bool w = true;
           if (it.part > 0) w = wait_flag_at_least(myflag - 1, epoch + 2, a.status, a.spin_limit_ns);

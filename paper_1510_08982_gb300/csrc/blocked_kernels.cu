@@ -76,10 +76,9 @@ __device__ __forceinline__ void publish_strips(const real (&v)[E], real* strips,
     if (p >= L && p < L + T) st_cg(mine + T + (p - L), v[e]);
   }
   __syncthreads();
-  if (tid == 0 && !stalled) {
-    __threadfence();
-    st_release_gpu(my_prog, ver);
-  }
+  // A release at GPU scope after the CTA barrier orders every thread's strip
+  // stores before the version (cumulativity); no separate fence.
+  if (tid == 0 && !stalled) st_release_gpu(my_prog, ver);
 }
 
 template <typename real, int E>

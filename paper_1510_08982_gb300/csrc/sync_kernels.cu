@@ -23,11 +23,13 @@ namespace {
 
 // Grid barrier on a counter that starts at zero: arrival number `epoch`
 // (0-based) completes when the counter reaches S*(epoch+1).  Called by one
-// thread per CTA between two __syncthreads().  Returns false on a timeout or a
-// failure raised elsewhere.
+// thread per CTA between two __syncthreads().  The arrival is a release
+// reduction (it orders the CTA's edge stores, seen through the CTA barrier,
+// before it) and the wait an acquire load that reads the last arrival (every
+// arrival is a release on the same counter), so no separate fences.  Returns
+// false on a timeout or a failure raised elsewhere.
 __device__ bool grid_barrier(unsigned* counter, unsigned target, int* status, int64_t limit_ns) {
-  __threadfence();
-  atomicAdd(counter, 1u);
+  red_release_gpu_add(counter, 1u);
   const uint64_t t0 = global_timer_ns();
   unsigned spins = 0;
   while (true) {
@@ -41,7 +43,6 @@ __device__ bool grid_barrier(unsigned* counter, unsigned target, int* status, in
       }
     }
   }
-  __threadfence();
   return true;
 }
 
