@@ -305,7 +305,8 @@ def run_small(args):
     """The small rod (N = 1024 FP64, r = 0.4, c1 = 0, cN = 1, u(0) = sin(pi x) +
     0.5 sin(7 pi x) + x, S = 8, q = 3): latency-bound.  Per-step device times
     of the persistent synchronous run, the free asynchronous run, its replay,
-    the asynchronous run with temporal blocking (T = 64 steps per block), and a
+    the asynchronous run with temporal blocking (the default block length: 32
+    steps on these 128-point segments), and a
     synchronous run relaunched once per step (the paper's structure without its
     host copies); then async vs sync at equal error: the steps and the time to
     ||u(k) - u_ss||_inf <= 1e-6."""

@@ -65,9 +65,9 @@ typedef struct heat1d_opts {
                             length q).  0: 3. */
   int32_t halo_steps;    /* T, steps advanced between two exchanges in the synchronous run
                             (overlapped halos of width T) and the block length of the blocked
-                            asynchronous run.  0: automatic (on-chip runs 64 in FP64, 128 in
-                            FP32, at most the shortest segment; streamed runs 32 in FP64, 128
-                            in FP32).  1: exchange and grid barrier after every step, as in
+                            asynchronous run.  0: automatic (on-chip runs: FP64 64, or 32 when the
+                            shortest segment has fewer than 4096 points; FP32 128; at most the
+                            shortest segment.  Streamed runs 32 in FP64, 128 in FP32).  1: exchange and grid barrier after every step, as in
                             Section 2. */
   int32_t block_threads; /* threads per CTA for the compute warps.  0: automatic. */
   int32_t elems_per_thread; /* points held in registers per thread (2, 4, 8 or 16).  0: automatic. */

@@ -173,7 +173,7 @@ __device__ void pull_loop(const SegmentRun& a, AsyncShared<real, E>& sh, const i
 }
 
 template <typename real, int E>
-__global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_persistent_kernel(SegmentRun a) {
+__global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_persistent_kernel(SegmentRun a) {
   using Win = Window<E, async_window_halo(sizeof(real), E)>;
   constexpr int kRefresh = Win::H;  // steps between two halo refreshes
   __shared__ AsyncShared<real, E> sh;

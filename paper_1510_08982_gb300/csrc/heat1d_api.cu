@@ -135,10 +135,11 @@ int configure(heat1d* h, const heat1d_opts& o) {
   // On-chip synchronous runs take halos from the neighbouring segment only,
   // so their T is at most the shortest segment (clamped unless on-chip mode
   // was asked for explicitly).
-  // Default depth: 64 steps in FP64, 128 in FP32, where a step costs less
-  // and the exchange weighs more (measured best on GB300 for 2^20- and
-  // 2^21-point rods on 152 segments).
-  int T = o.halo_steps ? o.halo_steps : (h->esize == 4 ? 128 : 64);
+  // Default depth (measured best on GB300): FP32 128 steps, where a step
+  // costs little and the exchange weighs more; FP64 64 steps on segments of
+  // 4096 points or more and 32 on shorter ones, where the halo's redundant
+  // arithmetic (2T per segment) weighs more.
+  int T = o.halo_steps ? o.halo_steps : (h->esize == 4 ? 128 : (Lmin >= 4096 ? 64 : 32));
   if (T > Lmin) {
     if (o.halo_steps && o.sync_mode == 1)
       return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: halo_steps exceeds the shortest segment");
@@ -240,7 +241,8 @@ int pick_shape(const heat1d* h, int64_t slots, int reserved, bool async_kernel, 
   for (int i = 0; i < 4; ++i) {
     const int e = prefer16 ? Es16[i] : Es[i];
     if (forced_E && e != forced_E) continue;
-    const int64_t limit = heat1d_impl::max_tile_threads(static_cast<int>(h->esize), e) - reserved;
+    const int64_t limit = (async_kernel ? heat1d_impl::max_async_threads(static_cast<int>(h->esize), e)
+                                        : heat1d_impl::max_tile_threads(static_cast<int>(h->esize), e)) - reserved;
     const int es = static_cast<int>(h->esize);
     const int H = async_kernel ? heat1d_impl::async_window_halo(es, e) : heat1d_impl::sync_window_halo(es, e);
     int64_t t = 32 * heat1d_impl::window_warps(slots, e, H);

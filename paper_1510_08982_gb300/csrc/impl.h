@@ -67,6 +67,11 @@ struct StreamRun {
 // tile of more than 64 bytes per thread needs more than 64 registers per
 // thread, so it is limited to 512 threads.
 constexpr int max_tile_threads(int elem_bytes, int E) { return elem_bytes * E > 64 ? 512 : 1024; }
+// The asynchronous kernel adds its communication warps to the compute
+// threads (within the 1024-thread CTA limit).
+constexpr int max_async_threads(int elem_bytes, int E) {
+  return max_tile_threads(elem_bytes, E) + 32 * kCommWarps > 1024 ? 1024 : max_tile_threads(elem_bytes, E) + 32 * kCommWarps;
+}
 
 // Warp windows (common.cuh): warp w covers 32E positions starting at w*D,
 // D = 32E - 2H, where H (halo points per warp side = steps between two
