@@ -45,6 +45,22 @@ struct AsyncShared {
 
 
 
+// v[idx] for a run-time idx, by a tree of selects on the bits of idx (no
+// local-memory array, log2(E) levels).
+template <typename real, int E>
+__device__ __forceinline__ real pick_slot(const real (&v)[E], int idx) {
+  real t[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) t[e] = v[e];
+#pragma unroll
+  for (int w = 1; w < E; w *= 2) {
+    const bool hi = (idx & w) != 0;
+#pragma unroll
+    for (int e = 0; e + w < E; e += 2 * w) t[e] = hi ? t[e + w] : t[e];
+  }
+  return t[0];
+}
+
 // Waits for the neighbour version this step needs and returns its value.
 // Returns false if the wait ran out or the run failed elsewhere.
 template <typename real>
@@ -238,7 +254,11 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
     if (g == end_lo) x = c1;
     if (g == end_hi) x = cN;
     v[e] = x;
-    if (p == 0 || p >= L + 1 || g <= end_lo || g >= end_hi) fixed |= 1u << e;
+    // Only points outside the rod and the Dirichlet ends are held.  The halo
+    // positions 0 and L+1 are written before every step that reads them, and
+    // positions past L+1 reach no point of the segment, so those warps can
+    // step without the per-point selects of the masked mode.
+    if (g <= end_lo || g >= end_hi) fixed |= 1u << e;
     const bool own = Win::owner(warp, lane, e, nwc);
     if (p == 1 && own) e_first = e;
     if (p == L && own) e_last = e;
@@ -337,16 +357,12 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
             if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) row[a0 - 1 + p] = v[e];
           }
         }
-        if (e_first >= 0) {
-#pragma unroll
-          for (int e = 0; e < E; ++e)
-            if (e == e_first) sh.own_l[j] = v[e];
+        if (e_first >= 0) {  // position 1: always slot 1 of lane 0 in warp 0
+          sh.own_l[j] = v[1];
           st_release_cta_shared(&sh.own_l_ver, ver);
         }
         if (e_last >= 0) {
-#pragma unroll
-          for (int e = 0; e < E; ++e)
-            if (e == e_last) sh.own_r[j] = v[e];
+          sh.own_r[j] = pick_slot<real, E>(v, e_last);
           st_release_cta_shared(&sh.own_r_ver, ver);
         }
       }
