@@ -323,14 +323,17 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
       else if (mode == kTileMasked)
         warp_steps<real, E, kTileMasked>(v, fixed, coef, n);
     } else {
-      for (int k = k0; k < k0 + n; ++k) {
+      // One step from `in` to `out`: the halo reads before it, the state
+      // records and edge hand-offs after it.  Steps alternate between v and
+      // w, so the loop carries no register rotation.
+      auto edge_step = [&](real (&in)[E], real (&out)[E], int k) {
         if (left_reader && !failed) {
           const int d = dl_next;
           if (trace_in && k + 1 < K) dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
           real val;
           if (fetch_halo<real>(a, &sh.lavail, sh.lring, k, trace_in, trace_out, static_cast<size_t>(k) * tstride + tl,
                                d, val))
-            v[0] = val;
+            in[0] = val;
           else
             failed = true;
         }
@@ -342,29 +345,47 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
                                d, val)) {
 #pragma unroll
             for (int e = 0; e < E; ++e)
-              if (e == e_rh) v[e] = val;
+              if (e == e_rh) in[e] = val;
           } else {
             failed = true;
           }
         }
-        warp_step_any<real, E>(mode, v, fixed, coef);
+        if (mode == kTileFree) {
+          warp_step_to<real, E, kTileFree>(in, out, fixed, coef);
+        } else if (mode == kTileMasked) {
+          warp_step_to<real, E, kTileMasked>(in, out, fixed, coef);
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) out[e] = in[e];
+        }
         const int ver = k + 1, j = ver & (a.R - 1);
         if (snap && ver % a.snap_every == 0) {  // owners record the state at step ver
           real* row = snap + static_cast<size_t>(ver / a.snap_every) * N;
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int p = Win::pos(warp, lane, e);
-            if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) row[a0 - 1 + p] = v[e];
+            if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) row[a0 - 1 + p] = out[e];
           }
         }
         if (e_first >= 0) {  // position 1: always slot 1 of lane 0 in warp 0
-          sh.own_l[j] = v[1];
+          sh.own_l[j] = out[1];
           st_release_cta_shared(&sh.own_l_ver, ver);
         }
         if (e_last >= 0) {
-          sh.own_r[j] = pick_slot<real, E>(v, e_last);
+          sh.own_r[j] = pick_slot<real, E>(out, e_last);
           st_release_cta_shared(&sh.own_r_ver, ver);
         }
+      };
+      real w[E];
+      int k = k0;
+      for (; k + 1 < k0 + n; k += 2) {
+        edge_step(v, w, k);
+        edge_step(w, v, k + 1);
+      }
+      if (k < k0 + n) {
+        edge_step(v, w, k);
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = w[e];
       }
     }
     // Refresh the warp halos after every run of kRefresh steps (and after the
