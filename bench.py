@@ -48,7 +48,7 @@ FP64_INSTR_PER_UPDATE = 3
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the asynchronous kernel on the
 # 2^20-point rod, from the committed ncu summary of that kernel.
-ASYNC_KERNEL_DRAM_BYTES = 8_486_656 + 2_560
+ASYNC_KERNEL_DRAM_BYTES = 8_503_552 + 1_792
 # DRAM bytes (read + write) per pass of the streamed kernel on the 2^26-point
 # FP32 rod, from the committed ncu summary (T = 1: 4 passes, T = 128: 2
 # passes); a launch makes ceil(K/T) passes of the same traffic.
