@@ -567,7 +567,10 @@ def run_inverse(args):
     dt_s = _max_over_ranks(torch, world, dt_s, dev)
     updates = nr * (N - 2) * K
     ups = world * updates / dt_s
-    alu = (FP64_NOMINAL_TFLOPS * 1e12 / 2) / 3
+    # FP64-pipe instructions per forward update over the three passes: 3
+    # (forward) + 3 (recompute) + 5 (backward: t, the r-gradient term and the
+    # lambda update, 2 + 1 + 2); the peak in forward-equivalent updates/s
+    alu = (FP64_NOMINAL_TFLOPS * 1e12 / 2) / (3 + 3 + 5)
     line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dt, "data": "synthetic",
@@ -579,7 +582,8 @@ def run_inverse(args):
             "gradient": {"grad_r_first_rods": [float(x) for x in out[2][:4]], "loss_first_rods": [float(x) for x in out[3][:4]]},
             "roofline": {"bound": "alu", "kernel": "adj_fwd_step / adj_bwd_step", "achieved": ups / 1e9,
                          "peak": alu / 1e9, "unit": "Gupdates/s (forward-equivalent)", "frac": ups / alu,
-                         "note": "three passes (forward, recompute, backward) per forward update"},
+                         "note": "three passes per forward update: forward and recompute 3 FP64 instructions "
+                                 "per point, backward 5; peak = nominal FP64 instruction rate / 11"},
             "clocks": clk, "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
