@@ -1,9 +1,17 @@
 """Rank logic of multi-GPU runs (one process per GPU, launched by torchrun).
 
-The path shards by independent rods: every rank advances its own rod(s) with
-no collective on the data path (weak scaling).  The only communication is
-host-side bookkeeping: barriers around the timed region and the maximum of
-the ranks' times, from which the whole-job throughput is computed.
+The benchmark shards by independent rods: every rank advances its own rod(s)
+with no collective on the data path (weak scaling).  The only communication
+there is host-side bookkeeping: barriers around the timed region and the
+maximum of the ranks' times, from which the whole-job throughput is computed.
+
+One rod can also be sharded: rank k owns the contiguous chunk ``chunk(N, W,
+k)`` (the paper's PE decomposition of Fig. 1 with one PE per GPU) and trades
+T-wide edge strips with its two neighbours once per block of T steps
+(``blocks``): synchronously (every strip current) or in the blocked
+asynchronous model (a strip up to q-1 blocks old, ``StripHistory``).  These
+helpers hold that protocol's host logic; the exchange itself is a send and a
+receive per neighbour and block.
 """
 from __future__ import annotations
 
@@ -46,3 +54,54 @@ def whole_job_rate(units_per_rank, seconds_max: float, world: int) -> float:
     list with one entry per rank."""
     total = units_per_rank * world if isinstance(units_per_rank, (int, float)) else sum(units_per_rank)
     return total / seconds_max
+
+
+# ----------------------------------------------------------------------------- one rod over several ranks
+
+
+def chunk(N: int, world: int, rank: int):
+    """Contiguous points [lo, hi) of rank `rank` when one rod of N points is
+    split over `world` ranks (the first N % world ranks get one more point,
+    the rule of the segment split)."""
+    return shard(N, rank, world)
+
+
+def neighbours(rank: int, world: int, periodic: bool = False):
+    """(left, right) neighbour ranks of a chunk; -1 where the rod ends."""
+    left = rank - 1 if rank > 0 else (world - 1 if periodic and world > 1 else -1)
+    right = rank + 1 if rank + 1 < world else (0 if periodic and world > 1 else -1)
+    return left, right
+
+
+def blocks(K: int, T: int):
+    """The blocks of a run of K steps, T steps per exchange: (first step,
+    steps) pairs, the last one possibly shorter."""
+    if T < 1:
+        raise ValueError("T must be >= 1")
+    return [(k0, min(T, K - k0)) for k0 in range(0, K, T)]
+
+
+class StripHistory:
+    """The last q strips received from one neighbour, by version (version b =
+    the neighbour's edge at the start of block b).  ``get(b, d)`` returns the
+    strip that block b reads with delay d (clamped to b, as no strip is older
+    than version 0) and fails loudly if it is not held."""
+
+    def __init__(self, q: int):
+        if q < 1:
+            raise ValueError("q must be >= 1")
+        self.q = q
+        self._strips = {}
+
+    def put(self, version: int, strip):
+        self._strips[version] = strip
+        for v in [v for v in self._strips if v <= version - self.q]:
+            del self._strips[v]
+
+    def get(self, block: int, delay: int):
+        if delay >= self.q:
+            raise ValueError("delay %d outside the window q = %d" % (delay, self.q))
+        v = block - min(delay, block)
+        if v not in self._strips:
+            raise KeyError("strip version %d is not held" % v)
+        return self._strips[v]
