@@ -67,10 +67,12 @@ typedef struct heat1d_opts {
                             (overlapped halos of width T) and the block length of the blocked
                             asynchronous run.  0: automatic (on-chip runs: FP64 64, or 32 when the
                             shortest segment has fewer than 4096 points; FP32 128; at most the
-                            shortest segment.  Streamed runs 32 in FP64, 128 in FP32).  1: exchange and grid barrier after every step, as in
-                            Section 2. */
-  int32_t block_threads; /* threads per CTA for the compute warps.  0: automatic. */
-  int32_t elems_per_thread; /* points held in registers per thread (2, 4, 8 or 16).  0: automatic. */
+                            shortest segment.  Streamed runs 32 in FP64, 128 in FP32).
+                            1: exchange and grid barrier after every step, as in Section 2. */
+  int32_t block_threads; /* threads per CTA for the compute warps (a multiple of 32; at most 512 in
+                            streamed runs, which add a loader and a releaser warp).  0: automatic. */
+  int32_t elems_per_thread; /* points held in registers per thread (2, 4, 8 or 16; streamed runs
+                            4, 8 or 16).  0: automatic. */
   int64_t spin_limit_ns; /* bound on every device-side wait.  0: 2e9 (2 s). */
   int32_t stall_segment; /* fault injection for tests: when >= 0, that segment of an asynchronous
                             run never publishes, so its neighbours' waits run out and the run
@@ -78,7 +80,8 @@ typedef struct heat1d_opts {
   int32_t sync_mode;     /* synchronous run: 0 automatic, 1 on-chip (one CTA per segment, the
                             segment in registers), 2 streamed (temporal blocking through HBM:
                             tiles of block_threads * elems_per_thread points, halo_steps steps
-                            per pass).  Automatic picks on-chip when every segment fits one CTA. */
+                            per pass, each tile copied into shared memory by one bulk copy).
+                            Automatic picks on-chip when every segment fits one CTA. */
   int32_t boundary;      /* 0: Dirichlet ends (Section 2).  1: periodic (Section 5.3): the two end
                             points are updated too, each with the other as its outer neighbour;
                             c1 and cN are then unused.  Periodic runs are on-chip synchronous runs
