@@ -233,3 +233,65 @@ int SUF(oracle_async_blocked)(int64_t N, REAL r, REAL c1, REAL cN, int64_t S, in
   free(tb_);
   return ORACLE_OK;
 }
+
+/* The blocked asynchronous model on the periodic ring (Section 5.3): as
+ * oracle_async_blocked, with S >= 2 segments on a ring.  Segment s takes its
+ * left halo (the T points before its first point, indices mod N) from
+ * W_{b-dL} and its right halo (the T points after its last one) from
+ * W_{b-dR}; boundary b joins segment b and (b+1) mod S, so the trace is
+ * uint8[ceil(K/T)][S][2] (side 0: segment b reads its right neighbour; side
+ * 1: segment (b+1) mod S reads its left one).  No point is held except the
+ * tile's two outermost ones.  T may not exceed the shortest segment.  With
+ * S = 2 both halos come from the one neighbour; where 2T exceeds its length
+ * they share points, each strip keeping its own copy (the tile holds
+ * L + 2T values). */
+int SUF(oracle_async_blocked_periodic)(int64_t N, REAL r, int64_t S, int q, int64_t T, const REAL* u0, int64_t K,
+                                       const uint8_t* trace, REAL* out) {
+  if (N < 3 || K < 0 || S < 2 || S > N || q < 1 || q > 255 || T < 1 || !u0 || !out) return ORACLE_EINVAL;
+  int64_t nb = (K + T - 1) / T;
+  if (T > N / S) return ORACLE_EINVAL;
+  if (nb > 0 && !trace) return ORACLE_EINVAL;
+  for (int64_t j = 0; j < nb * S * 2; ++j)
+    if (trace[j] >= q) return ORACLE_ETRACE;
+  int64_t Q = (int64_t)q + 1;
+  int64_t M = N / S + 1 + 2 * T; /* longest tile */
+  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S + 1));
+  REAL* W = (REAL*)malloc(sizeof(REAL) * (size_t)N * (size_t)Q);
+  REAL* ta = (REAL*)malloc(sizeof(REAL) * (size_t)M);
+  REAL* tb_ = (REAL*)malloc(sizeof(REAL) * (size_t)M);
+  if (!off || !W || !ta || !tb_) { free(off); free(W); free(ta); free(tb_); return ORACLE_ENOMEM; }
+  oracle_segments(N, S, off);
+#define WB(b, i) W[(size_t)((b) % Q) * (size_t)N + (size_t)(i)]
+  for (int64_t i = 0; i < N; ++i) WB(0, i) = u0[i];
+  for (int64_t b = 0; b < nb; ++b) {
+    int64_t steps = K - b * T < T ? K - b * T : T;
+    for (int64_t s = 0; s < S; ++s) {
+      int64_t lo = off[s], hi = off[s + 1], len = hi - lo + 2 * T; /* tile: T + own + T */
+      int64_t dl = trace[(b * S + (s + S - 1) % S) * 2 + 1], dr = trace[(b * S + s) * 2 + 0];
+      int64_t bl = b - (dl < b ? dl : b), br = b - (dr < b ? dr : b);
+      for (int64_t x = 0; x < len; ++x) {
+        int64_t g = ((lo - T + x) % N + N) % N;
+        ta[x] = x < T ? WB(bl, g) : (x >= len - T ? WB(br, g) : WB(b, g));
+      }
+      REAL* xa = ta;
+      REAL* ya = tb_;
+      for (int64_t j = 0; j < steps; ++j) {
+        ya[0] = xa[0];
+        ya[len - 1] = xa[len - 1];
+        for (int64_t x = 1; x < len - 1; ++x) {
+          REAL uL = xa[x - 1], u = xa[x], uR = xa[x + 1];
+          ya[x] = FMA(r, (uR - (REAL)2 * u) + uL, u);
+        }
+        REAL* t = xa; xa = ya; ya = t;
+      }
+      for (int64_t i = lo; i < hi; ++i) WB(b + 1, i) = xa[T + (i - lo)];
+    }
+  }
+  for (int64_t i = 0; i < N; ++i) out[i] = WB(nb, i);
+#undef WB
+  free(off);
+  free(W);
+  free(ta);
+  free(tb_);
+  return ORACLE_OK;
+}

@@ -253,3 +253,37 @@ def brute_async_blocked_fraction(u0, r, c1, cN, S, q, T, K, trace):
             new[lo:hi] = z[lo:hi]
         W.append(new)
     return W[nb]
+
+
+def brute_async_blocked_periodic_fraction(u0, r, S, q, T, K, trace):
+    """The blocked asynchronous model on the periodic ring, exactly: for block
+    b and segment s the composite vector (W_b with the T points before the
+    segment, indices mod N, from W_{b-dL} and the T points after it from
+    W_{b-dR}) is multiplied tb times by the circulant matrix; the segment's
+    entries of the product are its part of W_{b+1}.  trace: (nb, S, 2),
+    delays clamped to b; boundary b joins segment b and (b+1) mod S."""
+    N = len(u0)
+    A = periodic_matrix_fraction(N, r)
+    off = [0]
+    base, extra = divmod(N, S)
+    for s in range(S):
+        off.append(off[-1] + base + (1 if s < extra else 0))
+    W = [[_frac(v) for v in u0]]
+    trace = np.asarray(trace)
+    nb = (K + T - 1) // T
+    for b in range(nb):
+        tb = min(T, K - b * T)
+        new = list(W[b])
+        for s in range(S):
+            lo, hi = off[s], off[s + 1]
+            bl = b - int(trace[b][(s - 1) % S][1])
+            br = b - int(trace[b][s][0])
+            z = list(W[b])
+            for x in range(1, T + 1):
+                z[(lo - x) % N] = W[bl][(lo - x) % N]
+                z[(hi - 1 + x) % N] = W[br][(hi - 1 + x) % N]
+            for _ in range(tb):
+                z = matvec(A, z)
+            new[lo:hi] = z[lo:hi]
+        W.append(new)
+    return W[nb]

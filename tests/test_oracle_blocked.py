@@ -111,3 +111,52 @@ def test_blocked_rejects_bad_arguments():
         oracle.async_blocked(rod.u0, rod.r, rod.c1, rod.cN, 8, 3, 129, 10, np.zeros((1, 7, 2), np.uint8))
     with pytest.raises(ValueError):
         oracle.async_blocked(rod.u0, rod.r, rod.c1, rod.cN, 8, 3, 4, 10, np.zeros((2, 7, 2), np.uint8))
+
+
+# ----------------------------------------------------------------------------- periodic ring (Section 5.3)
+
+
+@pytest.mark.parametrize("T,K", [(1, 200), (5, 200), (16, 333)])
+def test_blocked_periodic_zero_trace_is_periodic_sync(T, K):
+    rng = np.random.default_rng(T)
+    u0 = rng.uniform(-1, 1, size=300)
+    tr = np.zeros((nblocks(K, T), 6, 2), dtype=np.uint8)
+    for dt in (np.float64, np.float32):
+        a = oracle.async_blocked_periodic(u0, 0.4, 6, 3, T, K, tr, dtype=dt)
+        assert np.array_equal(a, oracle.sync_periodic(u0, 0.4, K, dtype=dt))
+
+
+def test_blocked_periodic_T1_is_periodic_async():
+    rng = np.random.default_rng(3)
+    u0 = rng.uniform(-1, 1, size=301)
+    tr = inputs.periodic_delay_trace(250, 7, 3, seed=4)
+    a = oracle.async_blocked_periodic(u0, 0.45, 7, 3, 1, 250, tr)
+    assert np.array_equal(a, oracle.async_periodic(u0, 0.45, 7, 3, 250, tr))
+
+
+@pytest.mark.parametrize("N,S,q,T,K,seed", [(12, 3, 3, 2, 9, 0), (14, 2, 2, 3, 13, 1), (15, 5, 3, 3, 10, 2)])
+def test_blocked_periodic_brute_force_exact(N, S, q, T, K, seed):
+    """Exact rational restatement, on shapes whose two halos do not share a
+    point (2T at most the neighbours' length): the whole-vector form holds
+    one value per point, the tile one copy per strip."""
+    rng = np.random.default_rng(seed)
+    u0 = rng.integers(-16, 17, size=N) / 16.0
+    nb = nblocks(K, T)
+    tr = rng.integers(0, q, size=(nb, S, 2)).astype(np.uint8)
+    trc = np.minimum(tr, np.arange(nb)[:, None, None]).astype(np.uint8)
+    exact = pins.brute_async_blocked_periodic_fraction(u0, Fraction(1, 4), S, q, T, K, trc)
+    got = oracle.async_blocked_periodic(u0, 0.25, S, q, T, K, tr)
+    assert [Fraction(v) for v in got] == exact
+
+
+def test_blocked_periodic_sum_drifts_only_with_delays():
+    """The circulant update conserves the sum; stale strips break that (the
+    'no unique steady state' of Section 5.3), while current ones keep it up to
+    rounding."""
+    rng = np.random.default_rng(8)
+    u0 = rng.uniform(0, 1, size=200)
+    K, T, S, q = 400, 8, 5, 3
+    z = np.zeros((nblocks(K, T), S, 2), dtype=np.uint8)
+    assert abs(oracle.async_blocked_periodic(u0, 0.5, S, q, T, K, z).sum() - u0.sum()) < 1e-10
+    tr = inputs.periodic_delay_trace(nblocks(K, T), S, q, seed=1)
+    assert abs(oracle.async_blocked_periodic(u0, 0.5, S, q, T, K, tr).sum() - u0.sum()) > 1e-6

@@ -58,6 +58,7 @@ def build_mutant(tmp, func, old, new):
     lib.oracle_async_blocked_f64.argtypes = [i64, dbl, dbl, dbl, i64, i32, i64, vp, i64, vp, vp]
     lib.oracle_sync_periodic_f64.argtypes = [i64, dbl, vp, i64, vp]
     lib.oracle_adjoint_f64.argtypes = [i64, dbl, dbl, dbl, i64, i32, vp, i64, vp, vp, vp, vp, vp]
+    lib.oracle_async_blocked_periodic_f64.argtypes = [i64, dbl, i64, i32, i64, vp, i64, vp, vp]
     return lib
 
 
@@ -102,6 +103,19 @@ def pins_blocked(lib):
     return ok and np.array_equal(out, ref)
 
 
+def pins_blocked_periodic(lib):
+    rng = np.random.default_rng(6)
+    N, S, q, T, K = 15, 5, 3, 3, 10
+    u0 = rng.integers(-16, 17, size=N) / 16.0
+    nb = (K + T - 1) // T
+    tr = rng.integers(0, q, size=(nb, S, 2)).astype(np.uint8)
+    trc = np.minimum(tr, np.arange(nb)[:, None, None]).astype(np.uint8)
+    out = np.empty(N)
+    lib.oracle_async_blocked_periodic_f64(N, 0.25, S, q, T, _p(u0), K, _p(tr), _p(out))
+    return [Fraction(v) for v in out] == pins.brute_async_blocked_periodic_fraction(u0, Fraction(1, 4), S, q, T, K,
+                                                                                    trc)
+
+
 def pins_periodic(lib):
     rng = np.random.default_rng(3)
     N, K = 10, 9
@@ -143,6 +157,8 @@ MUTATIONS = [
      "lo - T > 0 ? lo - T : 0", "lo - T + 1 > 0 ? lo - T + 1 : 0"),
     ("blocked: sides swapped", "oracle_async_blocked", pins_blocked,
      "(s - 1)) * 2 + 1]", "(s - 1)) * 2 + 0]"),
+    ("blocked periodic: left halo with the right side's delay", "oracle_async_blocked_periodic",
+     pins_blocked_periodic, "(s + S - 1) % S) * 2 + 1]", "(s + S - 1) % S) * 2 + 0]"),
     ("periodic: wrap-around to the wrong end", "oracle_sync_periodic", pins_periodic,
      "a[(i + N - 1) % N]", "a[(i + N - 2) % N]"),
     ("adjoint: scatter to the wrong time level", "oracle_adjoint_f64", pins_adjoint,
