@@ -181,9 +181,11 @@ int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_devi
  * this is heat1d_run_sync bit for bit; with T = 1 it is Eq. (eqn:async).
  *
  * Trace layout: uint8 trace[b][boundary][side], ceil(K/T) blocks, S-1
- * boundaries, the sides as in heat1d_run_async (side 0: segment b's read of
+ * boundaries (S on the periodic ring, boundary b joining segments b and
+ * (b+1) mod S), the sides as in heat1d_run_async (side 0: segment b's read of
  * its right neighbour; side 1: segment b+1's read of its left neighbour).
- * Dirichlet ends only (boundary = 1 is rejected with HEAT1D_ERR_INVAL). */
+ * Periodic runs (boundary = 1) need S >= 2; with S = 2 both halos come from
+ * the one neighbour, each strip its own copy. */
 
 /* Free-running blocked run of K steps: each segment publishes its two edge
  * strips once per block and starts the next block with its neighbours'
@@ -196,7 +198,8 @@ int heat1d_run_async_blocked(heat1d_t h, int64_t K, uint8_t* trace_out, int trac
  * returns HEAT1D_ERR_TRACE from heat1d_sync() and the state is unspecified). */
 int heat1d_replay_blocked(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device);
 
-/* Size in bytes of a blocked trace of K steps: ceil(K/T) * (S-1) * 2. */
+/* Size in bytes of a blocked trace of K steps: ceil(K/T) * (S-1) * 2
+ * (ceil(K/T) * S * 2 on the periodic ring). */
 int64_t heat1d_blocked_trace_bytes(heat1d_t h, int64_t K);
 
 /* Waits for the handle's stream and returns the device-side status of the

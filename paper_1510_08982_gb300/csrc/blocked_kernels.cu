@@ -11,7 +11,8 @@
 // its version counter, and starts block b+1 with the newest strip of each
 // neighbour that is not newer than b+1 -- waiting only while that strip is
 // more than q-1 blocks old.  The delay d = (b+1) - v of every strip read is
-// recorded, and a replay waits for exactly v = b+1 - d.
+// recorded, and a replay waits for exactly v = b+1 - d.  On the periodic
+// ring (Section 5.3) the neighbours of the end segments are each other.
 //
 // Ring safety: a segment cannot start block b before both neighbours have
 // published version b-q+1, so neighbours drift at most q-1 blocks apart; a
@@ -100,8 +101,11 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
   real* strips = static_cast<real*>(a.rings);  // [S][R][2T]: first T points, last T points
   int* my_prog = a.prog + static_cast<size_t>(s) * kProgStride;
   const bool stalled = s == a.stall_segment;
-  const int sl = s > 0 ? s - 1 : -1;
-  const int sr = s + 1 < S ? s + 1 : -1;
+  const bool periodic = a.periodic != 0;
+  const int sl = s > 0 ? s - 1 : (periodic ? S - 1 : -1);  // neighbours (ring when periodic)
+  const int sr = s + 1 < S ? s + 1 : (periodic ? 0 : -1);
+  const int nbnd = periodic ? S : S - 1;                    // boundaries: S on the ring
+  const int bl = periodic ? (s + S - 1) % S : s - 1;        // boundary read on the left (side 1)
 
   // Position p of the CTA holds global point a0 - T + p (block 0: every
   // strip is version 0, the initial state itself).
@@ -112,10 +116,15 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
     const int p = Win::pos(warp, lane, e);
     const int64_t g = a0 - T + p;
     real x = static_cast<real>(0);
-    if (p < Lh && g >= 0 && g < N) x = uin[g];
-    if (g == 0) x = c1;
-    if (g == N - 1) x = cN;
-    if (p >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
+    if (periodic) {  // halos wrap around the ring
+      if (p < Lh) x = uin[((g % N) + N) % N];
+      if (p >= Lh) fixed |= 1u << e;
+    } else {
+      if (p < Lh && g >= 0 && g < N) x = uin[g];
+      if (g == 0) x = c1;
+      if (g == N - 1) x = cN;
+      if (p >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
+    }
     v[e] = x;
   }
   const int mode = tile_mode<E>(fixed);
@@ -137,7 +146,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
       const int nb = left ? sl : sr;
       int ver = j;
       if (nb >= 0) {
-        const size_t tidx = (static_cast<size_t>(j) * (S - 1) + (left ? s - 1 : s)) * 2 + (left ? 1 : 0);
+        const size_t tidx = (static_cast<size_t>(j) * nbnd + (left ? bl : s)) * 2 + (left ? 1 : 0);
         ver = strip_version(a, a.prog + static_cast<size_t>(nb) * kProgStride, j, tidx);
       }
       sh_v[left ? 0 : 1] = ver;
@@ -145,7 +154,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
     if (blockDim.x <= 32 && tid == 0) {  // one-warp CTA: thread 0 takes both sides
       int ver = j;
       if (sr >= 0) {
-        const size_t tidx = (static_cast<size_t>(j) * (S - 1) + s) * 2 + 0;
+        const size_t tidx = (static_cast<size_t>(j) * nbnd + s) * 2 + 0;
         ver = strip_version(a, a.prog + static_cast<size_t>(sr) * kProgStride, j, tidx);
       }
       sh_v[1] = ver;

@@ -354,7 +354,8 @@ int run_blocked_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_devi
                        int in_on_device) {
   if (K < 0 || K >= INT_MAX) return fail(HEAT1D_ERR_INVAL, "K out of range");
   if (K == 0) return HEAT1D_OK;
-  if (h->opts.boundary == 1) return fail(HEAT1D_ERR_INVAL, "blocked asynchronous runs have Dirichlet ends only");
+  const bool periodic = h->opts.boundary == 1;
+  if (periodic && h->S < 2) return fail(HEAT1D_ERR_INVAL, "periodic blocked runs need at least 2 segments");
   int E = 0, threads = 0;
   int rc = pick_shape(h, h->Lmax + 2 * h->T, 0, false, &E, &threads);
   if (rc) return rc;
@@ -373,7 +374,7 @@ int run_blocked_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_devi
     h->strips_bytes = sbytes;
   }
   const int64_t nb = (K + h->T - 1) / h->T;
-  const size_t tbytes = static_cast<size_t>(nb) * (h->S - 1) * 2;
+  const size_t tbytes = static_cast<size_t>(nb) * (periodic ? h->S : h->S - 1) * 2;
   SegmentRun a = base_run(h, K);
   a.rings = h->strips;
   uint8_t* out_dev = nullptr;
@@ -588,7 +589,7 @@ int heat1d_replay_blocked(heat1d_t h, int64_t K, const uint8_t* trace, int trace
 
 int64_t heat1d_blocked_trace_bytes(heat1d_t h, int64_t K) {
   if (!h || K < 0) return fail(HEAT1D_ERR_INVAL, "bad argument");
-  return (K + h->T - 1) / h->T * (h->S - 1) * 2;
+  return (K + h->T - 1) / h->T * (h->opts.boundary == 1 ? h->S : h->S - 1) * 2;
 }
 
 int64_t heat1d_trace_bytes(heat1d_t h, int64_t K) {

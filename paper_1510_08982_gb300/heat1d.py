@@ -280,8 +280,9 @@ class Heat1d:
     def new_blocked_trace(self, K, device=True):
         """A trace buffer for a blocked run of K steps: (ceil(K/T), S-1, 2) uint8."""
         torch = _torch()
-        T = self.get_opts()["halo_steps"]
-        shape = ((int(K) + T - 1) // T, max(self.S - 1, 0), 2)
+        o = self.get_opts()
+        T = o["halo_steps"]
+        shape = ((int(K) + T - 1) // T, self.S if o.get("boundary", 0) == 1 else max(self.S - 1, 0), 2)
         if device:
             return torch.empty(shape, dtype=torch.uint8, device="cuda")
         return np.empty(shape, dtype=np.uint8)

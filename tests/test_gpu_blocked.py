@@ -150,9 +150,9 @@ def test_blocked_rejects_bad_trace_and_periodic(H):
         h.set_u(rod.u0)  # the handle stays usable
         h.run_sync(10)
         h.sync()
-    with H.Heat1d(rod.N, rod.r, rod.c1, rod.cN, segments=8, q=3, boundary=1) as h:
+    with H.Heat1d(rod.N, rod.r, rod.c1, rod.cN, segments=1, q=3, boundary=1) as h:
         h.set_u(rod.u0)
-        with pytest.raises(H.Heat1dError):
+        with pytest.raises(H.Heat1dError):  # a ring needs two segments
             h.run_async_blocked(10)
 
 
@@ -172,3 +172,38 @@ def test_blocked_stalled_segment_times_out(H):
         h.set_u(rod.u0)
         h.run_async_blocked(rod.K)
         h.sync()
+
+
+# ----------------------------------------------------------------------------- periodic ring (Section 5.3)
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+@pytest.mark.parametrize("N,S,q,T,K", [(1000, 4, 3, 16, 800), (4099, 7, 2, 33, 700), (300, 100, 3, 1, 500),
+                                       (30, 2, 3, 12, 200)])
+def test_blocked_periodic_free_and_replay(H, dtype, N, S, q, T, K):
+    """Free blocked runs on the ring against the oracle through their traces,
+    and seeded replays; (30, 2, T = 12) has a two-segment ring whose halos
+    share points."""
+    npdt = np.float32 if dtype == "float32" else np.float64
+    rng = np.random.default_rng(N + S)
+    u0 = rng.uniform(-1, 1, size=N)
+    with H.Heat1d(N, 0.45, 0.0, 0.0, dtype=dtype, segments=S, q=q, halo_steps=T, boundary=1) as h:
+        tr = h.new_blocked_trace(K)
+        assert tuple(tr.shape) == (nblocks(K, T), S, 2)
+        h.set_u(u0)
+        h.run_async_blocked(K, tr)
+        h.sync()
+        got = h.get_u(device=False)
+        trh = tr.cpu().numpy()
+        assert trh.max() < q
+        assert np.array_equal(got, oracle.async_blocked_periodic(u0, 0.45, S, q, T, K, trh, dtype=npdt))
+        seeded = inputs.periodic_delay_trace(nblocks(K, T), S, q, seed=9)
+        h.set_u(u0)
+        h.replay_blocked(K, seeded)
+        h.sync()
+        assert np.array_equal(h.get_u(device=False),
+                              oracle.async_blocked_periodic(u0, 0.45, S, q, T, K, seeded, dtype=npdt))
+        h.set_u(u0)
+        h.replay_blocked(K, np.zeros((nblocks(K, T), S, 2), dtype=np.uint8))
+        h.sync()
+        assert np.array_equal(h.get_u(device=False), oracle.sync_periodic(u0, 0.45, K, dtype=npdt))

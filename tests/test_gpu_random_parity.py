@@ -1,7 +1,8 @@
 """Randomised GPU parity: seeded random shapes (rod length, segments, delay
 window, halo depth, step count, precision, ends) through every on-chip run
-of the library -- synchronous, asynchronous replay, blocked replay, periodic
-synchronous and asynchronous replay -- against the oracle, bit for bit.
+of the library -- synchronous, asynchronous replay, blocked replay, and on
+the periodic ring synchronous, asynchronous and blocked replay -- against
+the oracle, bit for bit.
 
 The shapes include the degenerate ones (N = 3, one point per segment, K = 0,
 q = 1, T = 1, one segment) so that the corner cases of the segment split,
@@ -96,3 +97,9 @@ def test_random_shape_parity(H, seed):
             h.sync()
             ref = oracle.async_periodic(u0, rs, S, q, K, ptr, dtype=npdt)
             assert np.array_equal(h.get_u(device=False), ref), "periodic replay " + ctx
+            pbtr = inputs.periodic_delay_trace((K + T - 1) // T, S, q, seed=seed + 5)
+            h.set_u(u0)
+            h.replay_blocked(K, pbtr)
+            h.sync()
+            ref = oracle.async_blocked_periodic(u0, rs, S, q, T, K, pbtr, dtype=npdt)
+            assert np.array_equal(h.get_u(device=False), ref), "periodic blocked " + ctx
