@@ -677,6 +677,27 @@ def main():
     per = {name: M * K / (t / args.steps * 1e-3) for name, t in
            (("sync", t_sync), ("async", t_async), ("replay", t_replay))}
 
+    # --- the blocked asynchronous run on the same rod (its own timing, not part of the step) --
+    btr = h.new_blocked_trace(K)
+    h.set_u(u0)
+    h.run_async_blocked(K, btr)
+    h.sync()
+    t_blocked = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        h.set_u(u0)
+        eb0 = torch.cuda.Event(enable_timing=True)
+        eb1 = torch.cuda.Event(enable_timing=True)
+        eb0.record(stream)
+        h.run_async_blocked(K, btr)
+        eb1.record(stream)
+        eb1.synchronize()
+        t_blocked += eb0.elapsed_time(eb1)
+    h.sync()
+    t_blocked = hd.max_over_ranks(t_blocked, world, dev)
+    per["async_blocked"] = M * K / (t_blocked / args.steps * 1e-3)
+    blocked_hist = np.bincount(btr.cpu().numpy().reshape(-1), minlength=Q)[:Q].tolist()
+
     # --- error at the stated tolerance (untimed) -----------------------------------------
     from scipy.fft import dst, idst
     h.set_u(u0)
@@ -753,6 +774,10 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, S),
             "sync_updates_per_s": per["sync"], "async_updates_per_s": per["async"],
             "replay_updates_per_s": per["replay"],
+            "async_blocked_updates_per_s": per["async_blocked"],
+            "async_blocked": {"block_steps": h.get_opts()["halo_steps"], "delay_histogram_blocks": blocked_hist,
+                              "note": "blocked asynchronous run (strips up to q-1 blocks old) on the same rod, "
+                                      "timed on its own, not part of value"},
             "error": {"sync_vs_closed_form_max_abs": err_sync, "async_vs_sync_max_abs": async_vs_sync,
                       "replay_bit_identical": replay_exact, "delay_histogram": hist},
             "roofline": roofline, "clocks": clk, "e2e": e2e,
