@@ -65,6 +65,27 @@ __device__ __forceinline__ int64_t seg_start(int s, int64_t N, int S) {
   return s * base + (s < extra ? s : extra);
 }
 
+// The segment of a thread's points as they increase: one division for the
+// first point, then comparisons only (a thread's points are kAdjThreads
+// apart, far less than a segment is long in the workloads of interest, and
+// any gap is walked).
+struct SegTrack {
+  int s;
+  int64_t lo, hi;  // the current segment's points [lo, hi)
+  __device__ __forceinline__ void init(int64_t i, int64_t N, int S) {
+    s = seg_of(i, N, S);
+    lo = seg_start(s, N, S);
+    hi = seg_start(s + 1, N, S);
+  }
+  __device__ __forceinline__ void advance(int64_t i, int64_t N, int S) {
+    while (i >= hi) {
+      ++s;
+      lo = hi;
+      hi = seg_start(s + 1, N, S);
+    }
+  }
+};
+
 __device__ __forceinline__ int delay_at(const AdjGeom& g, int64_t rod, int64_t k, int b, int side) {
   const int d = g.trace[((rod * g.K + k) * (g.S - 1) + b) * 2 + side];
   return static_cast<int>(d < k ? d : k);
@@ -112,7 +133,17 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step(AdjGeom g, int64_t k
   real* orow = out + rod * g.N;
   const real r = static_cast<real>(g.r[rod]);
   const real one = static_cast<real>(g.N > 0);
+  SegTrack sg{};
+  if (g.trace) sg.init(b0 + threadIdx.x, g.N, g.S);
   for (int64_t i = b0 + threadIdx.x; i < b1; i += kAdjThreads) {
+    bool first = false, last = false;  // the segment's first / last point
+    int s = 0;
+    if (g.trace) {
+      sg.advance(i, g.N, g.S);
+      s = sg.s;
+      first = s > 0 && i == sg.lo;
+      last = s + 1 < g.S && i == sg.hi - 1;
+    }
     real v;
     if (i == 0) {
       v = static_cast<real>(g.c1[rod]);
@@ -120,25 +151,21 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step(AdjGeom g, int64_t k
       v = static_cast<real>(g.cN[rod]);
     } else {
       real uL = ur[i - 1], uR = ur[i + 1];
-      if (g.trace) {
-        const int s = seg_of(i, g.N, g.S);
-        if (s > 0 && i == seg_start(s, g.N, g.S)) {
-          const int d = delay_at(g, rod, k, s - 1, 1);
-          if (d > 0) uL = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1];
-        }
-        if (s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1) {
-          const int d = delay_at(g, rod, k, s, 0);
-          if (d > 0) uR = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + s) * 2 + 0];
-        }
+      if (first) {
+        const int d = delay_at(g, rod, k, s - 1, 1);
+        if (d > 0) uL = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1];
+      }
+      if (last) {
+        const int d = delay_at(g, rod, k, s, 0);
+        if (d > 0) uR = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + s) * 2 + 0];
       }
       v = ftcs(r, one, uL, ur[i], uR);
     }
     orow[i] = v;
-    if (g.trace) {  // boundary points of time k+1 into the history
-      const int s = seg_of(i, g.N, g.S);
+    if (first || last) {  // boundary points of time k+1 into the history
       real* row = eh_row(eh, g, k + 1 - t0);
-      if (s > 0 && i == seg_start(s, g.N, g.S)) row[(rod * (g.S - 1) + (s - 1)) * 2 + 0] = v;
-      if (s + 1 < g.S && i == seg_start(s + 1, g.N, g.S) - 1) row[(rod * (g.S - 1) + s) * 2 + 1] = v;
+      if (first) row[(rod * (g.S - 1) + (s - 1)) * 2 + 0] = v;
+      if (last) row[(rod * (g.S - 1) + s) * 2 + 1] = v;
     }
   }
 }
@@ -211,6 +238,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
   // The additions are issued as fused multiply-adds by a run-time 1.0 (exact,
   // the same rounded sums): the FP64 pipe sustains DFMA at a higher rate.
   const double one = static_cast<double>(g.N > 0);
+  SegTrack sg{};
+  if (g.trace) sg.init(b0 + threadIdx.x, g.N, g.S);
   for (int64_t i = b0 + threadIdx.x; i < b1; i += kAdjThreads) {
     const int64_t base = rod * g.N;
     const int64_t N = g.N;
@@ -227,9 +256,10 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
       double tl = t;      // t without the neighbour terms that arrive delayed
       double pending = 0.0;
       if (g.trace) {
-        const int s = seg_of(i, N, g.S);
-        const bool first = s > 0 && i == seg_start(s, N, g.S);
-        const bool last = s + 1 < g.S && i == seg_start(s + 1, N, g.S) - 1;
+        sg.advance(i, N, g.S);
+        const int s = sg.s;
+        const bool first = s > 0 && i == sg.lo;
+        const bool last = s + 1 < g.S && i == sg.hi - 1;
         if (first || last) {
           double* prow = pend + (k % g.Q) * g.nrods * (g.S - 1) * 2;
           if (first) {
