@@ -12,10 +12,13 @@
 // received).  Separate warps let the publish fence and the two neighbours'
 // L2 round trips overlap.
 //
-// At step k a compute warp takes, from that local buffer, the newest
-// neighbour version v <= k; it waits only while v < k-q+1 (bounded delay,
-// k* in {k, ..., k-q+1}).  It records d = k - v for the trace.  In replay mode
-// it waits for, and takes, exactly v = k - min(d, k) from the given trace.
+// At step k the compute warp holding a halo takes, from that local buffer,
+// the newest neighbour version v <= k; it waits only while v < k-q+1 (bounded
+// delay, k* in {k, ..., k-q+1}).  It records d = k - v for the trace.  In
+// replay mode it waits for, and takes, exactly v = k - min(d, k) from the
+// given trace.  Only the two edge warps (halo reads, edge hand-offs) stop
+// after every step; the other compute warps advance each run of refresh steps
+// at once, and all meet at the warp-halo refresh.
 //
 // Flow control: a segment cannot start step k until both neighbours have
 // published version k-q+1, so no two neighbours drift more than q steps
