@@ -71,6 +71,7 @@ def parse():
                         "temporal-blocking rod; uneven-rods: 4096 rods in one batched launch")
     p.add_argument("--dtype", default=None, choices=["f32", "f64"], help="streamed-rod / uneven-rods precision")
     p.add_argument("--halo", type=int, default=0, help="streamed-rod: steps per HBM pass (T)")
+    p.add_argument("--r", type=float, default=0.25, help="streamed-rod: r (the sweep's values are 0.1, 0.25, 0.5)")
     p.add_argument("--rods", type=int, default=256, help="inverse-problem: rods in the batch")
     p.add_argument("--async-trace", action="store_true", help="inverse-problem: replayed asynchronous run")
     return p.parse_args()
@@ -231,8 +232,9 @@ def _max_over_ranks(torch, world, x, dev):
 
 
 def run_streamed(args):
-    """The 2^26-point rod (c1 = cN = 0, u(0) ~ U[0,1), r = 0.25, K = 1e4)
-    advanced by the streamed synchronous run, T steps per HBM pass."""
+    """The 2^26-point rod (c1 = cN = 0, u(0) ~ U[0,1), r = --r, 0.25 by
+    default, K = 1e4) advanced by the streamed synchronous run, T steps per HBM
+    pass."""
     torch, rank, world, local = _device_setup()
     from paper_1510_08982_gb300 import heat1d, inputs
     dev = torch.device("cuda", local)
@@ -244,7 +246,7 @@ def run_streamed(args):
     tdt = torch.float32 if dt == "f32" else torch.float64
     g = torch.Generator(device=dev).manual_seed(hd_seed(rank))
     u0 = torch.rand(N, dtype=tdt, device=dev, generator=g)
-    h = heat1d.Heat1d(N, 0.25, 0.0, 0.0, dtype="float32" if dt == "f32" else "float64", sync_mode=2, halo_steps=T)
+    h = heat1d.Heat1d(N, args.r, 0.0, 0.0, dtype="float32" if dt == "f32" else "float64", sync_mode=2, halo_steps=T)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         h.set_u(u0)
@@ -291,8 +293,8 @@ def run_streamed(args):
     line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dt, "data": "synthetic",
-            "config": {"workload": "streamed rod: N=%d %s, r=0.25, c1=cN=0, u(0)~U[0,1), K=%d, T=%d steps per "
-                                   "HBM pass" % (N, dt.upper(), K, T), "N": N, "K": K, "T": T,
+            "config": {"workload": "streamed rod: N=%d %s, r=%g, c1=cN=0, u(0)~U[0,1), K=%d, T=%d steps per "
+                                   "HBM pass" % (N, dt.upper(), args.r, K, T), "N": N, "K": K, "T": T, "r": args.r,
                        "l2": "inputs larger than L2 (%d MB state)" % (N * esz >> 20)},
             "roofline": roof, "clocks": clk, "gpu_launches": 2 * args.steps}
     if rank == 0:
@@ -569,8 +571,20 @@ def run_inverse(args):
     ups = world * updates / dt_s
     # FP64-pipe instructions per forward update over the three passes: 3
     # (forward) + 3 (recompute) + 5 (backward: t, the r-gradient term and the
-    # lambda update, 2 + 1 + 2); the peak in forward-equivalent updates/s
-    alu = (FP64_NOMINAL_TFLOPS * 1e12 / 2) / (3 + 3 + 5)
+    # lambda update, 2 + 1 + 2); the peak in forward-equivalent updates/s.  In
+    # FP32 the forward and recompute passes run in FP32 and stream the state
+    # (read + write, 8 bytes per point and step, each pass: one launch per
+    # step over all rods, state larger than L2); the backward stays FP64.
+    fp64_rate = FP64_NOMINAL_TFLOPS * 1e12 / 2
+    if dt == "f64":
+        alu = fp64_rate / (3 + 3 + 5)
+        roof_note = ("three passes per forward update: forward and recompute 3 FP64 instructions per point, "
+                     "backward 5; peak = nominal FP64 instruction rate / 11")
+    else:
+        hbm = float(measured_peaks()[0].get("hbm_gbs", 6800.0)) * 1e9
+        alu = 1.0 / (5.0 / fp64_rate + 2 * 8.0 / hbm)
+        roof_note = ("FP32 forward and recompute passes bound by HBM (8 bytes per point and step each, measured "
+                     "HBM), FP64 backward by 5 FP64 instructions per point; peak = 1 / (5/FP64 rate + 16 B/HBM)")
     line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dt, "data": "synthetic",
@@ -582,8 +596,7 @@ def run_inverse(args):
             "gradient": {"grad_r_first_rods": [float(x) for x in out[2][:4]], "loss_first_rods": [float(x) for x in out[3][:4]]},
             "roofline": {"bound": "alu", "kernel": "adj_fwd_step / adj_bwd_step", "achieved": ups / 1e9,
                          "peak": alu / 1e9, "unit": "Gupdates/s (forward-equivalent)", "frac": ups / alu,
-                         "note": "three passes per forward update: forward and recompute 3 FP64 instructions "
-                                 "per point, backward 5; peak = nominal FP64 instruction rate / 11"},
+                         "note": roof_note},
             "clocks": clk, "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
