@@ -301,6 +301,36 @@ int ensure_trace_staging(heat1d* h, size_t bytes) {
   return HEAT1D_OK;
 }
 
+// Device addresses of a run's trace buffers (tbytes bytes each; none when
+// tbytes is 0, i.e. one segment): a host output trace is written to the
+// staging buffer and copied back after the run, a host input trace is copied
+// into it before; only one of the two may be on the host.
+int stage_traces(heat1d* h, size_t tbytes, uint8_t* trace_out, int out_on_device, const uint8_t* trace_in,
+                 int in_on_device, uint8_t** out_dev, const uint8_t** in_dev) {
+  int rc;
+  *out_dev = nullptr;
+  *in_dev = nullptr;
+  if (trace_out && tbytes) {
+    if (out_on_device) {
+      *out_dev = trace_out;
+    } else {
+      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
+      *out_dev = h->d_trace;
+    }
+  }
+  if (trace_in && tbytes) {
+    if (in_on_device) {
+      *in_dev = trace_in;
+    } else {
+      if (*out_dev && *out_dev == h->d_trace) return fail(HEAT1D_ERR_INVAL, "host trace in and out at once");
+      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
+      HEAT1D_CUDA(cudaMemcpyAsync(h->d_trace, trace_in, tbytes, cudaMemcpyHostToDevice, h->stream));
+      *in_dev = h->d_trace;
+    }
+  }
+  return HEAT1D_OK;
+}
+
 int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device, const uint8_t* trace_in,
                      int in_on_device) {
   if (K < 0 || K >= INT_MAX) return fail(HEAT1D_ERR_INVAL, "K out of range");
@@ -315,27 +345,8 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   const size_t tbytes = static_cast<size_t>(K) * (periodic ? h->S : h->S - 1) * 2;
   SegmentRun a = base_run(h, K);
   uint8_t* out_dev = nullptr;
-  if (trace_out && tbytes) {
-    if (out_on_device) {
-      out_dev = trace_out;
-    } else {
-      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
-      out_dev = h->d_trace;
-    }
-  }
   const uint8_t* in_dev = nullptr;
-  if (trace_in) {
-    if (tbytes == 0) {
-      in_dev = nullptr;  // one segment: nothing to replay
-    } else if (in_on_device) {
-      in_dev = trace_in;
-    } else {
-      if (out_dev && out_dev == h->d_trace) return fail(HEAT1D_ERR_INVAL, "host trace in and out at once");
-      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
-      HEAT1D_CUDA(cudaMemcpyAsync(h->d_trace, trace_in, tbytes, cudaMemcpyHostToDevice, h->stream));
-      in_dev = h->d_trace;
-    }
-  }
+  if ((rc = stage_traces(h, tbytes, trace_out, out_on_device, trace_in, in_on_device, &out_dev, &in_dev))) return rc;
   a.trace_out = out_dev;
   a.trace_in = in_dev;
   HEAT1D_CUDA(cudaMemsetAsync(h->prog, 0xff, sizeof(int) * h->S * heat1d_impl::kProgStride, h->stream));
@@ -378,25 +389,8 @@ int run_blocked_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_devi
   SegmentRun a = base_run(h, K);
   a.rings = h->strips;
   uint8_t* out_dev = nullptr;
-  if (trace_out && tbytes) {
-    if (out_on_device) {
-      out_dev = trace_out;
-    } else {
-      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
-      out_dev = h->d_trace;
-    }
-  }
   const uint8_t* in_dev = nullptr;
-  if (trace_in && tbytes) {
-    if (in_on_device) {
-      in_dev = trace_in;
-    } else {
-      if (out_dev && out_dev == h->d_trace) return fail(HEAT1D_ERR_INVAL, "host trace in and out at once");
-      if ((rc = ensure_trace_staging(h, tbytes))) return rc;
-      HEAT1D_CUDA(cudaMemcpyAsync(h->d_trace, trace_in, tbytes, cudaMemcpyHostToDevice, h->stream));
-      in_dev = h->d_trace;
-    }
-  }
+  if ((rc = stage_traces(h, tbytes, trace_out, out_on_device, trace_in, in_on_device, &out_dev, &in_dev))) return rc;
   a.trace_out = out_dev;
   a.trace_in = in_dev;
   HEAT1D_CUDA(cudaMemsetAsync(h->prog, 0xff, sizeof(int) * h->S * heat1d_impl::kProgStride, h->stream));
