@@ -214,6 +214,19 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+def _build_once(rank, world):
+    """Builds the library (if stale) on rank 0 only; the other ranks wait, so
+    that concurrent ranks never write the same object files."""
+    from paper_1510_08982_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if rank != 0:
+        build.build()  # up to date by now: only checks
+
+
 def _device_setup():
     import torch
     rank, world, local = dist_env()
@@ -221,8 +234,7 @@ def _device_setup():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1510_08982_gb300 import build
-    build.build()
+    _build_once(rank, world)
     return torch, rank, world, local
 
 
@@ -621,8 +633,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1510_08982_gb300 import build, heat1d, inputs
-    build.build()
+    from paper_1510_08982_gb300 import heat1d, inputs
+    _build_once(rank, world)
     dev = torch.device("cuda", local)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     from paper_1510_08982_gb300 import dist as hd
