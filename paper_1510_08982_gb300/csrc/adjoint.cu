@@ -170,6 +170,106 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step(AdjGeom g, int64_t k
   }
 }
 
+template <typename real>
+struct Vec16T;
+template <>
+struct Vec16T<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec16T<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+// The same forward step with 16-byte vectors: a thread updates VN consecutive
+// points per pass and takes its two outer neighbours from the adjacent lanes
+// (lane 0, lane 31 and a lane whose right neighbour is past the block load
+// theirs).  Same arithmetic, delayed reads and history writes as adj_fwd_step.
+// Requires N to be a multiple of VN, so that every rod row and every block
+// starts on a 16-byte boundary and no vector straddles the end of a block.
+template <typename real>
+__global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64_t k, const real* __restrict__ u,
+                                                                real* __restrict__ out, real* eh, int64_t t0) {
+  using V = typename Vec16T<real>::type;
+  constexpr int VN = Vec16T<real>::n;
+  const int64_t rod = blockIdx.x / g.bpr;
+  const int64_t b0 = (blockIdx.x % g.bpr) * g.span;
+  const int64_t b1 = min(b0 + g.span, g.N);
+  const int64_t N = g.N;
+  const real* ur = u + rod * N;
+  real* orow = out + rod * N;
+  const real r = static_cast<real>(g.r[rod]);
+  const real one = static_cast<real>(g.N > 0);
+  const real c1 = static_cast<real>(g.c1[rod]), cN = static_cast<real>(g.cN[rod]);
+  const int lane = threadIdx.x & 31;
+  const int passes = static_cast<int>(g.span / (static_cast<int64_t>(kAdjThreads) * VN));
+  SegTrack sg{};
+  if (g.trace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), N, g.S);
+  for (int pass = 0; pass < passes; ++pass) {  // warp-uniform trip count (the shuffles need every lane)
+    const int64_t i0 = b0 + (static_cast<int64_t>(pass) * kAdjThreads + threadIdx.x) * VN;
+    const bool active = i0 < b1;
+    real x[VN];
+    if (active) {
+      const V w = *reinterpret_cast<const V*>(ur + i0);
+      const real* ws = reinterpret_cast<const real*>(&w);
+#pragma unroll
+      for (int e = 0; e < VN; ++e) x[e] = ws[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < VN; ++e) x[e] = static_cast<real>(0);
+    }
+    real left = __shfl_up_sync(0xffffffffu, x[VN - 1], 1);
+    real right = __shfl_down_sync(0xffffffffu, x[0], 1);
+    if (!active) continue;
+    if (lane == 0) left = i0 > 0 ? ur[i0 - 1] : static_cast<real>(0);
+    if ((lane == 31 || i0 + VN >= b1) && i0 + VN < N) right = ur[i0 + VN];
+    real y[VN];
+#pragma unroll
+    for (int e = 0; e < VN; ++e) {
+      const int64_t i = i0 + e;
+      bool first = false, last = false;
+      int s = 0;
+      if (g.trace) {
+        sg.advance(i, N, g.S);
+        s = sg.s;
+        first = s > 0 && i == sg.lo;
+        last = s + 1 < g.S && i == sg.hi - 1;
+      }
+      real v;
+      if (i == 0) {
+        v = c1;
+      } else if (i == N - 1) {
+        v = cN;
+      } else {
+        real uL = e > 0 ? x[e - 1] : left;
+        real uR = e + 1 < VN ? x[e + 1] : right;
+        if (first) {
+          const int d = delay_at(g, rod, k, s - 1, 1);
+          if (d > 0) uL = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1];
+        }
+        if (last) {
+          const int d = delay_at(g, rod, k, s, 0);
+          if (d > 0) uR = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + s) * 2 + 0];
+        }
+        v = ftcs(r, one, uL, x[e], uR);
+      }
+      y[e] = v;
+      if (first || last) {  // boundary points of time k+1 into the history
+        real* row = eh_row(eh, g, k + 1 - t0);
+        if (first) row[(rod * (g.S - 1) + (s - 1)) * 2 + 0] = v;
+        if (last) row[(rod * (g.S - 1) + s) * 2 + 1] = v;
+      }
+    }
+    V w;
+    real* ws = reinterpret_cast<real*>(&w);
+#pragma unroll
+    for (int e = 0; e < VN; ++e) ws[e] = y[e];
+    *reinterpret_cast<V*>(orow + i0) = w;
+  }
+}
+
 // Block-wide sum of one double per thread in a fixed order: warp shuffles,
 // then the warps' sums in warp order.
 __device__ double block_sum(double x, double* red) {
@@ -309,6 +409,16 @@ __global__ void adj_finish(AdjGeom g, const double* loss_part, const double* gr_
   gr_out[rod] = gs;
 }
 
+// One forward step over all rods: the vector kernel where rows are 16-byte aligned.
+template <typename real>
+void fwd_step(bool vec, dim3 grid, dim3 block, cudaStream_t st, const AdjGeom& g, int64_t k, const real* in,
+              real* out, real* eh, int64_t t0) {
+  if (vec)
+    adj_fwd_step_vec<real><<<grid, block, 0, st>>>(g, k, in, out, eh, t0);
+  else
+    adj_fwd_step<real><<<grid, block, 0, st>>>(g, k, in, out, eh, t0);
+}
+
 template <typename real>
 int adjoint_t(const AdjointRun& a) {
   cudaStream_t st = a.stream;
@@ -374,6 +484,10 @@ int adjoint_t(const AdjointRun& a) {
     return HEAT1D_ERR_CUDA;
   }
   const dim3 grid(static_cast<unsigned>(nblocks)), block(kAdjThreads);
+  // 16-byte vectors where every rod row starts on a 16-byte boundary (the
+  // blocks' span, kAdjThreads * kAdjPointsPerThread, is a multiple of the
+  // vector width times kAdjThreads)
+  const bool vec = N % Vec16T<real>::n == 0 && g.span % (static_cast<int64_t>(kAdjThreads) * Vec16T<real>::n) == 0;
   const int gather_blocks = static_cast<int>(std::min<int64_t>(1024, (std::max<int64_t>(ehw / 2, 1) + 255) / 256));
   adj_force_ends<real><<<static_cast<unsigned>((nr + 127) / 128), 128, 0, st>>>(g, X);  // u(0) with its ends set
   // history rows for times <= 0 all hold u(0) (reads before 0 are clamped, so
@@ -398,7 +512,7 @@ int adjoint_t(const AdjointRun& a) {
       e = cudaMemcpyAsync(ckeh + c * q * ehw, eh, sizeof(real) * q * ehw, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) break;
     for (int64_t j = 0; j < Cc; ++j)
-      adj_fwd_step<real><<<grid, block, 0, st>>>(g, kc + j, X + j * npts, X + (j + 1) * npts, eh, t0);
+      fwd_step<real>(vec, grid, block, st, g, kc + j, X + j * npts, X + (j + 1) * npts, eh, t0);
     if (c == nc - 1 && Cc != C)  // make the final state sit where the next interval would look
       e = cudaMemcpyAsync(X + C * npts, X + Cc * npts, sizeof(real) * npts, cudaMemcpyDeviceToDevice, st);
   }
@@ -421,7 +535,7 @@ int adjoint_t(const AdjointRun& a) {
     if (e == cudaSuccess && async_run)
       e = cudaMemcpyAsync(eh, ckeh + c * q * ehw, sizeof(real) * q * ehw, cudaMemcpyDeviceToDevice, st);
     for (int64_t j = 0; j + 1 < Cc && e == cudaSuccess; ++j)  // states kc .. kc+Cc-1
-      adj_fwd_step<real><<<grid, block, 0, st>>>(g, kc + j, X + j * npts, X + (j + 1) * npts, eh, t0);
+      fwd_step<real>(vec, grid, block, st, g, kc + j, X + j * npts, X + (j + 1) * npts, eh, t0);
     for (int64_t k = kc + Cc - 1; k >= kc; --k) {
       adj_bwd_step<real><<<grid, block, 0, st>>>(g, k, lin, lout, X + (k - kc) * npts, eh, t0, pend,
                                                  parts + nblocks, parts + 2 * nblocks);
