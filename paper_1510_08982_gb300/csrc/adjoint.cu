@@ -395,6 +395,113 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
   if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
 }
 
+// The same backward step, two points per thread and pass: lambda moves as
+// 16-byte double2 vectors and u as 2-element vectors, the outer lambda
+// neighbours come from the adjacent lanes (lane 0, lane 31 and a lane whose
+// right neighbour is past the block load theirs).  Per point the arithmetic,
+// the delayed-read corrections and the pending ring are those of
+// adj_bwd_step; the r-gradient partial of a block is summed in a fixed order
+// (each thread's points in order, then block_sum), so it does not depend on
+// the checkpoint interval.  Requires N even.
+template <typename real>
+__global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, int64_t k, const double* __restrict__ lin,
+                                                                double* __restrict__ lout, const real* __restrict__ u,
+                                                                const real* eh, int64_t t0, double* pend,
+                                                                double* gr_sum, double* gr_comp) {
+  __shared__ double red[kAdjThreads / 32];
+  const int64_t rod = blockIdx.x / g.bpr;
+  const int64_t b0 = (blockIdx.x % g.bpr) * g.span;
+  const int64_t b1 = min(b0 + g.span, g.N);
+  const int64_t N = g.N;
+  const int64_t base = rod * N;
+  const real* ur = u + base;
+  const double r = g.r[rod];
+  const double one = static_cast<double>(g.N > 0);
+  const int lane = threadIdx.x & 31;
+  const int passes = static_cast<int>(g.span / (static_cast<int64_t>(kAdjThreads) * 2));
+  double contrib = 0.0;
+  SegTrack sg{};
+  if (g.trace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * 2, N - 1), N, g.S);
+  for (int pass = 0; pass < passes; ++pass) {  // warp-uniform trip count (the shuffles need every lane)
+    const int64_t i0 = b0 + (static_cast<int64_t>(pass) * kAdjThreads + threadIdx.x) * 2;
+    const bool active = i0 < b1;
+    double L[2] = {0.0, 0.0};
+    if (active) {
+      const double2 w = *reinterpret_cast<const double2*>(lin + base + i0);
+      L[0] = w.x;
+      L[1] = w.y;
+    }
+    double lleft = __shfl_up_sync(0xffffffffu, L[1], 1);
+    double lright = __shfl_down_sync(0xffffffffu, L[0], 1);
+    if (!active) continue;
+    if (lane == 0) lleft = i0 > 0 ? lin[base + i0 - 1] : 0.0;
+    if ((lane == 31 || i0 + 2 >= b1) && i0 + 2 < N) lright = lin[base + i0 + 2];
+    double U[2];
+    if (sizeof(real) == 8) {
+      const double2 w = *reinterpret_cast<const double2*>(ur + i0);
+      U[0] = w.x;
+      U[1] = w.y;
+    } else {
+      const float2 w = *reinterpret_cast<const float2*>(ur + i0);
+      U[0] = static_cast<double>(w.x);
+      U[1] = static_cast<double>(w.y);
+    }
+    double out2[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int64_t i = i0 + e;
+      const double lc = (i >= 1 && i <= N - 2) ? L[e] : 0.0;
+      const double ll = (i - 1 >= 1 && i - 1 <= N - 2) ? (e == 0 ? lleft : L[0]) : 0.0;
+      const double lr = (i + 1 >= 1 && i + 1 <= N - 2) ? (e == 1 ? lright : L[1]) : 0.0;
+      const double t = __fma_rn(one, __fma_rn(-2.0, lc, lr), ll);
+      contrib = __fma_rn(U[e], t, contrib);
+      if (i == 0 || i == N - 1) {
+        out2[e] = 0.0;
+        continue;
+      }
+      double tl = t;      // t without the neighbour terms that arrive delayed
+      double pending = 0.0;
+      if (g.trace) {
+        sg.advance(i, N, g.S);
+        const int s = sg.s;
+        const bool first = s > 0 && i == sg.lo;
+        const bool last = s + 1 < g.S && i == sg.hi - 1;
+        if (first || last) {
+          double* prow = pend + (k % g.Q) * g.nrods * (g.S - 1) * 2;
+          if (first) {
+            double* p = prow + (rod * (g.S - 1) + (s - 1)) * 2 + 0;  // parked from i-1's delayed right reads
+            pending += *p;
+            *p = 0.0;
+            if (delay_at(g, rod, k, s - 1, 0) > 0) tl -= ll;  // i-1 read u_i late: its term is parked
+            const int dL = delay_at(g, rod, k, s - 1, 1);   // this point's own left read
+            if (dL > 0) {
+              const double uLd = static_cast<double>(eh_row(eh, g, k - dL - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1]);
+              contrib += lc * (uLd - static_cast<double>(ur[i - 1]));
+              pend[((k - dL) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + (s - 1)) * 2 + 1] += r * lc;
+            }
+          }
+          if (last) {
+            double* p = prow + (rod * (g.S - 1) + s) * 2 + 1;  // parked from i+1's delayed left reads
+            pending += *p;
+            *p = 0.0;
+            if (delay_at(g, rod, k, s, 1) > 0) tl -= lr;    // i+1 read u_i late
+            const int dR = delay_at(g, rod, k, s, 0);       // this point's own right read
+            if (dR > 0) {
+              const double uRd = static_cast<double>(eh_row(eh, g, k - dR - t0)[(rod * (g.S - 1) + s) * 2 + 0]);
+              contrib += lc * (uRd - static_cast<double>(ur[i + 1]));
+              pend[((k - dR) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + s) * 2 + 0] += r * lc;
+            }
+          }
+        }
+      }
+      out2[e] = __fma_rn(one, __fma_rn(r, tl, lc), pending);
+    }
+    *reinterpret_cast<double2*>(lout + base + i0) = make_double2(out2[0], out2[1]);
+  }
+  const double bs = block_sum(contrib, red);
+  if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
+}
+
 // Per rod: sums of the block partials, in block order.
 __global__ void adj_finish(AdjGeom g, const double* loss_part, const double* gr_sum, double* loss_out,
                            double* gr_out) {
@@ -488,6 +595,7 @@ int adjoint_t(const AdjointRun& a) {
   // blocks' span, kAdjThreads * kAdjPointsPerThread, is a multiple of the
   // vector width times kAdjThreads)
   const bool vec = N % Vec16T<real>::n == 0 && g.span % (static_cast<int64_t>(kAdjThreads) * Vec16T<real>::n) == 0;
+  const bool bvec = N % 2 == 0 && g.span % (static_cast<int64_t>(kAdjThreads) * 2) == 0;  // backward: pairs
   const int gather_blocks = static_cast<int>(std::min<int64_t>(1024, (std::max<int64_t>(ehw / 2, 1) + 255) / 256));
   adj_force_ends<real><<<static_cast<unsigned>((nr + 127) / 128), 128, 0, st>>>(g, X);  // u(0) with its ends set
   // history rows for times <= 0 all hold u(0) (reads before 0 are clamped, so
@@ -537,8 +645,12 @@ int adjoint_t(const AdjointRun& a) {
     for (int64_t j = 0; j + 1 < Cc && e == cudaSuccess; ++j)  // states kc .. kc+Cc-1
       fwd_step<real>(vec, grid, block, st, g, kc + j, X + j * npts, X + (j + 1) * npts, eh, t0);
     for (int64_t k = kc + Cc - 1; k >= kc; --k) {
-      adj_bwd_step<real><<<grid, block, 0, st>>>(g, k, lin, lout, X + (k - kc) * npts, eh, t0, pend,
-                                                 parts + nblocks, parts + 2 * nblocks);
+      if (bvec)
+        adj_bwd_step_vec<real><<<grid, block, 0, st>>>(g, k, lin, lout, X + (k - kc) * npts, eh, t0, pend,
+                                                       parts + nblocks, parts + 2 * nblocks);
+      else
+        adj_bwd_step<real><<<grid, block, 0, st>>>(g, k, lin, lout, X + (k - kc) * npts, eh, t0, pend,
+                                                   parts + nblocks, parts + 2 * nblocks);
       std::swap(lin, lout);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
