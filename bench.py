@@ -139,10 +139,12 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- oracle arm
 
 
-def oracle_sample(rod, seconds=10.0, S=152):
+def oracle_sample(rod, seconds=10.0, S=152, all_cores=False):
     """Times the plain C oracle (single thread) on a bounded sample of the
     workload: the synchronous sweep and the asynchronous replay on the full N
-    for Ks steps, Ks chosen for about `seconds` of CPU work."""
+    for Ks steps, Ks chosen for about `seconds` of CPU work.  With `all_cores`
+    the same sample, at half the steps, also runs as one process per host core
+    (the host's aggregate rate)."""
     import oracle
     N = rod.N
     probe = 4
@@ -159,9 +161,48 @@ def oracle_sample(rod, seconds=10.0, S=152):
     oracle.async_replay(rod.u0, rod.r, rod.c1, rod.cN, S, Q, Ks, tr)
     dt = time.perf_counter() - t0
     updates = 2 * (N - 2) * Ks
-    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "plain C oracle, one thread: synchronous sweep + asynchronous replay (seeded q=3 delays, "
-                      "S=%d) of the N=%d rod for %d steps each (%.1f s)" % (S, N, Ks, dt)}
+    out = {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "plain C oracle, one thread: synchronous sweep + asynchronous replay (seeded q=3 delays, "
+                     "S=%d) of the N=%d rod for %d steps each (%.1f s)" % (S, N, Ks, dt)}
+    if all_cores:
+        out["all_cores"] = oracle_all_cores(rod, S, max(2, Ks // 2))
+    return out
+
+
+_ORACLE_JOB = None
+
+
+def _oracle_init(job):
+    global _ORACLE_JOB
+    import oracle  # noqa: F401  (loaded before the timed region)
+    _ORACLE_JOB = job
+
+
+def _oracle_job(_):
+    import oracle
+    u0, r, c1, cN, S, Ks, tr = _ORACLE_JOB
+    oracle.sync(u0, r, c1, cN, Ks)
+    oracle.async_replay(u0, r, c1, cN, S, Q, Ks, tr)
+    return os.getpid()
+
+
+def oracle_all_cores(rod, S, Ks):
+    """The same single-threaded oracle sample run as one process per host core
+    at once (spawned workers, inputs handed over before the clock starts):
+    the aggregate updates/s of the host.  None on a one-core host."""
+    import multiprocessing as mp
+    P = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    if P < 2:
+        return None
+    from paper_1510_08982_gb300 import inputs
+    job = (rod.u0, rod.r, rod.c1, rod.cN, S, Ks, inputs.delay_trace(Ks, S, Q, seed=0))
+    with mp.get_context("spawn").Pool(P, initializer=_oracle_init, initargs=(job,)) as pool:
+        t0 = time.perf_counter()
+        pids = pool.map(_oracle_job, range(P), chunksize=1)
+        dt = time.perf_counter() - t0
+    updates = P * 2 * (rod.N - 2) * Ks
+    return {"value": updates / dt, "cores": P, "processes_used": len(set(pids)),
+            "sample": "%d concurrent copies of the one-thread sample, %d steps each (%.1f s wall)" % (P, Ks, dt)}
 
 
 def run_reference(args):
@@ -808,7 +849,7 @@ def main():
             "roofline": roofline, "clocks": clk, "e2e": e2e,
             "gpu_launches": 6 * args.steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(rod, seconds=10.0, S=S)
+        line["cpu_baseline"] = oracle_sample(rod, seconds=10.0, S=S, all_cores=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
