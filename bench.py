@@ -622,22 +622,24 @@ def run_inverse(args):
     dt_s = _max_over_ranks(torch, world, dt_s, dev)
     updates = nr * (N - 2) * K
     ups = world * updates / dt_s
-    # FP64-pipe instructions per forward update over the three passes: 3
-    # (forward) + 3 (recompute) + 5 (backward: t, the r-gradient term and the
-    # lambda update, 2 + 1 + 2); the peak in forward-equivalent updates/s.  In
-    # FP32 the forward and recompute passes run in FP32 and stream the state
-    # (read + write, 8 bytes per point and step, each pass: one launch per
-    # step over all rods, state larger than L2); the backward stays FP64.
+    # FP64: FP64-pipe instructions per forward update over the three passes:
+    # 3 (forward) + 3 (recompute) + 5 (backward: t, the r-gradient term and
+    # the lambda update, 2 + 1 + 2); the peak in forward-equivalent updates/s.
+    # FP32: u and lambda in FP32, every pass one launch per step over all rods
+    # streaming its arrays: forward and recompute read u(k) and write u(k+1)
+    # (8 bytes per point and step each), the backward reads u(k) and
+    # lambda(k+1) and writes lambda(k) (12 bytes): 28 bytes per forward update
+    # at the measured HBM rate.
     fp64_rate = FP64_NOMINAL_TFLOPS * 1e12 / 2
     if dt == "f64":
-        alu = fp64_rate / (3 + 3 + 5)
+        bound, alu = "alu", fp64_rate / (3 + 3 + 5)
         roof_note = ("three passes per forward update: forward and recompute 3 FP64 instructions per point, "
                      "backward 5; peak = nominal FP64 instruction rate / 11")
     else:
         hbm = float(measured_peaks()[0].get("hbm_gbs", 6800.0)) * 1e9
-        alu = 1.0 / (5.0 / fp64_rate + 2 * 8.0 / hbm)
-        roof_note = ("FP32 forward and recompute passes bound by HBM (8 bytes per point and step each, measured "
-                     "HBM), FP64 backward by 5 FP64 instructions per point; peak = 1 / (5/FP64 rate + 16 B/HBM)")
+        bound, alu = "hbm", hbm / 28.0
+        roof_note = ("FP32 passes bound by HBM: forward 8 + recompute 8 + backward 12 bytes per point and step; "
+                     "peak = measured HBM / 28 B, in forward-equivalent updates/s")
     line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dt, "data": "synthetic",
@@ -647,7 +649,7 @@ def run_inverse(args):
                                    % (nr, N, K, "replayed trace S=16 q=3" if trace is not None else "synchronous"),
                        "rods": nr, "N": N, "K": K, "ckpt_every": 128},
             "gradient": {"grad_r_first_rods": [float(x) for x in out[2][:4]], "loss_first_rods": [float(x) for x in out[3][:4]]},
-            "roofline": {"bound": "alu", "kernel": "adj_fwd_step / adj_bwd_step", "achieved": ups / 1e9,
+            "roofline": {"bound": bound, "kernel": "adj_fwd_step / adj_bwd_step", "achieved": ups / 1e9,
                          "peak": alu / 1e9, "unit": "Gupdates/s (forward-equivalent)", "frac": ups / alu,
                          "note": roof_note},
             "clocks": clk, "gpu_launches": None}

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -293,11 +294,37 @@ __device__ void kahan_add(double* sum, double* comp, double x) {
   *sum = t;
 }
 
+// The backward step's arithmetic in the run's precision: lambda is stored and
+// stepped in the state's type.  FP64: the additions are issued as fused
+// multiply-adds by a run-time 1.0 (exact, the same rounded sums; the FP64 pipe
+// sustains DFMA at a higher rate than DADD).  FP32: FP32 operations.
+__device__ __forceinline__ double adj_lap(double one, double lc, double ll, double lr) {
+  return __fma_rn(one, __fma_rn(-2.0, lc, lr), ll);
+}
+__device__ __forceinline__ float adj_lap(float, float lc, float ll, float lr) {
+  return __fadd_rn(__fmaf_rn(-2.0f, lc, lr), ll);
+}
+__device__ __forceinline__ double adj_new(double one, double r, double tl, double lc, double pending) {
+  return __fma_rn(one, __fma_rn(r, tl, lc), pending);
+}
+__device__ __forceinline__ float adj_new(float, float r, float tl, float lc, double pending) {
+  return __fadd_rn(__fmaf_rn(r, tl, lc), static_cast<float>(pending));
+}
+// dL/dr products u_i t_i of a thread: FP64 runs sum them in FP64; FP32 runs
+// sum a thread's products (its points of one block) in FP32 and add that sum
+// to the FP64 partials, so that the FP64 pipe is not the bound of an FP32 run.
+__device__ __forceinline__ double adj_prod(double u, double t, double acc) { return __fma_rn(u, t, acc); }
+__device__ __forceinline__ float adj_prod(float u, float t, float acc) { return __fmaf_rn(u, t, acc); }
+// A delayed-read term of dL/dr: into the FP64 sum (FP64 runs keep one sum, in
+// point order).
+__device__ __forceinline__ void adj_term(double& acc, double& /*terms*/, double x) { acc += x; }
+__device__ __forceinline__ void adj_term(float& /*acc*/, double& terms, double x) { terms += x; }
+
 // lambda(K) = u(K) - u_obs on the interior; per-block loss partials.
 // With `cotangent` set, uobs is dL/du(K) itself and the loss is reported 0.
 template <typename real>
 __global__ void __launch_bounds__(kAdjThreads) adj_init(AdjGeom g, const real* __restrict__ uK,
-                                                        const double* __restrict__ uobs, double* __restrict__ lam,
+                                                        const double* __restrict__ uobs, real* __restrict__ lam,
                                                         double* loss_part, int cotangent) {
   __shared__ double red[kAdjThreads / 32];
   const int64_t rod = blockIdx.x / g.bpr;
@@ -308,7 +335,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_init(AdjGeom g, const real* _
     const int64_t x = rod * g.N + i;
     const double e = cotangent ? uobs[x] : static_cast<double>(uK[x]) - uobs[x];
     if (!cotangent) e2 += 0.5 * e * e;
-    lam[x] = (i > 0 && i < g.N - 1) ? e : 0.0;
+    lam[x] = static_cast<real>((i > 0 && i < g.N - 1) ? e : 0.0);
   }
   const double s = block_sum(e2, red);
   if (threadIdx.x == 0) loss_part[blockIdx.x] = s;
@@ -326,34 +353,34 @@ __global__ void __launch_bounds__(kAdjThreads) adj_init(AdjGeom g, const real* _
 //     plus lambda_i (u_{i+-1}(k-d) - u_{i+-1}(k)) where point i read a
 //     neighbour with delay d > 0.
 template <typename real>
-__global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k, const double* __restrict__ lin,
-                                                            double* __restrict__ lout, const real* __restrict__ u,
+__global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k, const real* __restrict__ lin,
+                                                            real* __restrict__ lout, const real* __restrict__ u,
                                                             const real* eh, int64_t t0, double* pend,
                                                             double* gr_sum, double* gr_comp) {
   __shared__ double red[kAdjThreads / 32];
   const int64_t rod = blockIdx.x / g.bpr;
   const int64_t b0 = (blockIdx.x % g.bpr) * g.span;
   const int64_t b1 = min(b0 + g.span, g.N);
-  double contrib = 0.0;
-  // The additions are issued as fused multiply-adds by a run-time 1.0 (exact,
-  // the same rounded sums): the FP64 pipe sustains DFMA at a higher rate.
-  const double one = static_cast<double>(g.N > 0);
+  real acc = 0;          // products u_i t_i (and, in FP64, the delayed-read terms)
+  double contrib = 0.0;  // FP32: the delayed-read terms
+  const real one = static_cast<real>(g.N > 0);
+  const real zero = 0;
   SegTrack sg{};
   if (g.trace) sg.init(b0 + threadIdx.x, g.N, g.S);
   for (int64_t i = b0 + threadIdx.x; i < b1; i += kAdjThreads) {
     const int64_t base = rod * g.N;
     const int64_t N = g.N;
-    const double lc = (i >= 1 && i <= N - 2) ? lin[base + i] : 0.0;
-    const double ll = (i - 1 >= 1 && i - 1 <= N - 2) ? lin[base + i - 1] : 0.0;
-    const double lr = (i + 1 >= 1 && i + 1 <= N - 2) ? lin[base + i + 1] : 0.0;
+    const real lc = (i >= 1 && i <= N - 2) ? lin[base + i] : zero;
+    const real ll = (i - 1 >= 1 && i - 1 <= N - 2) ? lin[base + i - 1] : zero;
+    const real lr = (i + 1 >= 1 && i + 1 <= N - 2) ? lin[base + i + 1] : zero;
     const real* ur = u + base;
-    const double t = __fma_rn(one, __fma_rn(-2.0, lc, lr), ll);
-    contrib = __fma_rn(static_cast<double>(ur[i]), t, contrib);
+    const real t = adj_lap(one, lc, ll, lr);
+    acc = adj_prod(ur[i], t, acc);
     if (i == 0 || i == N - 1) {
-      lout[base + i] = 0.0;
+      lout[base + i] = zero;
     } else {
-      const double r = g.r[rod];
-      double tl = t;      // t without the neighbour terms that arrive delayed
+      const real r = static_cast<real>(g.r[rod]);
+      real tl = t;        // t without the neighbour terms that arrive delayed
       double pending = 0.0;
       if (g.trace) {
         sg.advance(i, N, g.S);
@@ -370,7 +397,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
             const int dL = delay_at(g, rod, k, s - 1, 1);   // this point's own left read
             if (dL > 0) {
               const double uLd = static_cast<double>(eh_row(eh, g, k - dL - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1]);
-              contrib += lc * (uLd - static_cast<double>(ur[i - 1]));
+              adj_term(acc, contrib, static_cast<double>(lc) * (uLd - static_cast<double>(ur[i - 1])));
               pend[((k - dL) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + (s - 1)) * 2 + 1] += r * lc;
             }
           }
@@ -382,16 +409,16 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
             const int dR = delay_at(g, rod, k, s, 0);       // this point's own right read
             if (dR > 0) {
               const double uRd = static_cast<double>(eh_row(eh, g, k - dR - t0)[(rod * (g.S - 1) + s) * 2 + 0]);
-              contrib += lc * (uRd - static_cast<double>(ur[i + 1]));
+              adj_term(acc, contrib, static_cast<double>(lc) * (uRd - static_cast<double>(ur[i + 1])));
               pend[((k - dR) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + s) * 2 + 0] += r * lc;
             }
           }
         }
       }
-      lout[base + i] = __fma_rn(one, __fma_rn(r, tl, lc), pending);
+      lout[base + i] = adj_new(one, r, tl, lc, pending);
     }
   }
-  const double bs = block_sum(contrib, red);
+  const double bs = block_sum(static_cast<double>(acc) + contrib, red);
   if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
 }
 
@@ -404,8 +431,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
 // (each thread's points in order, then block_sum), so it does not depend on
 // the checkpoint interval.  Requires N even.
 template <typename real>
-__global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, int64_t k, const double* __restrict__ lin,
-                                                                double* __restrict__ lout, const real* __restrict__ u,
+__global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, int64_t k, const real* __restrict__ lin,
+                                                                real* __restrict__ lout, const real* __restrict__ u,
                                                                 const real* eh, int64_t t0, double* pend,
                                                                 double* gr_sum, double* gr_comp) {
   __shared__ double red[kAdjThreads / 32];
@@ -415,51 +442,50 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
   const int64_t N = g.N;
   const int64_t base = rod * N;
   const real* ur = u + base;
-  const double r = g.r[rod];
-  const double one = static_cast<double>(g.N > 0);
+  const real r = static_cast<real>(g.r[rod]);
+  const real one = static_cast<real>(g.N > 0);
+  const real zero = 0;
   const int lane = threadIdx.x & 31;
   const int passes = static_cast<int>(g.span / (static_cast<int64_t>(kAdjThreads) * 2));
-  double contrib = 0.0;
+  using V2 = typename std::conditional<sizeof(real) == 8, double2, float2>::type;
+  real acc = 0;          // products u_i t_i (and, in FP64, the delayed-read terms)
+  double contrib = 0.0;  // FP32: the delayed-read terms
   SegTrack sg{};
   if (g.trace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * 2, N - 1), N, g.S);
   for (int pass = 0; pass < passes; ++pass) {  // warp-uniform trip count (the shuffles need every lane)
     const int64_t i0 = b0 + (static_cast<int64_t>(pass) * kAdjThreads + threadIdx.x) * 2;
     const bool active = i0 < b1;
-    double L[2] = {0.0, 0.0};
+    real L[2] = {zero, zero};
     if (active) {
-      const double2 w = *reinterpret_cast<const double2*>(lin + base + i0);
+      const V2 w = *reinterpret_cast<const V2*>(lin + base + i0);
       L[0] = w.x;
       L[1] = w.y;
     }
-    double lleft = __shfl_up_sync(0xffffffffu, L[1], 1);
-    double lright = __shfl_down_sync(0xffffffffu, L[0], 1);
+    real lleft = __shfl_up_sync(0xffffffffu, L[1], 1);
+    real lright = __shfl_down_sync(0xffffffffu, L[0], 1);
     if (!active) continue;
-    if (lane == 0) lleft = i0 > 0 ? lin[base + i0 - 1] : 0.0;
+    if (lane == 0) lleft = i0 > 0 ? lin[base + i0 - 1] : zero;
     if ((lane == 31 || i0 + 2 >= b1) && i0 + 2 < N) lright = lin[base + i0 + 2];
-    double U[2];
-    if (sizeof(real) == 8) {
-      const double2 w = *reinterpret_cast<const double2*>(ur + i0);
+    real U[2];
+    {
+      const V2 w = *reinterpret_cast<const V2*>(ur + i0);
       U[0] = w.x;
       U[1] = w.y;
-    } else {
-      const float2 w = *reinterpret_cast<const float2*>(ur + i0);
-      U[0] = static_cast<double>(w.x);
-      U[1] = static_cast<double>(w.y);
     }
-    double out2[2];
+    real out2[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int64_t i = i0 + e;
-      const double lc = (i >= 1 && i <= N - 2) ? L[e] : 0.0;
-      const double ll = (i - 1 >= 1 && i - 1 <= N - 2) ? (e == 0 ? lleft : L[0]) : 0.0;
-      const double lr = (i + 1 >= 1 && i + 1 <= N - 2) ? (e == 1 ? lright : L[1]) : 0.0;
-      const double t = __fma_rn(one, __fma_rn(-2.0, lc, lr), ll);
-      contrib = __fma_rn(U[e], t, contrib);
+      const real lc = (i >= 1 && i <= N - 2) ? L[e] : zero;
+      const real ll = (i - 1 >= 1 && i - 1 <= N - 2) ? (e == 0 ? lleft : L[0]) : zero;
+      const real lr = (i + 1 >= 1 && i + 1 <= N - 2) ? (e == 1 ? lright : L[1]) : zero;
+      const real t = adj_lap(one, lc, ll, lr);
+      acc = adj_prod(U[e], t, acc);
       if (i == 0 || i == N - 1) {
-        out2[e] = 0.0;
+        out2[e] = zero;
         continue;
       }
-      double tl = t;      // t without the neighbour terms that arrive delayed
+      real tl = t;        // t without the neighbour terms that arrive delayed
       double pending = 0.0;
       if (g.trace) {
         sg.advance(i, N, g.S);
@@ -476,7 +502,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
             const int dL = delay_at(g, rod, k, s - 1, 1);   // this point's own left read
             if (dL > 0) {
               const double uLd = static_cast<double>(eh_row(eh, g, k - dL - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1]);
-              contrib += lc * (uLd - static_cast<double>(ur[i - 1]));
+              adj_term(acc, contrib, static_cast<double>(lc) * (uLd - static_cast<double>(ur[i - 1])));
               pend[((k - dL) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + (s - 1)) * 2 + 1] += r * lc;
             }
           }
@@ -488,18 +514,29 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
             const int dR = delay_at(g, rod, k, s, 0);       // this point's own right read
             if (dR > 0) {
               const double uRd = static_cast<double>(eh_row(eh, g, k - dR - t0)[(rod * (g.S - 1) + s) * 2 + 0]);
-              contrib += lc * (uRd - static_cast<double>(ur[i + 1]));
+              adj_term(acc, contrib, static_cast<double>(lc) * (uRd - static_cast<double>(ur[i + 1])));
               pend[((k - dR) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + s) * 2 + 0] += r * lc;
             }
           }
         }
       }
-      out2[e] = __fma_rn(one, __fma_rn(r, tl, lc), pending);
+      out2[e] = adj_new(one, r, tl, lc, pending);
     }
-    *reinterpret_cast<double2*>(lout + base + i0) = make_double2(out2[0], out2[1]);
+    V2 o;
+    o.x = out2[0];
+    o.y = out2[1];
+    *reinterpret_cast<V2*>(lout + base + i0) = o;
   }
-  const double bs = block_sum(contrib, red);
+  const double bs = block_sum(static_cast<double>(acc) + contrib, red);
   if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
+}
+
+// lambda(0) of an FP32 run into the caller's FP64 gradient array.
+template <typename real>
+__global__ void adj_widen(const real* __restrict__ lam, double* __restrict__ out, int64_t n) {
+  for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < n;
+       x += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[x] = static_cast<double>(lam[x]);
 }
 
 // Per rod: sums of the block partials, in block order.
@@ -565,7 +602,7 @@ int adjoint_t(const AdjointRun& a) {
   real* ck = static_cast<real*>(alloc(sizeof(real) * nc * npts));           // checkpoints u(kc)
   real* eh = static_cast<real*>(alloc(sizeof(real) * eh_rows * std::max<int64_t>(ehw, 1)));
   real* ckeh = static_cast<real*>(alloc(sizeof(real) * nc * q * std::max<int64_t>(ehw, 1)));
-  double* lam = static_cast<double*>(alloc(sizeof(double) * 2 * npts));
+  real* lam = static_cast<real*>(alloc(sizeof(real) * 2 * npts));
   double* pend = static_cast<double*>(alloc(sizeof(double) * g.Q * std::max<int64_t>(ehw, 1)));
   double* parts = static_cast<double*>(alloc(sizeof(double) * 3 * nblocks));
   double* outs = static_cast<double*>(alloc(sizeof(double) * 2 * nr));
@@ -631,8 +668,8 @@ int adjoint_t(const AdjointRun& a) {
     cleanup();
     return HEAT1D_ERR_CUDA;
   }
-  double* lin = lam;
-  double* lout = lam + npts;
+  real* lin = lam;
+  real* lout = lam + npts;
   adj_init<real><<<grid, block, 0, st>>>(g, X + C * npts, a.u_obs, lin, parts, a.cotangent);
 
   // ---- backward: recompute each interval, then march lambda back through it
@@ -659,7 +696,15 @@ int adjoint_t(const AdjointRun& a) {
     adj_finish<<<static_cast<unsigned>((nr + 127) / 128), 128, 0, st>>>(g, parts, parts + nblocks, outs, outs + nr);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(a.grad_u0, lin, sizeof(double) * npts, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) {
+    if (sizeof(real) == sizeof(double)) {
+      e = cudaMemcpyAsync(a.grad_u0, lin, sizeof(double) * npts, cudaMemcpyDeviceToDevice, st);
+    } else {
+      adj_widen<real><<<static_cast<unsigned>(std::min<int64_t>((npts + 255) / 256, 65535)), 256, 0, st>>>(
+          lin, a.grad_u0, npts);
+      e = cudaGetLastError();
+    }
+  }
   std::vector<double> host(2 * nr);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), outs, sizeof(double) * 2 * nr, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
