@@ -623,8 +623,9 @@ def run_inverse(args):
     updates = nr * (N - 2) * K
     ups = world * updates / dt_s
     # FP64: FP64-pipe instructions per forward update over the three passes:
-    # 3 (forward) + 3 (recompute) + 5 (backward: t, the r-gradient term and
-    # the lambda update, 2 + 1 + 2); the peak in forward-equivalent updates/s.
+    # 3 (forward) + 3 (recompute) + 4 (backward: t, the r-gradient term and
+    # the lambda update, 2 + 1 + 1, where nothing is pending); the peak in
+    # forward-equivalent updates/s.
     # FP32: u and lambda in FP32, every pass one launch per step over all rods
     # streaming its arrays: forward and recompute read u(k) and write u(k+1)
     # (8 bytes per point and step each), the backward reads u(k) and
@@ -632,9 +633,9 @@ def run_inverse(args):
     # at the measured HBM rate.
     fp64_rate = FP64_NOMINAL_TFLOPS * 1e12 / 2
     if dt == "f64":
-        bound, alu = "alu", fp64_rate / (3 + 3 + 5)
+        bound, alu = "alu", fp64_rate / (3 + 3 + 4)
         roof_note = ("three passes per forward update: forward and recompute 3 FP64 instructions per point, "
-                     "backward 5; peak = nominal FP64 instruction rate / 11")
+                     "backward 4; peak = nominal FP64 instruction rate / 10")
     else:
         hbm = float(measured_peaks()[0].get("hbm_gbs", 6800.0)) * 1e9
         bound, alu = "hbm", hbm / 28.0

@@ -188,15 +188,20 @@ struct Vec16T<double> {
 // points per pass and takes its two outer neighbours from the adjacent lanes
 // (lane 0, lane 31 and a lane whose right neighbour is past the block load
 // theirs).  Same arithmetic, delayed reads and history writes as adj_fwd_step.
-// Requires N to be a multiple of VN, so that every rod row and every block
-// starts on a 16-byte boundary and no vector straddles the end of a block.
-template <typename real>
+// The next pass's vector is loaded before the current one is computed; a
+// vector whose points are all interior (and, in a replay, none a segment's
+// first or last) takes the plain stencil.  Requires N to be a multiple of VN,
+// so that every rod row and every block starts on a 16-byte boundary and no
+// vector straddles the end of a block.
+template <typename real, bool kTrace>
 __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64_t k, const real* __restrict__ u,
                                                                 real* __restrict__ out, real* eh, int64_t t0) {
   using V = typename Vec16T<real>::type;
   constexpr int VN = Vec16T<real>::n;
-  const int64_t rod = blockIdx.x / g.bpr;
-  const int64_t b0 = (blockIdx.x % g.bpr) * g.span;
+  const unsigned bpr = static_cast<unsigned>(g.bpr);
+  const unsigned rod32 = blockIdx.x / bpr;
+  const int64_t rod = rod32;
+  const int64_t b0 = static_cast<int64_t>(blockIdx.x - rod32 * bpr) * g.span;
   const int64_t b1 = min(b0 + g.span, g.N);
   const int64_t N = g.N;
   const real* ur = u + rod * N;
@@ -206,61 +211,71 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
   const real c1 = static_cast<real>(g.c1[rod]), cN = static_cast<real>(g.cN[rod]);
   const int lane = threadIdx.x & 31;
   const int passes = static_cast<int>(g.span / (static_cast<int64_t>(kAdjThreads) * VN));
+  constexpr int64_t stride = static_cast<int64_t>(kAdjThreads) * VN;
   SegTrack sg{};
-  if (g.trace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), N, g.S);
-  for (int pass = 0; pass < passes; ++pass) {  // warp-uniform trip count (the shuffles need every lane)
-    const int64_t i0 = b0 + (static_cast<int64_t>(pass) * kAdjThreads + threadIdx.x) * VN;
+  if (kTrace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), N, g.S);
+  int64_t i0 = b0 + static_cast<int64_t>(threadIdx.x) * VN;
+  V wn{};
+  if (i0 < b1) wn = *reinterpret_cast<const V*>(ur + i0);
+  for (int pass = 0; pass < passes; ++pass, i0 += stride) {  // warp-uniform trip count (shuffles)
     const bool active = i0 < b1;
     real x[VN];
-    if (active) {
-      const V w = *reinterpret_cast<const V*>(ur + i0);
-      const real* ws = reinterpret_cast<const real*>(&w);
+    {
+      const real* ws = reinterpret_cast<const real*>(&wn);
 #pragma unroll
       for (int e = 0; e < VN; ++e) x[e] = ws[e];
-    } else {
-#pragma unroll
-      for (int e = 0; e < VN; ++e) x[e] = static_cast<real>(0);
     }
+    if (pass + 1 < passes && i0 + stride < b1) wn = *reinterpret_cast<const V*>(ur + i0 + stride);
     real left = __shfl_up_sync(0xffffffffu, x[VN - 1], 1);
     real right = __shfl_down_sync(0xffffffffu, x[0], 1);
     if (!active) continue;
     if (lane == 0) left = i0 > 0 ? ur[i0 - 1] : static_cast<real>(0);
     if ((lane == 31 || i0 + VN >= b1) && i0 + VN < N) right = ur[i0 + VN];
     real y[VN];
+    bool plain = i0 >= 1 && i0 + VN <= N - 1;
+    if (kTrace && plain) {
+      sg.advance(i0, N, g.S);
+      plain = i0 > sg.lo && i0 + VN < sg.hi;
+    }
+    if (plain) {
 #pragma unroll
-    for (int e = 0; e < VN; ++e) {
-      const int64_t i = i0 + e;
-      bool first = false, last = false;
-      int s = 0;
-      if (g.trace) {
-        sg.advance(i, N, g.S);
-        s = sg.s;
-        first = s > 0 && i == sg.lo;
-        last = s + 1 < g.S && i == sg.hi - 1;
-      }
-      real v;
-      if (i == 0) {
-        v = c1;
-      } else if (i == N - 1) {
-        v = cN;
-      } else {
-        real uL = e > 0 ? x[e - 1] : left;
-        real uR = e + 1 < VN ? x[e + 1] : right;
-        if (first) {
-          const int d = delay_at(g, rod, k, s - 1, 1);
-          if (d > 0) uL = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1];
+      for (int e = 0; e < VN; ++e) y[e] = ftcs(r, one, e > 0 ? x[e - 1] : left, x[e], e + 1 < VN ? x[e + 1] : right);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VN; ++e) {
+        const int64_t i = i0 + e;
+        bool first = false, last = false;
+        int s = 0;
+        if (kTrace) {
+          sg.advance(i, N, g.S);
+          s = sg.s;
+          first = s > 0 && i == sg.lo;
+          last = s + 1 < g.S && i == sg.hi - 1;
         }
-        if (last) {
-          const int d = delay_at(g, rod, k, s, 0);
-          if (d > 0) uR = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + s) * 2 + 0];
+        real v;
+        if (i == 0) {
+          v = c1;
+        } else if (i == N - 1) {
+          v = cN;
+        } else {
+          real uL = e > 0 ? x[e - 1] : left;
+          real uR = e + 1 < VN ? x[e + 1] : right;
+          if (first) {
+            const int d = delay_at(g, rod, k, s - 1, 1);
+            if (d > 0) uL = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1];
+          }
+          if (last) {
+            const int d = delay_at(g, rod, k, s, 0);
+            if (d > 0) uR = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + s) * 2 + 0];
+          }
+          v = ftcs(r, one, uL, x[e], uR);
         }
-        v = ftcs(r, one, uL, x[e], uR);
-      }
-      y[e] = v;
-      if (first || last) {  // boundary points of time k+1 into the history
-        real* row = eh_row(eh, g, k + 1 - t0);
-        if (first) row[(rod * (g.S - 1) + (s - 1)) * 2 + 0] = v;
-        if (last) row[(rod * (g.S - 1) + s) * 2 + 1] = v;
+        y[e] = v;
+        if (first || last) {  // boundary points of time k+1 into the history
+          real* row = eh_row(eh, g, k + 1 - t0);
+          if (first) row[(rod * (g.S - 1) + (s - 1)) * 2 + 0] = v;
+          if (last) row[(rod * (g.S - 1) + s) * 2 + 1] = v;
+        }
       }
     }
     V w;
@@ -307,9 +322,12 @@ __device__ __forceinline__ float adj_lap(float, float lc, float ll, float lr) {
 __device__ __forceinline__ double adj_new(double one, double r, double tl, double lc, double pending) {
   return __fma_rn(one, __fma_rn(r, tl, lc), pending);
 }
-__device__ __forceinline__ float adj_new(float, float r, float tl, float lc, double pending) {
-  return __fadd_rn(__fmaf_rn(r, tl, lc), static_cast<float>(pending));
+__device__ __forceinline__ float adj_new(float, float r, float tl, float lc, float pending) {
+  return __fadd_rn(__fmaf_rn(r, tl, lc), pending);
 }
+// The update of a point with nothing pending (no delayed read involved).
+__device__ __forceinline__ double adj_new0(double r, double t, double lc) { return __fma_rn(r, t, lc); }
+__device__ __forceinline__ float adj_new0(float r, float t, float lc) { return __fmaf_rn(r, t, lc); }
 // dL/dr products u_i t_i of a thread: FP64 runs sum them in FP64; FP32 runs
 // sum a thread's products (its points of one block) in FP32 and add that sum
 // to the FP64 partials, so that the FP64 pipe is not the bound of an FP32 run.
@@ -381,7 +399,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
     } else {
       const real r = static_cast<real>(g.r[rod]);
       real tl = t;        // t without the neighbour terms that arrive delayed
-      double pending = 0.0;
+      real pending = 0;
       if (g.trace) {
         sg.advance(i, N, g.S);
         const int s = sg.s;
@@ -391,7 +409,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
           double* prow = pend + (k % g.Q) * g.nrods * (g.S - 1) * 2;
           if (first) {
             double* p = prow + (rod * (g.S - 1) + (s - 1)) * 2 + 0;  // parked from i-1's delayed right reads
-            pending += *p;
+            pending += static_cast<real>(*p);
             *p = 0.0;
             if (delay_at(g, rod, k, s - 1, 0) > 0) tl -= ll;  // i-1 read u_i late: its term is parked
             const int dL = delay_at(g, rod, k, s - 1, 1);   // this point's own left read
@@ -403,7 +421,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
           }
           if (last) {
             double* p = prow + (rod * (g.S - 1) + s) * 2 + 1;  // parked from i+1's delayed left reads
-            pending += *p;
+            pending += static_cast<real>(*p);
             *p = 0.0;
             if (delay_at(g, rod, k, s, 1) > 0) tl -= lr;    // i+1 read u_i late
             const int dR = delay_at(g, rod, k, s, 0);       // this point's own right read
@@ -422,22 +440,29 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
   if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
 }
 
-// The same backward step, two points per thread and pass: lambda moves as
-// 16-byte double2 vectors and u as 2-element vectors, the outer lambda
-// neighbours come from the adjacent lanes (lane 0, lane 31 and a lane whose
-// right neighbour is past the block load theirs).  Per point the arithmetic,
-// the delayed-read corrections and the pending ring are those of
-// adj_bwd_step; the r-gradient partial of a block is summed in a fixed order
-// (each thread's points in order, then block_sum), so it does not depend on
-// the checkpoint interval.  Requires N even.
-template <typename real>
+// The same backward step, VN points per thread and pass: lambda and u move as
+// 16-byte vectors, the next pass's vectors are loaded before the current ones
+// are used, and the outer lambda neighbours come from the adjacent lanes (lane
+// 0, lane 31 and a lane whose right neighbour is past the block load theirs).
+// A vector whose points and neighbours are all interior (and, in a replay,
+// none of whose points is a segment's first or last) takes the plain
+// transposed stencil with nothing pending; the others follow adj_bwd_step
+// point by point (delayed-read corrections, pending ring).  The r-gradient
+// partial of a block is summed in a fixed order (each thread's points in
+// order, then block_sum), so it does not depend on the checkpoint interval.
+// Requires N to be a multiple of VN.
+template <typename real, bool kTrace>
 __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, int64_t k, const real* __restrict__ lin,
                                                                 real* __restrict__ lout, const real* __restrict__ u,
                                                                 const real* eh, int64_t t0, double* pend,
                                                                 double* gr_sum, double* gr_comp) {
+  using V = typename Vec16T<real>::type;
+  constexpr int VN = Vec16T<real>::n;
   __shared__ double red[kAdjThreads / 32];
-  const int64_t rod = blockIdx.x / g.bpr;
-  const int64_t b0 = (blockIdx.x % g.bpr) * g.span;
+  const unsigned bpr = static_cast<unsigned>(g.bpr);
+  const unsigned rod32 = blockIdx.x / bpr;
+  const int64_t rod = rod32;
+  const int64_t b0 = static_cast<int64_t>(blockIdx.x - rod32 * bpr) * g.span;
   const int64_t b1 = min(b0 + g.span, g.N);
   const int64_t N = g.N;
   const int64_t base = rod * N;
@@ -446,86 +471,110 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
   const real one = static_cast<real>(g.N > 0);
   const real zero = 0;
   const int lane = threadIdx.x & 31;
-  const int passes = static_cast<int>(g.span / (static_cast<int64_t>(kAdjThreads) * 2));
-  using V2 = typename std::conditional<sizeof(real) == 8, double2, float2>::type;
+  const int passes = static_cast<int>(g.span / (static_cast<int64_t>(kAdjThreads) * VN));
+  constexpr int64_t stride = static_cast<int64_t>(kAdjThreads) * VN;
   real acc = 0;          // products u_i t_i (and, in FP64, the delayed-read terms)
   double contrib = 0.0;  // FP32: the delayed-read terms
   SegTrack sg{};
-  if (g.trace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * 2, N - 1), N, g.S);
-  for (int pass = 0; pass < passes; ++pass) {  // warp-uniform trip count (the shuffles need every lane)
-    const int64_t i0 = b0 + (static_cast<int64_t>(pass) * kAdjThreads + threadIdx.x) * 2;
+  if (kTrace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), N, g.S);
+  int64_t i0 = b0 + static_cast<int64_t>(threadIdx.x) * VN;
+  V ln{}, un{};
+  if (i0 < b1) {
+    ln = *reinterpret_cast<const V*>(lin + base + i0);
+    un = *reinterpret_cast<const V*>(ur + i0);
+  }
+  for (int pass = 0; pass < passes; ++pass, i0 += stride) {  // warp-uniform trip count (shuffles)
     const bool active = i0 < b1;
-    real L[2] = {zero, zero};
-    if (active) {
-      const V2 w = *reinterpret_cast<const V2*>(lin + base + i0);
-      L[0] = w.x;
-      L[1] = w.y;
+    real L[VN], U[VN];
+    {
+      const real* lv = reinterpret_cast<const real*>(&ln);
+      const real* uv = reinterpret_cast<const real*>(&un);
+#pragma unroll
+      for (int e = 0; e < VN; ++e) {
+        L[e] = lv[e];
+        U[e] = uv[e];
+      }
     }
-    real lleft = __shfl_up_sync(0xffffffffu, L[1], 1);
+    if (pass + 1 < passes && i0 + stride < b1) {
+      ln = *reinterpret_cast<const V*>(lin + base + i0 + stride);
+      un = *reinterpret_cast<const V*>(ur + i0 + stride);
+    }
+    real lleft = __shfl_up_sync(0xffffffffu, L[VN - 1], 1);
     real lright = __shfl_down_sync(0xffffffffu, L[0], 1);
     if (!active) continue;
     if (lane == 0) lleft = i0 > 0 ? lin[base + i0 - 1] : zero;
-    if ((lane == 31 || i0 + 2 >= b1) && i0 + 2 < N) lright = lin[base + i0 + 2];
-    real U[2];
-    {
-      const V2 w = *reinterpret_cast<const V2*>(ur + i0);
-      U[0] = w.x;
-      U[1] = w.y;
+    if ((lane == 31 || i0 + VN >= b1) && i0 + VN < N) lright = lin[base + i0 + VN];
+    real out[VN];
+    bool plain = i0 >= 2 && i0 + VN <= N - 2;  // the points and their neighbours interior
+    if (kTrace && plain) {
+      sg.advance(i0, N, g.S);
+      plain = i0 > sg.lo && i0 + VN < sg.hi;
     }
-    real out2[2];
+    if (plain) {
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int64_t i = i0 + e;
-      const real lc = (i >= 1 && i <= N - 2) ? L[e] : zero;
-      const real ll = (i - 1 >= 1 && i - 1 <= N - 2) ? (e == 0 ? lleft : L[0]) : zero;
-      const real lr = (i + 1 >= 1 && i + 1 <= N - 2) ? (e == 1 ? lright : L[1]) : zero;
-      const real t = adj_lap(one, lc, ll, lr);
-      acc = adj_prod(U[e], t, acc);
-      if (i == 0 || i == N - 1) {
-        out2[e] = zero;
-        continue;
+      for (int e = 0; e < VN; ++e) {
+        const real t = adj_lap(one, L[e], e > 0 ? L[e - 1] : lleft, e + 1 < VN ? L[e + 1] : lright);
+        acc = adj_prod(U[e], t, acc);
+        out[e] = adj_new0(r, t, L[e]);
       }
-      real tl = t;        // t without the neighbour terms that arrive delayed
-      double pending = 0.0;
-      if (g.trace) {
-        sg.advance(i, N, g.S);
-        const int s = sg.s;
-        const bool first = s > 0 && i == sg.lo;
-        const bool last = s + 1 < g.S && i == sg.hi - 1;
-        if (first || last) {
-          double* prow = pend + (k % g.Q) * g.nrods * (g.S - 1) * 2;
-          if (first) {
-            double* p = prow + (rod * (g.S - 1) + (s - 1)) * 2 + 0;  // parked from i-1's delayed right reads
-            pending += *p;
-            *p = 0.0;
-            if (delay_at(g, rod, k, s - 1, 0) > 0) tl -= ll;  // i-1 read u_i late: its term is parked
-            const int dL = delay_at(g, rod, k, s - 1, 1);   // this point's own left read
-            if (dL > 0) {
-              const double uLd = static_cast<double>(eh_row(eh, g, k - dL - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1]);
-              adj_term(acc, contrib, static_cast<double>(lc) * (uLd - static_cast<double>(ur[i - 1])));
-              pend[((k - dL) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + (s - 1)) * 2 + 1] += r * lc;
+    } else {
+#pragma unroll
+      for (int e = 0; e < VN; ++e) {
+        const int64_t i = i0 + e;
+        const real lc = (i >= 1 && i <= N - 2) ? L[e] : zero;
+        const real ll = (i - 1 >= 1 && i - 1 <= N - 2) ? (e > 0 ? L[e - 1] : lleft) : zero;
+        const real lr = (i + 1 >= 1 && i + 1 <= N - 2) ? (e + 1 < VN ? L[e + 1] : lright) : zero;
+        const real t = adj_lap(one, lc, ll, lr);
+        acc = adj_prod(U[e], t, acc);
+        if (i == 0 || i == N - 1) {
+          out[e] = zero;
+          continue;
+        }
+        real tl = t;  // t without the neighbour terms that arrive delayed
+        real pending = 0;
+        bool parked = false;
+        if (kTrace) {
+          sg.advance(i, N, g.S);
+          const int s = sg.s;
+          const bool first = s > 0 && i == sg.lo;
+          const bool last = s + 1 < g.S && i == sg.hi - 1;
+          if (first || last) {
+            parked = true;
+            double* prow = pend + (k % g.Q) * g.nrods * (g.S - 1) * 2;
+            if (first) {
+              double* p = prow + (rod * (g.S - 1) + (s - 1)) * 2 + 0;  // parked from i-1's delayed right reads
+              pending += static_cast<real>(*p);
+              *p = 0.0;
+              if (delay_at(g, rod, k, s - 1, 0) > 0) tl -= ll;  // i-1 read u_i late: its term is parked
+              const int dL = delay_at(g, rod, k, s - 1, 1);   // this point's own left read
+              if (dL > 0) {
+                const double uLd = static_cast<double>(eh_row(eh, g, k - dL - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1]);
+                adj_term(acc, contrib, static_cast<double>(lc) * (uLd - static_cast<double>(ur[i - 1])));
+                pend[((k - dL) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + (s - 1)) * 2 + 1] += r * lc;
+              }
             }
-          }
-          if (last) {
-            double* p = prow + (rod * (g.S - 1) + s) * 2 + 1;  // parked from i+1's delayed left reads
-            pending += *p;
-            *p = 0.0;
-            if (delay_at(g, rod, k, s, 1) > 0) tl -= lr;    // i+1 read u_i late
-            const int dR = delay_at(g, rod, k, s, 0);       // this point's own right read
-            if (dR > 0) {
-              const double uRd = static_cast<double>(eh_row(eh, g, k - dR - t0)[(rod * (g.S - 1) + s) * 2 + 0]);
-              adj_term(acc, contrib, static_cast<double>(lc) * (uRd - static_cast<double>(ur[i + 1])));
-              pend[((k - dR) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + s) * 2 + 0] += r * lc;
+            if (last) {
+              double* p = prow + (rod * (g.S - 1) + s) * 2 + 1;  // parked from i+1's delayed left reads
+              pending += static_cast<real>(*p);
+              *p = 0.0;
+              if (delay_at(g, rod, k, s, 1) > 0) tl -= lr;    // i+1 read u_i late
+              const int dR = delay_at(g, rod, k, s, 0);       // this point's own right read
+              if (dR > 0) {
+                const double uRd = static_cast<double>(eh_row(eh, g, k - dR - t0)[(rod * (g.S - 1) + s) * 2 + 0]);
+                adj_term(acc, contrib, static_cast<double>(lc) * (uRd - static_cast<double>(ur[i + 1])));
+                pend[((k - dR) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + s) * 2 + 0] += r * lc;
+              }
             }
           }
         }
+        out[e] = parked ? adj_new(one, r, tl, lc, pending) : adj_new0(r, tl, lc);
       }
-      out2[e] = adj_new(one, r, tl, lc, pending);
     }
-    V2 o;
-    o.x = out2[0];
-    o.y = out2[1];
-    *reinterpret_cast<V2*>(lout + base + i0) = o;
+    V o;
+    real* ov = reinterpret_cast<real*>(&o);
+#pragma unroll
+    for (int e = 0; e < VN; ++e) ov[e] = out[e];
+    *reinterpret_cast<V*>(lout + base + i0) = o;
   }
   const double bs = block_sum(static_cast<double>(acc) + contrib, red);
   if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
@@ -557,10 +606,24 @@ __global__ void adj_finish(AdjGeom g, const double* loss_part, const double* gr_
 template <typename real>
 void fwd_step(bool vec, dim3 grid, dim3 block, cudaStream_t st, const AdjGeom& g, int64_t k, const real* in,
               real* out, real* eh, int64_t t0) {
-  if (vec)
-    adj_fwd_step_vec<real><<<grid, block, 0, st>>>(g, k, in, out, eh, t0);
+  if (vec && g.trace)
+    adj_fwd_step_vec<real, true><<<grid, block, 0, st>>>(g, k, in, out, eh, t0);
+  else if (vec)
+    adj_fwd_step_vec<real, false><<<grid, block, 0, st>>>(g, k, in, out, eh, t0);
   else
     adj_fwd_step<real><<<grid, block, 0, st>>>(g, k, in, out, eh, t0);
+}
+
+// One backward step over all rods.
+template <typename real>
+void bwd_step(bool vec, dim3 grid, dim3 block, cudaStream_t st, const AdjGeom& g, int64_t k, const real* lin,
+              real* lout, const real* x, const real* eh, int64_t t0, double* pend, double* gr_sum, double* gr_comp) {
+  if (vec && g.trace)
+    adj_bwd_step_vec<real, true><<<grid, block, 0, st>>>(g, k, lin, lout, x, eh, t0, pend, gr_sum, gr_comp);
+  else if (vec)
+    adj_bwd_step_vec<real, false><<<grid, block, 0, st>>>(g, k, lin, lout, x, eh, t0, pend, gr_sum, gr_comp);
+  else
+    adj_bwd_step<real><<<grid, block, 0, st>>>(g, k, lin, lout, x, eh, t0, pend, gr_sum, gr_comp);
 }
 
 template <typename real>
@@ -632,7 +695,7 @@ int adjoint_t(const AdjointRun& a) {
   // blocks' span, kAdjThreads * kAdjPointsPerThread, is a multiple of the
   // vector width times kAdjThreads)
   const bool vec = N % Vec16T<real>::n == 0 && g.span % (static_cast<int64_t>(kAdjThreads) * Vec16T<real>::n) == 0;
-  const bool bvec = N % 2 == 0 && g.span % (static_cast<int64_t>(kAdjThreads) * 2) == 0;  // backward: pairs
+  const bool bvec = vec;
   const int gather_blocks = static_cast<int>(std::min<int64_t>(1024, (std::max<int64_t>(ehw / 2, 1) + 255) / 256));
   adj_force_ends<real><<<static_cast<unsigned>((nr + 127) / 128), 128, 0, st>>>(g, X);  // u(0) with its ends set
   // history rows for times <= 0 all hold u(0) (reads before 0 are clamped, so
@@ -682,12 +745,8 @@ int adjoint_t(const AdjointRun& a) {
     for (int64_t j = 0; j + 1 < Cc && e == cudaSuccess; ++j)  // states kc .. kc+Cc-1
       fwd_step<real>(vec, grid, block, st, g, kc + j, X + j * npts, X + (j + 1) * npts, eh, t0);
     for (int64_t k = kc + Cc - 1; k >= kc; --k) {
-      if (bvec)
-        adj_bwd_step_vec<real><<<grid, block, 0, st>>>(g, k, lin, lout, X + (k - kc) * npts, eh, t0, pend,
-                                                       parts + nblocks, parts + 2 * nblocks);
-      else
-        adj_bwd_step<real><<<grid, block, 0, st>>>(g, k, lin, lout, X + (k - kc) * npts, eh, t0, pend,
-                                                   parts + nblocks, parts + 2 * nblocks);
+      bwd_step<real>(bvec, grid, block, st, g, k, lin, lout, X + (k - kc) * npts, eh, t0, pend, parts + nblocks,
+                     parts + 2 * nblocks);
       std::swap(lin, lout);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
