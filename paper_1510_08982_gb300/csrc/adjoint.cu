@@ -42,7 +42,10 @@ using namespace heat1d_dev;
 namespace {
 
 constexpr int kAdjThreads = 256;
-constexpr int kAdjPointsPerThread = 16;  // a block walks kAdjThreads * 16 points of one rod
+// A block walks kAdjThreads * this many points of one rod: 16 in FP64, 32 in
+// FP32 (measured: FP32 runs gain from the longer walk, FP64 runs lose).
+template <typename real>
+constexpr int adj_points_per_thread() { return sizeof(real) == 4 ? 32 : 16; }
 
 struct AdjGeom {
   int64_t nrods, N;
@@ -53,8 +56,27 @@ struct AdjGeom {
   const double* r;
   const double* c1;
   const double* cN;
+  const float* rf;   // the same coefficients rounded to FP32 (read by FP32 runs: no conversions on the FP64 pipe)
+  const float* c1f;
+  const float* cNf;
   const uint8_t* trace;  // [rod][K][S-1][2] or null (synchronous)
   int64_t K;
+};
+
+// Rod coefficients in the run's precision.
+template <typename real>
+struct Coefs;
+template <>
+struct Coefs<double> {
+  __device__ static double r(const AdjGeom& g, int64_t rod) { return g.r[rod]; }
+  __device__ static double c1(const AdjGeom& g, int64_t rod) { return g.c1[rod]; }
+  __device__ static double cN(const AdjGeom& g, int64_t rod) { return g.cN[rod]; }
+};
+template <>
+struct Coefs<float> {
+  __device__ static float r(const AdjGeom& g, int64_t rod) { return g.rf[rod]; }
+  __device__ static float c1(const AdjGeom& g, int64_t rod) { return g.c1f[rod]; }
+  __device__ static float cN(const AdjGeom& g, int64_t rod) { return g.cNf[rod]; }
 };
 
 __device__ __forceinline__ int seg_of(int64_t i, int64_t N, int S) {
@@ -105,8 +127,8 @@ template <typename real>
 __global__ void adj_force_ends(AdjGeom g, real* u) {
   const int64_t rod = blockIdx.x * blockDim.x + threadIdx.x;
   if (rod >= g.nrods) return;
-  u[rod * g.N] = static_cast<real>(g.c1[rod]);
-  u[rod * g.N + g.N - 1] = static_cast<real>(g.cN[rod]);
+  u[rod * g.N] = Coefs<real>::c1(g, rod);
+  u[rod * g.N + g.N - 1] = Coefs<real>::cN(g, rod);
 }
 
 // Writes the boundary points of state row `u` (all rods) into history row.
@@ -132,7 +154,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step(AdjGeom g, int64_t k
   const int64_t b1 = min(b0 + g.span, g.N);
   const real* ur = u + rod * g.N;
   real* orow = out + rod * g.N;
-  const real r = static_cast<real>(g.r[rod]);
+  const real r = Coefs<real>::r(g, rod);
   const real one = static_cast<real>(g.N > 0);
   SegTrack sg{};
   if (g.trace) sg.init(b0 + threadIdx.x, g.N, g.S);
@@ -147,9 +169,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step(AdjGeom g, int64_t k
     }
     real v;
     if (i == 0) {
-      v = static_cast<real>(g.c1[rod]);
+      v = Coefs<real>::c1(g, rod);
     } else if (i == g.N - 1) {
-      v = static_cast<real>(g.cN[rod]);
+      v = Coefs<real>::cN(g, rod);
     } else {
       real uL = ur[i - 1], uR = ur[i + 1];
       if (first) {
@@ -206,9 +228,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
   const int64_t N = g.N;
   const real* ur = u + rod * N;
   real* orow = out + rod * N;
-  const real r = static_cast<real>(g.r[rod]);
+  const real r = Coefs<real>::r(g, rod);
   const real one = static_cast<real>(g.N > 0);
-  const real c1 = static_cast<real>(g.c1[rod]), cN = static_cast<real>(g.cN[rod]);
+  const real c1 = Coefs<real>::c1(g, rod), cN = Coefs<real>::cN(g, rod);
   const int lane = threadIdx.x & 31;
   const int passes = static_cast<int>(g.span / (static_cast<int64_t>(kAdjThreads) * VN));
   constexpr int64_t stride = static_cast<int64_t>(kAdjThreads) * VN;
@@ -293,6 +315,33 @@ __device__ double block_sum(double x, double* red) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFullMask, x, o);
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) red[w] = x;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int j = 0; j < kAdjThreads / 32; ++j) s += red[j];
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+// The r-gradient partial of a block: a thread's product sum `acc` plus its
+// FP64 delayed-read terms.  FP64 runs sum both in FP64.  FP32 runs sum the
+// products of a warp in FP32 and the warps' sums in FP64 (the shuffled
+// additions of a warp would otherwise be FP64-pipe work for every lane); the
+// delayed-read terms, present only in replays, stay FP64.
+template <bool kTrace>
+__device__ double block_sum_acc(double acc, double terms, double* red) {
+  return block_sum(acc + terms, red);
+}
+template <bool kTrace>
+__device__ double block_sum_acc(float acc, double terms, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFullMask, acc, o);
+  if (kTrace) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) terms += __shfl_down_sync(kFullMask, terms, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = static_cast<double>(acc) + terms;
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x == 0)
@@ -397,7 +446,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
     if (i == 0 || i == N - 1) {
       lout[base + i] = zero;
     } else {
-      const real r = static_cast<real>(g.r[rod]);
+      const real r = Coefs<real>::r(g, rod);
       real tl = t;        // t without the neighbour terms that arrive delayed
       real pending = 0;
       if (g.trace) {
@@ -467,7 +516,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
   const int64_t N = g.N;
   const int64_t base = rod * N;
   const real* ur = u + base;
-  const real r = static_cast<real>(g.r[rod]);
+  const real r = Coefs<real>::r(g, rod);
   const real one = static_cast<real>(g.N > 0);
   const real zero = 0;
   const int lane = threadIdx.x & 31;
@@ -576,7 +625,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
     for (int e = 0; e < VN; ++e) ov[e] = out[e];
     *reinterpret_cast<V*>(lout + base + i0) = o;
   }
-  const double bs = block_sum(static_cast<double>(acc) + contrib, red);
+  const double bs = block_sum_acc<kTrace>(acc, contrib, red);
   if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
 }
 
@@ -640,7 +689,7 @@ int adjoint_t(const AdjointRun& a) {
   g.S = S;
   g.q = q;
   g.Q = q + 1;
-  g.span = static_cast<int64_t>(kAdjThreads) * kAdjPointsPerThread;
+  g.span = static_cast<int64_t>(kAdjThreads) * adj_points_per_thread<real>();
   g.bpr = (N + g.span - 1) / g.span;
   g.trace = a.trace;
   g.K = K;
@@ -661,6 +710,7 @@ int adjoint_t(const AdjointRun& a) {
     for (void* p : owned) cudaFree(p);
   };
   double* d_coef = static_cast<double*>(alloc(sizeof(double) * 3 * nr));
+  float* d_coef32 = static_cast<float*>(alloc(sizeof(float) * 3 * nr));
   real* X = static_cast<real*>(alloc(sizeof(real) * (C + 1) * npts));       // interval workspace
   real* ck = static_cast<real*>(alloc(sizeof(real) * nc * npts));           // checkpoints u(kc)
   real* eh = static_cast<real*>(alloc(sizeof(real) * eh_rows * std::max<int64_t>(ehw, 1)));
@@ -669,7 +719,7 @@ int adjoint_t(const AdjointRun& a) {
   double* pend = static_cast<double*>(alloc(sizeof(double) * g.Q * std::max<int64_t>(ehw, 1)));
   double* parts = static_cast<double*>(alloc(sizeof(double) * 3 * nblocks));
   double* outs = static_cast<double*>(alloc(sizeof(double) * 2 * nr));
-  if (!d_coef || !X || !ck || !eh || !ckeh || !lam || !pend || !parts || !outs) {
+  if (!d_coef || !d_coef32 || !X || !ck || !eh || !ckeh || !lam || !pend || !parts || !outs) {
     cleanup();
     return HEAT1D_ERR_OOM;
   }
@@ -679,10 +729,16 @@ int adjoint_t(const AdjointRun& a) {
     coef[nr + j] = a.c1[j];
     coef[2 * nr + j] = a.cN[j];
   }
+  std::vector<float> coef32(coef.begin(), coef.end());
   g.r = d_coef;
   g.c1 = d_coef + nr;
   g.cN = d_coef + 2 * nr;
+  g.rf = d_coef32;
+  g.c1f = d_coef32 + nr;
+  g.cNf = d_coef32 + 2 * nr;
   cudaError_t e = cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * 3 * nr, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_coef32, coef32.data(), sizeof(float) * 3 * nr, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(pend, 0, sizeof(double) * g.Q * std::max<int64_t>(ehw, 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(parts, 0, sizeof(double) * 3 * nblocks, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(X, a.u0, sizeof(real) * npts, cudaMemcpyDeviceToDevice, st);
@@ -692,7 +748,7 @@ int adjoint_t(const AdjointRun& a) {
   }
   const dim3 grid(static_cast<unsigned>(nblocks)), block(kAdjThreads);
   // 16-byte vectors where every rod row starts on a 16-byte boundary (the
-  // blocks' span, kAdjThreads * kAdjPointsPerThread, is a multiple of the
+  // blocks' span, kAdjThreads * adj_points_per_thread, is a multiple of the
   // vector width times kAdjThreads)
   const bool vec = N % Vec16T<real>::n == 0 && g.span % (static_cast<int64_t>(kAdjThreads) * Vec16T<real>::n) == 0;
   const bool bvec = vec;
