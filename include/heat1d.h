@@ -266,8 +266,10 @@ int heat1d_run_batched(const heat1d_rod* rods, int64_t nrods, void* u_packed, in
  * The forward pass keeps a checkpoint every ckpt_every steps (0: 128): the
  * state plus the last q values of every point next to a segment boundary.
  * The backward pass recomputes each interval from its checkpoint and marches
- * lambda back through it.  lambda and every reduction are FP64 (the forward
- * states are in the handle's dtype); reductions are deterministic.  Scratch
+ * lambda back through it.  lambda has the handle's dtype; the loss and dL/dr
+ * are accumulated in FP64 (an FP32 run sums the products of a warp's points
+ * in FP32 first) and every reduction is deterministic, the same for any
+ * ckpt_every.  grad_u0 is always FP64.  Scratch
  * (checkpoints, one interval of states) is allocated per call and freed;
  * HEAT1D_ERR_OOM if it does not fit.  The call waits for the stream.
  */

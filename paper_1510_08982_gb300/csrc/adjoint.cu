@@ -378,8 +378,9 @@ __device__ __forceinline__ float adj_new(float, float r, float tl, float lc, flo
 __device__ __forceinline__ double adj_new0(double r, double t, double lc) { return __fma_rn(r, t, lc); }
 __device__ __forceinline__ float adj_new0(float r, float t, float lc) { return __fmaf_rn(r, t, lc); }
 // dL/dr products u_i t_i of a thread: FP64 runs sum them in FP64; FP32 runs
-// sum a thread's products (its points of one block) in FP32 and add that sum
-// to the FP64 partials, so that the FP64 pipe is not the bound of an FP32 run.
+// sum a thread's products (its points of one block) in FP32, then a warp's
+// thread sums in FP32 (block_sum_acc), and add the warp sums to the FP64
+// partials, so that the FP64 pipe is not the bound of an FP32 run.
 __device__ __forceinline__ double adj_prod(double u, double t, double acc) { return __fma_rn(u, t, acc); }
 __device__ __forceinline__ float adj_prod(float u, float t, float acc) { return __fmaf_rn(u, t, acc); }
 // A delayed-read term of dL/dr: into the FP64 sum (FP64 runs keep one sum, in

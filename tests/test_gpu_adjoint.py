@@ -134,8 +134,8 @@ def test_adjoint_central_differences_full_size_rod(H):
 
 @pytest.mark.parametrize("N,K,C", [(1024, 400, 50), (4096, 2000, 128)])
 def test_fp32_adjoint_close_to_fp64_oracle(H, N, K, C):
-    """An FP32 run steps u and lambda in FP32 (the dL/dr products of a thread
-    summed in FP32, the sums in FP64).  Each step rounds lambda once more, so
+    """An FP32 run steps u and lambda in FP32 (the dL/dr products of a warp's
+    points in one block summed in FP32, those sums in FP64).  Each step rounds lambda once more, so
     its error grows like sqrt(K) FP32 roundings: dL/du(0) is held to
     4 sqrt(K) 2^-24 of its largest entry, dL/dr to 1e-4 (relative), both
     against the FP64 oracle on the FP32-rounded inputs."""
