@@ -50,6 +50,7 @@ constexpr int adj_points_per_thread() { return sizeof(real) == 4 ? 32 : 16; }
 struct AdjGeom {
   int64_t nrods, N;
   int S;          // segments per rod
+  int64_t seg_base, seg_extra;  // N / S and N mod S
   int q, Q;       // delay window, pending ring length (q+1)
   int64_t bpr;    // blocks per rod
   int64_t span;   // points per block (a block never straddles two rods)
@@ -79,13 +80,21 @@ struct Coefs<float> {
   __device__ static float cN(const AdjGeom& g, int64_t rod) { return g.cNf[rod]; }
 };
 
-__device__ __forceinline__ int seg_of(int64_t i, int64_t N, int S) {
-  const int64_t base = N / S, extra = N % S, big = extra * (base + 1);
-  return static_cast<int>(i < big ? i / (base + 1) : extra + (i - big) / base);
+// Segment geometry of a rod (the first N mod S segments one point longer),
+// from seg_base = N / S and seg_extra = N mod S computed on the host: no
+// 64-bit division on the device (it costs hundreds of instructions), and a
+// 32-bit one where the operands fit.
+__device__ __forceinline__ int64_t udiv(int64_t a, int64_t b) {  // a >= 0, b > 0
+  return (a <= 0xffffffffLL && b <= 0xffffffffLL)
+             ? static_cast<int64_t>(static_cast<uint32_t>(a) / static_cast<uint32_t>(b))
+             : a / b;
 }
-__device__ __forceinline__ int64_t seg_start(int s, int64_t N, int S) {
-  const int64_t base = N / S, extra = N % S;
-  return s * base + (s < extra ? s : extra);
+__device__ __forceinline__ int seg_of(int64_t i, const AdjGeom& g) {
+  const int64_t big = g.seg_extra * (g.seg_base + 1);
+  return static_cast<int>(i < big ? udiv(i, g.seg_base + 1) : g.seg_extra + udiv(i - big, g.seg_base));
+}
+__device__ __forceinline__ int64_t seg_start(int s, const AdjGeom& g) {
+  return s * g.seg_base + (s < g.seg_extra ? s : g.seg_extra);
 }
 
 // The segment of a thread's points as they increase: one division for the
@@ -95,16 +104,16 @@ __device__ __forceinline__ int64_t seg_start(int s, int64_t N, int S) {
 struct SegTrack {
   int s;
   int64_t lo, hi;  // the current segment's points [lo, hi)
-  __device__ __forceinline__ void init(int64_t i, int64_t N, int S) {
-    s = seg_of(i, N, S);
-    lo = seg_start(s, N, S);
-    hi = seg_start(s + 1, N, S);
+  __device__ __forceinline__ void init(int64_t i, const AdjGeom& g) {
+    s = seg_of(i, g);
+    lo = seg_start(s, g);
+    hi = seg_start(s + 1, g);
   }
-  __device__ __forceinline__ void advance(int64_t i, int64_t N, int S) {
+  __device__ __forceinline__ void advance(int64_t i, const AdjGeom& g) {
     while (i >= hi) {
       ++s;
       lo = hi;
-      hi = seg_start(s + 1, N, S);
+      hi = seg_start(s + 1, g);
     }
   }
 };
@@ -138,7 +147,7 @@ __global__ void adj_edge_gather(AdjGeom g, const real* u, real* eh_dst) {
   for (int64_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
     const int64_t rod = x / (g.S - 1);
     const int b = static_cast<int>(x % (g.S - 1));
-    const int64_t first = seg_start(b + 1, g.N, g.S);
+    const int64_t first = seg_start(b + 1, g);
     eh_dst[x * 2 + 0] = u[rod * g.N + first];
     eh_dst[x * 2 + 1] = u[rod * g.N + first - 1];
   }
@@ -157,12 +166,12 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step(AdjGeom g, int64_t k
   const real r = Coefs<real>::r(g, rod);
   const real one = static_cast<real>(g.N > 0);
   SegTrack sg{};
-  if (g.trace) sg.init(b0 + threadIdx.x, g.N, g.S);
+  if (g.trace) sg.init(b0 + threadIdx.x, g);
   for (int64_t i = b0 + threadIdx.x; i < b1; i += kAdjThreads) {
     bool first = false, last = false;  // the segment's first / last point
     int s = 0;
     if (g.trace) {
-      sg.advance(i, g.N, g.S);
+      sg.advance(i, g);
       s = sg.s;
       first = s > 0 && i == sg.lo;
       last = s + 1 < g.S && i == sg.hi - 1;
@@ -235,7 +244,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
   const int passes = static_cast<int>(g.span / (static_cast<int64_t>(kAdjThreads) * VN));
   constexpr int64_t stride = static_cast<int64_t>(kAdjThreads) * VN;
   SegTrack sg{};
-  if (kTrace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), N, g.S);
+  if (kTrace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), g);
   int64_t i0 = b0 + static_cast<int64_t>(threadIdx.x) * VN;
   V wn{};
   if (i0 < b1) wn = *reinterpret_cast<const V*>(ur + i0);
@@ -256,7 +265,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
     real y[VN];
     bool plain = i0 >= 1 && i0 + VN <= N - 1;
     if (kTrace && plain) {
-      sg.advance(i0, N, g.S);
+      sg.advance(i0, g);
       plain = i0 > sg.lo && i0 + VN < sg.hi;
     }
     if (plain) {
@@ -269,7 +278,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
         bool first = false, last = false;
         int s = 0;
         if (kTrace) {
-          sg.advance(i, N, g.S);
+          sg.advance(i, g);
           s = sg.s;
           first = s > 0 && i == sg.lo;
           last = s + 1 < g.S && i == sg.hi - 1;
@@ -434,7 +443,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
   const real one = static_cast<real>(g.N > 0);
   const real zero = 0;
   SegTrack sg{};
-  if (g.trace) sg.init(b0 + threadIdx.x, g.N, g.S);
+  if (g.trace) sg.init(b0 + threadIdx.x, g);
   for (int64_t i = b0 + threadIdx.x; i < b1; i += kAdjThreads) {
     const int64_t base = rod * g.N;
     const int64_t N = g.N;
@@ -451,7 +460,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
       real tl = t;        // t without the neighbour terms that arrive delayed
       real pending = 0;
       if (g.trace) {
-        sg.advance(i, N, g.S);
+        sg.advance(i, g);
         const int s = sg.s;
         const bool first = s > 0 && i == sg.lo;
         const bool last = s + 1 < g.S && i == sg.hi - 1;
@@ -526,7 +535,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
   real acc = 0;          // products u_i t_i (and, in FP64, the delayed-read terms)
   double contrib = 0.0;  // FP32: the delayed-read terms
   SegTrack sg{};
-  if (kTrace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), N, g.S);
+  if (kTrace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), g);
   int64_t i0 = b0 + static_cast<int64_t>(threadIdx.x) * VN;
   V ln{}, un{};
   if (i0 < b1) {
@@ -557,7 +566,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
     real out[VN];
     bool plain = i0 >= 2 && i0 + VN <= N - 2;  // the points and their neighbours interior
     if (kTrace && plain) {
-      sg.advance(i0, N, g.S);
+      sg.advance(i0, g);
       plain = i0 > sg.lo && i0 + VN < sg.hi;
     }
     if (plain) {
@@ -584,7 +593,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
         real pending = 0;
         bool parked = false;
         if (kTrace) {
-          sg.advance(i, N, g.S);
+          sg.advance(i, g);
           const int s = sg.s;
           const bool first = s > 0 && i == sg.lo;
           const bool last = s + 1 < g.S && i == sg.hi - 1;
@@ -688,6 +697,8 @@ int adjoint_t(const AdjointRun& a) {
   g.nrods = nr;
   g.N = N;
   g.S = S;
+  g.seg_base = N / S;
+  g.seg_extra = N % S;
   g.q = q;
   g.Q = q + 1;
   g.span = static_cast<int64_t>(kAdjThreads) * adj_points_per_thread<real>();
