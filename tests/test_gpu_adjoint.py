@@ -197,6 +197,41 @@ def test_batched_adjoint_matches_oracle(H, async_run):
         assert abs(gr[j] - grref) <= 1e-11 * abs(grref)
 
 
+@pytest.mark.parametrize("async_run", [False, True])
+def test_batched_adjoint_fp32(H, async_run):
+    """The batched FP32 adjoint (rod lengths a multiple of 4, so the 16-byte
+    vector kernels run): u(K) bit for bit against the oracle's FP32 run, the
+    gradients within the FP32 tolerances against the FP64 oracle on the
+    FP32-rounded inputs."""
+    import torch
+    nrods, N, K, S, q = 3, 4096, 256, 8, 3
+    rng = np.random.default_rng(31)
+    u0 = rng.uniform(-1, 1, size=(nrods, N)).astype(np.float32)
+    uobs = rng.uniform(-1, 1, size=(nrods, N))
+    r = rng.uniform(0.1, 0.45, size=nrods)
+    c1 = rng.uniform(-1, 1, size=nrods)
+    cN = rng.uniform(-1, 1, size=nrods)
+    traces = np.stack([inputs.delay_trace(K, S, q, seed=50 + j) for j in range(nrods)]) if async_run else None
+    tr_t = torch.tensor(traces, device="cuda") if async_run else None
+    uK, g, gr, ls = H.adjoint_batched(torch.tensor(u0, device="cuda"), torch.tensor(uobs, device="cuda"), r, c1, cN,
+                                      K, trace=tr_t, segments=S if async_run else 0, q=q, ckpt_every=64)
+    g = g.cpu().numpy()
+    uK = uK.cpu().numpy()
+    for j in range(nrods):
+        r32, c132, cN32 = (float(np.float32(x)) for x in (r[j], c1[j], cN[j]))
+        u64 = u0[j].astype(np.float64)
+        if async_run:
+            uref = oracle.async_replay(u64, r32, c132, cN32, S, q, K, traces[j], dtype=np.float32)
+            L, gref, grref = oracle.adjoint(u64, r32, c132, cN32, K, uobs[j], S, q, traces[j])
+        else:
+            uref = oracle.sync(u64, r32, c132, cN32, K, dtype=np.float32)
+            L, gref, grref = oracle.adjoint(u64, r32, c132, cN32, K, uobs[j])
+        assert np.array_equal(uK[j], uref)
+        assert abs(ls[j] - L) <= 1e-5 * abs(L)
+        assert close(g[j], gref, 4 * np.sqrt(K) * 2.0 ** -24)
+        assert abs(gr[j] - grref) <= 1e-4 * abs(grref)
+
+
 def test_autograd_function(H):
     import torch
     from paper_1510_08982_gb300.autograd import heat1d_run
