@@ -215,6 +215,62 @@ struct Vec16T<double> {
   static constexpr int n = 2;
 };
 
+// The segment-boundary points of a block [b0, b1) of one rod: candidate j is
+// the first (even j) or last (odd j) point of segment s0 + j/2, where s0 is
+// the segment of b0.  Returns false when candidate j is not such a point of
+// this block; a one-point segment is handled once, as its first point.
+__device__ __forceinline__ bool boundary_point(const AdjGeom& g, int s0, int j, int64_t b0, int64_t b1, int64_t& i,
+                                               int& s, bool& first, bool& last) {
+  s = s0 + j / 2;
+  const int64_t lo = seg_start(s, g), hi = seg_start(s + 1, g);
+  i = (j & 1) ? hi - 1 : lo;
+  if ((j & 1) && i == lo) return false;
+  first = i == lo && s > 0;
+  last = i == hi - 1 && s + 1 < g.S;
+  return (first || last) && i >= b0 && i < b1;
+}
+__device__ __forceinline__ int boundary_candidates(const AdjGeom& g, int64_t b0, int64_t b1, int& s0) {
+  s0 = seg_of(b0, g);
+  return 2 * (seg_of(b1 - 1, g) - s0 + 1);
+}
+
+// Forward step of a replay at the block's segment-boundary points: the
+// delayed neighbour values from the edge history (the synchronous sweep
+// used the current ones), and the new values into the history row k+1.
+template <typename real>
+__device__ void fwd_fixup(const AdjGeom& g, int64_t k, const real* ur, real* orow, real* eh, int64_t t0, int64_t rod,
+                          int64_t b0, int64_t b1, real r, real one, real c1, real cN) {
+  int s0 = 0;
+  const int nc = boundary_candidates(g, b0, b1, s0);
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+    int64_t i;
+    int s;
+    bool first, last;
+    if (!boundary_point(g, s0, j, b0, b1, i, s, first, last)) continue;
+    real v;
+    if (i == 0) {
+      v = c1;
+    } else if (i == g.N - 1) {
+      v = cN;
+    } else {
+      real uL = ur[i - 1], uR = ur[i + 1];
+      if (first) {
+        const int d = delay_at(g, rod, k, s - 1, 1);
+        if (d > 0) uL = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1];
+      }
+      if (last) {
+        const int d = delay_at(g, rod, k, s, 0);
+        if (d > 0) uR = eh_row(eh, g, k - d - t0)[(rod * (g.S - 1) + s) * 2 + 0];
+      }
+      v = ftcs(r, one, uL, ur[i], uR);
+    }
+    orow[i] = v;
+    real* row = eh_row(eh, g, k + 1 - t0);  // boundary points of time k+1 into the history
+    if (first) row[(rod * (g.S - 1) + (s - 1)) * 2 + 0] = v;
+    if (last) row[(rod * (g.S - 1) + s) * 2 + 1] = v;
+  }
+}
+
 // The same forward step with 16-byte vectors: a thread updates VN consecutive
 // points per pass and takes its two outer neighbours from the adjacent lanes
 // (lane 0, lane 31 and a lane whose right neighbour is past the block load
@@ -229,6 +285,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
                                                                 real* __restrict__ out, real* eh, int64_t t0) {
   using V = typename Vec16T<real>::type;
   constexpr int VN = Vec16T<real>::n;
+  constexpr bool kInline = kTrace && sizeof(real) == 8;  // replay: delayed reads inside the sweep (FP64)
+  constexpr bool kFix = kTrace && sizeof(real) == 4;     // replay: synchronous sweep, then fwd_fixup (FP32)
   const unsigned bpr = static_cast<unsigned>(g.bpr);
   const unsigned rod32 = blockIdx.x / bpr;
   const int64_t rod = rod32;
@@ -244,7 +302,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
   const int passes = static_cast<int>(g.span / (static_cast<int64_t>(kAdjThreads) * VN));
   constexpr int64_t stride = static_cast<int64_t>(kAdjThreads) * VN;
   SegTrack sg{};
-  if (kTrace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), g);
+  if (kInline) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), g);
   int64_t i0 = b0 + static_cast<int64_t>(threadIdx.x) * VN;
   V wn{};
   if (i0 < b1) wn = *reinterpret_cast<const V*>(ur + i0);
@@ -264,7 +322,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
     if ((lane == 31 || i0 + VN >= b1) && i0 + VN < N) right = ur[i0 + VN];
     real y[VN];
     bool plain = i0 >= 1 && i0 + VN <= N - 1;
-    if (kTrace && plain) {
+    if (kInline && plain) {
       sg.advance(i0, g);
       plain = i0 > sg.lo && i0 + VN < sg.hi;
     }
@@ -277,7 +335,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
         const int64_t i = i0 + e;
         bool first = false, last = false;
         int s = 0;
-        if (kTrace) {
+        if (kInline) {
           sg.advance(i, g);
           s = sg.s;
           first = s > 0 && i == sg.lo;
@@ -314,6 +372,10 @@ __global__ void __launch_bounds__(kAdjThreads) adj_fwd_step_vec(AdjGeom g, int64
 #pragma unroll
     for (int e = 0; e < VN; ++e) ws[e] = y[e];
     *reinterpret_cast<V*>(orow + i0) = w;
+  }
+  if (kFix) {  // the block's segment-boundary points, redone with their delayed reads
+    __syncthreads();
+    fwd_fixup<real>(g, k, ur, orow, eh, t0, rod, b0, b1, r, one, c1, cN);
   }
 }
 
@@ -499,6 +561,58 @@ __global__ void __launch_bounds__(kAdjThreads) adj_bwd_step(AdjGeom g, int64_t k
   if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
 }
 
+// Backward step of a replay at the block's segment-boundary points, as in
+// adj_bwd_step: the neighbour terms whose reads were delayed leave t and come
+// back through the pending ring; this point's own delayed reads add their
+// dL/dr terms and park r * lambda_i for the earlier level they came from.
+template <typename real>
+__device__ void bwd_fixup(const AdjGeom& g, int64_t k, const real* lin, real* lout, const real* ur, const real* eh,
+                          int64_t t0, double* pend, int64_t rod, int64_t base, int64_t b0, int64_t b1, real r,
+                          real one, real& acc, double& contrib) {
+  const int64_t N = g.N;
+  const real zero = 0;
+  int s0 = 0;
+  const int nc = boundary_candidates(g, b0, b1, s0);
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+    int64_t i;
+    int s;
+    bool first, last;
+    if (!boundary_point(g, s0, j, b0, b1, i, s, first, last)) continue;
+    if (i == 0 || i == N - 1) continue;  // Dirichlet ends: lambda stays 0
+    const real lc = lin[base + i];
+    const real ll = i - 1 >= 1 ? lin[base + i - 1] : zero;
+    const real lr = i + 1 <= N - 2 ? lin[base + i + 1] : zero;
+    real tl = adj_lap(one, lc, ll, lr);  // t without the neighbour terms that arrive delayed
+    real pending = 0;
+    double* prow = pend + (k % g.Q) * g.nrods * (g.S - 1) * 2;
+    if (first) {
+      double* p = prow + (rod * (g.S - 1) + (s - 1)) * 2 + 0;  // parked from i-1's delayed right reads
+      pending += static_cast<real>(*p);
+      *p = 0.0;
+      if (delay_at(g, rod, k, s - 1, 0) > 0) tl -= ll;  // i-1 read u_i late: its term is parked
+      const int dL = delay_at(g, rod, k, s - 1, 1);   // this point's own left read
+      if (dL > 0) {
+        const double uLd = static_cast<double>(eh_row(eh, g, k - dL - t0)[(rod * (g.S - 1) + (s - 1)) * 2 + 1]);
+        adj_term(acc, contrib, static_cast<double>(lc) * (uLd - static_cast<double>(ur[i - 1])));
+        pend[((k - dL) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + (s - 1)) * 2 + 1] += r * lc;
+      }
+    }
+    if (last) {
+      double* p = prow + (rod * (g.S - 1) + s) * 2 + 1;  // parked from i+1's delayed left reads
+      pending += static_cast<real>(*p);
+      *p = 0.0;
+      if (delay_at(g, rod, k, s, 1) > 0) tl -= lr;    // i+1 read u_i late
+      const int dR = delay_at(g, rod, k, s, 0);       // this point's own right read
+      if (dR > 0) {
+        const double uRd = static_cast<double>(eh_row(eh, g, k - dR - t0)[(rod * (g.S - 1) + s) * 2 + 0]);
+        adj_term(acc, contrib, static_cast<double>(lc) * (uRd - static_cast<double>(ur[i + 1])));
+        pend[((k - dR) % g.Q) * g.nrods * (g.S - 1) * 2 + (rod * (g.S - 1) + s) * 2 + 0] += r * lc;
+      }
+    }
+    lout[base + i] = adj_new(one, r, tl, lc, pending);
+  }
+}
+
 // The same backward step, VN points per thread and pass: lambda and u move as
 // 16-byte vectors, the next pass's vectors are loaded before the current ones
 // are used, and the outer lambda neighbours come from the adjacent lanes (lane
@@ -517,6 +631,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
                                                                 double* gr_sum, double* gr_comp) {
   using V = typename Vec16T<real>::type;
   constexpr int VN = Vec16T<real>::n;
+  constexpr bool kInline = kTrace && sizeof(real) == 8;  // replay: delayed reads inside the sweep (FP64)
+  constexpr bool kFix = kTrace && sizeof(real) == 4;     // replay: synchronous sweep, then bwd_fixup (FP32)
   __shared__ double red[kAdjThreads / 32];
   const unsigned bpr = static_cast<unsigned>(g.bpr);
   const unsigned rod32 = blockIdx.x / bpr;
@@ -535,7 +651,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
   real acc = 0;          // products u_i t_i (and, in FP64, the delayed-read terms)
   double contrib = 0.0;  // FP32: the delayed-read terms
   SegTrack sg{};
-  if (kTrace) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), g);
+  if (kInline) sg.init(min(b0 + static_cast<int64_t>(threadIdx.x) * VN, N - 1), g);
   int64_t i0 = b0 + static_cast<int64_t>(threadIdx.x) * VN;
   V ln{}, un{};
   if (i0 < b1) {
@@ -565,7 +681,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
     if ((lane == 31 || i0 + VN >= b1) && i0 + VN < N) lright = lin[base + i0 + VN];
     real out[VN];
     bool plain = i0 >= 2 && i0 + VN <= N - 2;  // the points and their neighbours interior
-    if (kTrace && plain) {
+    if (kInline && plain) {
       sg.advance(i0, g);
       plain = i0 > sg.lo && i0 + VN < sg.hi;
     }
@@ -592,7 +708,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
         real tl = t;  // t without the neighbour terms that arrive delayed
         real pending = 0;
         bool parked = false;
-        if (kTrace) {
+        if (kInline) {
           sg.advance(i, g);
           const int s = sg.s;
           const bool first = s > 0 && i == sg.lo;
@@ -634,6 +750,10 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_bwd_step_vec(AdjGeom g, in
 #pragma unroll
     for (int e = 0; e < VN; ++e) ov[e] = out[e];
     *reinterpret_cast<V*>(lout + base + i0) = o;
+  }
+  if (kFix) {  // the block's segment-boundary points, redone with their delayed reads
+    __syncthreads();
+    bwd_fixup<real>(g, k, lin, lout, ur, eh, t0, pend, rod, base, b0, b1, r, one, acc, contrib);
   }
   const double bs = block_sum_acc<kTrace>(acc, contrib, red);
   if (threadIdx.x == 0) kahan_add(gr_sum + blockIdx.x, gr_comp + blockIdx.x, bs);
