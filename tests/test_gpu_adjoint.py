@@ -197,6 +197,33 @@ def test_batched_adjoint_matches_oracle(H, async_run):
         assert abs(gr[j] - grref) <= 1e-11 * abs(grref)
 
 
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("N,S", [(4096, 1024), (1024, 1024), (2052, 513)])
+def test_replay_adjoint_short_segments(H, dtype, N, S):
+    """Replays with segments of 4, 1 and about 4 points: every block holds far
+    more segment-boundary points than threads, and one-point segments are
+    both a first and a last point."""
+    rod, uobs = problem(N, 120, 17, r=0.4)
+    q = 3
+    tr = inputs.delay_trace(rod.K, S, q, seed=23)
+    loss, g, gr, uK = gpu_adjoint(H, rod, uobs, S=S, q=q, trace=tr, C=40, dtype=dtype)
+    if dtype == "float64":
+        L, gref, grref = oracle.adjoint(rod.u0, rod.r, rod.c1, rod.cN, rod.K, uobs, S, q, tr)
+        assert np.array_equal(uK, oracle.async_replay(rod.u0, rod.r, rod.c1, rod.cN, S, q, rod.K, tr))
+        assert abs(loss - L) <= 1e-13 * abs(L)
+        assert close(g, gref, 1e-12)
+        assert abs(gr - grref) <= 1e-11 * abs(grref)
+    else:
+        f = np.float32
+        r32, c132, cN32 = float(f(rod.r)), float(f(rod.c1)), float(f(rod.cN))
+        u64 = rod.u0.astype(f).astype(np.float64)
+        L, gref, grref = oracle.adjoint(u64, r32, c132, cN32, rod.K, uobs, S, q, tr)
+        assert np.array_equal(uK, oracle.async_replay(u64, r32, c132, cN32, S, q, rod.K, tr, dtype=f))
+        assert abs(loss - L) <= 1e-5 * abs(L)
+        assert close(g, gref, 4 * np.sqrt(rod.K) * 2.0 ** -24)
+        assert abs(gr - grref) <= 1e-4 * abs(grref)
+
+
 @pytest.mark.parametrize("async_run", [False, True])
 def test_batched_adjoint_fp32(H, async_run):
     """The batched FP32 adjoint (rod lengths a multiple of 4, so the 16-byte
