@@ -24,9 +24,11 @@
 // a workspace of C+1 states and then marches lambda back through it.
 //
 // Each step is one launch over all points of all rods (the backward march
-// needs every point of step k before any of step k-1).  Every reduction (loss,
-// dL/dr) is deterministic: fixed per-block partials with compensated sums,
-// added in a fixed order at the end.
+// needs every point of step k before any of step k-1).  lambda is stored and
+// stepped in the state's precision; the loss and dL/dr are summed in FP64
+// (an FP32 run adds a warp's products in FP32 first).  Every reduction is
+// deterministic: fixed per-block partials with compensated sums, added in a
+// fixed order at the end.
 #include <algorithm>
 #include <cmath>
 #include <string>
