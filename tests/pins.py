@@ -14,6 +14,10 @@ the mathematics fixes for the update of Section 2 (Eq. eqn:sync) and Section 3
   z(k) = [u(k); u(k-1); ...; u(k-q+1)] with one explicit block matrix per step
   built from the delays; times before 0 are served by z(0) = [u0; ...; u0].
 * brute_adjoint: gradients by the transposed products of those matrices.
+* fp32_sync_exact / fp32_async_exact: the FP32 operation order of Section 4's
+  kernels with every operation's exact rational result rounded once to the
+  nearest binary32 (round_to_float32, ties to even), so that the oracle's FP32
+  mode can be checked bit for bit rather than within a bound.
 """
 from __future__ import annotations
 
@@ -287,3 +291,74 @@ def brute_async_blocked_periodic_fraction(u0, r, S, q, T, K, trace):
             new[lo:hi] = z[lo:hi]
         W.append(new)
     return W[nb]
+
+
+# ----------------------------------------------------------------------------- FP32 operation order
+
+
+def round_to_float32(q):
+    """The binary32 value nearest to the rational q, ties to even (IEEE 754
+    round to nearest), returned as a Python float (exact: binary32 values are
+    binary64 values).  |q| must be below 2^128."""
+    if q == 0:
+        return 0.0
+    sign = -1 if q < 0 else 1
+    a = abs(q)
+    e = a.numerator.bit_length() - a.denominator.bit_length()  # 2^e <= a < 2^(e+1) after the fix-ups
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    e = max(e, -126)  # subnormals share the spacing of the smallest normal binade
+    ulp = Fraction(2) ** (e - 23)
+    n, rem = divmod(a, ulp)
+    n = int(n)
+    half = ulp / 2
+    if rem > half or (rem == half and n % 2 == 1):
+        n += 1
+    return sign * float(n * ulp)
+
+
+def _fp32_update(r, uL, u, uR):
+    """One interior update in the FP32 order of the paper's kernels (Section
+    4): t = uR - 2u rounded (2u is exact), s = t + uL rounded, then r*s + u with
+    a single rounding (the fused multiply-add)."""
+    t = Fraction(round_to_float32(uR - 2 * u))
+    s = Fraction(round_to_float32(t + uL))
+    return Fraction(round_to_float32(r * s + u))
+
+
+def fp32_sync_exact(u0, r, c1, cN, K):
+    """u(K) of Eq. (eqn:sync) in FP32, every operation rounded exactly once
+    from its exact rational value (inputs must be binary32 values)."""
+    u = [Fraction(float(v)) for v in u0]
+    u[0], u[-1] = Fraction(float(c1)), Fraction(float(cN))
+    R = Fraction(float(r))
+    for _ in range(K):
+        u = [u[0]] + [_fp32_update(R, u[i - 1], u[i], u[i + 1]) for i in range(1, len(u) - 1)] + [u[-1]]
+    return np.array([float(x) for x in u], dtype=np.float32)
+
+
+def fp32_async_exact(u0, r, c1, cN, S, q, trace):
+    """u(K) of Eq. (eqn:async) in FP32 with the same exact roundings: a read
+    across a segment boundary takes the neighbour's value at step k - d
+    (d clamped to k) from the kept history of states."""
+    N = len(u0)
+    u = [Fraction(float(v)) for v in u0]
+    u[0], u[-1] = Fraction(float(c1)), Fraction(float(cN))
+    R = Fraction(float(r))
+    seg = segment_of(N, S)
+    hist = [u]
+    trace = np.asarray(trace)
+    for k in range(trace.shape[0]):
+        cur = hist[-1]
+        nxt = [cur[0]] + [Fraction(0)] * (N - 2) + [cur[-1]]
+        for i in range(1, N - 1):
+            uL, uR = cur[i - 1], cur[i + 1]
+            if seg[i - 1] != seg[i]:
+                uL = hist[k - min(int(trace[k][seg[i - 1]][1]), k)][i - 1]
+            if seg[i + 1] != seg[i]:
+                uR = hist[k - min(int(trace[k][seg[i]][0]), k)][i + 1]
+            nxt[i] = _fp32_update(R, uL, cur[i], uR)
+        hist.append(nxt)
+    return np.array([float(x) for x in hist[-1]], dtype=np.float32)

@@ -174,6 +174,35 @@ def test_sync_fp32_mode_is_float_arithmetic():
     assert np.abs(a - b).max() > 0  # it really is float arithmetic
 
 
+def _fp32_inputs(N, seed):
+    rng = np.random.default_rng(seed)
+    # float32 values over several binades, so that the roundings of every
+    # operation land in different places
+    u0 = (rng.uniform(-1, 1, size=N) * 2.0 ** rng.integers(-6, 7, size=N)).astype(np.float32)
+    return u0, np.float32(0.37), np.float32(0.3125), np.float32(-1.7)
+
+
+def test_sync_fp32_mode_rounds_each_operation_once():
+    """The FP32 mode against an exact-rational restatement of the FP32 order
+    of Section 4's kernels (uR - 2u, + uL, fused r*s + u, each rounded to the
+    nearest binary32 once), bit for bit."""
+    u0, r, c1, cN = _fp32_inputs(24, 7)
+    got = oracle.sync(u0, r, c1, cN, 14, dtype=np.float32)
+    assert np.array_equal(got.view(np.uint32), pins.fp32_sync_exact(u0, r, c1, cN, 14).view(np.uint32))
+
+
+@pytest.mark.parametrize("S,q,seed", [(4, 3, 1), (24, 2, 2), (3, 4, 3)])
+def test_async_fp32_mode_rounds_each_operation_once(S, q, seed):
+    """The FP32 switched system (Eq. eqn:async) against the same exact
+    roundings with delayed reads from the kept history, bit for bit."""
+    u0, r, c1, cN = _fp32_inputs(24, 10 + seed)
+    K = 12
+    tr = inputs.delay_trace(K, S, q, seed=seed)
+    got = oracle.async_replay(u0, r, c1, cN, S, q, K, tr, dtype=np.float32)
+    want = pins.fp32_async_exact(u0, r, c1, cN, S, q, tr)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
 # --------------------------------------------------------------------------- async
 
 
