@@ -362,3 +362,27 @@ def fp32_async_exact(u0, r, c1, cN, S, q, trace):
             nxt[i] = _fp32_update(R, uL, cur[i], uR)
         hist.append(nxt)
     return np.array([float(x) for x in hist[-1]], dtype=np.float32)
+
+
+def fp32_periodic_exact(u0, r, K, S=1, q=1, trace=None):
+    """u(K) on the periodic ring (Section 5.3) in FP32 with the exact single
+    roundings of fp32_sync_exact; with a trace (K, S, 2), a read across
+    boundary b (segment b to segment (b+1) mod S) takes the neighbour's value
+    at step k - d, d clamped to k."""
+    N = len(u0)
+    R = Fraction(float(r))
+    seg = segment_of(N, S)
+    hist = [[Fraction(float(v)) for v in u0]]
+    for k in range(K):
+        cur = hist[-1]
+        nxt = []
+        for i in range(N):
+            il, ir = (i - 1) % N, (i + 1) % N
+            tl = tr_ = k
+            if trace is not None and seg[il] != seg[i]:
+                tl = k - min(int(trace[k][seg[il]][1]), k)
+            if trace is not None and seg[ir] != seg[i]:
+                tr_ = k - min(int(trace[k][seg[i]][0]), k)
+            nxt.append(_fp32_update(R, hist[tl][il], cur[i], hist[tr_][ir]))
+        hist.append(nxt)
+    return np.array([float(x) for x in hist[-1]], dtype=np.float32)

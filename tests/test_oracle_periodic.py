@@ -85,3 +85,22 @@ def test_async_periodic_has_no_unique_steady_state():
         finals.append(u.mean())
     assert abs(finals[0] - finals[1]) > 1e-6      # ... but not to a unique one
     assert abs(finals[0] - rod.u0.mean()) > 1e-6
+
+
+@pytest.mark.parametrize("S,q,seed", [(1, 1, 0), (2, 3, 1), (5, 2, 2), (20, 3, 3)])
+def test_periodic_fp32_mode_rounds_each_operation_once(S, q, seed):
+    """The FP32 ring, synchronous (S = 1) and driven by ring traces, against the
+    exact-rational restatement of the FP32 operation order with each operation
+    rounded once to the nearest binary32, bit for bit."""
+    rng = np.random.default_rng(40 + seed)
+    N, K = 20, 12
+    u0 = (rng.uniform(-1, 1, size=N) * 2.0 ** rng.integers(-5, 6, size=N)).astype(np.float32)
+    r = np.float32(0.4375)
+    if S == 1:
+        got = oracle.sync_periodic(u0, r, K, dtype=np.float32)
+        want = pins.fp32_periodic_exact(u0, r, K)
+    else:
+        tr = inputs.periodic_delay_trace(K, S, q, seed=seed)
+        got = oracle.async_periodic(u0, r, S, q, K, tr, dtype=np.float32)
+        want = pins.fp32_periodic_exact(u0, r, K, S, q, tr)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
