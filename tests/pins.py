@@ -14,10 +14,11 @@ the mathematics fixes for the update of Section 2 (Eq. eqn:sync) and Section 3
   z(k) = [u(k); u(k-1); ...; u(k-q+1)] with one explicit block matrix per step
   built from the delays; times before 0 are served by z(0) = [u0; ...; u0].
 * brute_adjoint: gradients by the transposed products of those matrices.
-* fp32_sync_exact / fp32_async_exact: the FP32 operation order of Section 4's
-  kernels with every operation's exact rational result rounded once to the
-  nearest binary32 (round_to_float32, ties to even), so that the oracle's FP32
-  mode can be checked bit for bit rather than within a bound.
+* fp64_sync_exact, fp32_sync_exact, fp32_async_exact, fp32_periodic_exact:
+  the operation order of Section 4's kernels with every operation's exact
+  rational result rounded once to the nearest binary64 or binary32 (ties to
+  even), so that the oracle is checked bit for bit on general data rather than
+  within a bound.
 """
 from __future__ import annotations
 
@@ -319,13 +320,34 @@ def round_to_float32(q):
     return sign * float(n * ulp)
 
 
+def round_to_float64(q):
+    """The binary64 value nearest to the rational q, ties to even: Python's
+    int / int division (which float(Fraction) uses) is correctly rounded."""
+    return float(q)
+
+
+def _update(r, uL, u, uR, rnd):
+    """One interior update in the order of the paper's kernels (Section 4):
+    t = uR - 2u rounded (2u is exact), s = t + uL rounded, then r*s + u with a
+    single rounding (the fused multiply-add); rnd rounds a rational."""
+    t = Fraction(rnd(uR - 2 * u))
+    s = Fraction(rnd(t + uL))
+    return Fraction(rnd(r * s + u))
+
+
 def _fp32_update(r, uL, u, uR):
-    """One interior update in the FP32 order of the paper's kernels (Section
-    4): t = uR - 2u rounded (2u is exact), s = t + uL rounded, then r*s + u with
-    a single rounding (the fused multiply-add)."""
-    t = Fraction(round_to_float32(uR - 2 * u))
-    s = Fraction(round_to_float32(t + uL))
-    return Fraction(round_to_float32(r * s + u))
+    return _update(r, uL, u, uR, round_to_float32)
+
+
+def fp64_sync_exact(u0, r, c1, cN, K):
+    """u(K) of Eq. (eqn:sync) in FP64 with every operation's exact rational
+    result rounded once to the nearest binary64."""
+    u = [Fraction(float(v)) for v in u0]
+    u[0], u[-1] = Fraction(float(c1)), Fraction(float(cN))
+    R = Fraction(float(r))
+    for _ in range(K):
+        u = [u[0]] + [_update(R, u[i - 1], u[i], u[i + 1], round_to_float64) for i in range(1, len(u) - 1)] + [u[-1]]
+    return np.array([float(x) for x in u])
 
 
 def fp32_sync_exact(u0, r, c1, cN, K):

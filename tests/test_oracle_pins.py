@@ -191,6 +191,15 @@ def test_sync_fp32_mode_rounds_each_operation_once():
     assert np.array_equal(got.view(np.uint32), pins.fp32_sync_exact(u0, r, c1, cN, 14).view(np.uint32))
 
 
+def test_sync_fp64_rounds_each_operation_once():
+    """The FP64 sweep on general (non-dyadic) data against the same
+    exact-rational restatement with binary64 roundings, bit for bit."""
+    rng = np.random.default_rng(8)
+    u0 = rng.uniform(-1, 1, size=24) * 2.0 ** rng.integers(-30, 31, size=24)
+    got = oracle.sync(u0, 0.3712, 0.1, -2.5, 14)
+    assert np.array_equal(got.view(np.uint64), pins.fp64_sync_exact(u0, 0.3712, 0.1, -2.5, 14).view(np.uint64))
+
+
 @pytest.mark.parametrize("S,q,seed", [(4, 3, 1), (24, 2, 2), (3, 4, 3)])
 def test_async_fp32_mode_rounds_each_operation_once(S, q, seed):
     """The FP32 switched system (Eq. eqn:async) against the same exact
