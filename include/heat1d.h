@@ -171,8 +171,8 @@ int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_devi
  * The bounded-delay model of Section 3 (Eq. (eqn:async)) applied to blocks of
  * T steps instead of single steps; the paper has no such run (its PEs exchange
  * one value per step), so the model is defined here.  T is the handle's halo
- * depth (heat1d_opts.halo_steps, default 64, at most the shortest segment;
- * heat1d_get_opts reports the value in use).  Time is cut into blocks of T
+ * depth (heat1d_opts.halo_steps, with the on-chip defaults given there, at
+ * most the shortest segment; heat1d_get_opts reports the value in use).  Time is cut into blocks of T
  * steps; in block b (steps bT .. bT+tb-1, tb = min(T, K-bT)) every segment
  * advances tb steps on its own points at step bT plus two T-wide halo strips:
  * its left neighbour's last T points at step (b-dL)T and its right
