@@ -132,6 +132,21 @@ def test_sharded_blocked_async_equals_oracle():
     assert np.array_equal(got, oracle.async_blocked(u0, 0.41, 0.1, 0.9, world, q, T, K, trace))
 
 
+def test_sharded_per_step_async_equals_eqn_async():
+    """Blocks of one step over two gloo ranks (one point-wide strips, delays per
+    step): the run of Eq. (eqn:async) with one segment per rank, bit for bit."""
+    import oracle
+    from paper_1510_08982_gb300 import inputs
+    world, N, K, q = 2, 120, 40, 3
+    cfg = (N, K, 1, q, 0.45, -0.3, 0.6, 8, True)
+    got = _run(world, cfg)
+    rng = np.random.default_rng(8)
+    u0 = rng.uniform(-1, 1, size=N)
+    trace = inputs.delay_trace(K, world, q, seed=8)
+    assert trace.any()
+    assert np.array_equal(got, oracle.async_replay(u0, 0.45, -0.3, 0.6, world, q, K, trace))
+
+
 def test_strip_history_and_plan():
     from paper_1510_08982_gb300 import dist as hd
     assert [hd.chunk(10, 3, k) for k in range(3)] == [(0, 4), (4, 7), (7, 10)]
