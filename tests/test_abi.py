@@ -59,3 +59,53 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
 def test_build_is_in_tree_for_sm103a():
     assert build_mod.LIB.startswith(os.path.join(ROOT, "paper_1510_08982_gb300"))
     assert "arch=compute_103a,code=sm_103a" in build_mod.ARCH
+
+
+def test_every_entry_point_rejects_a_null_handle_without_a_gpu(lib):
+    """Each call checks its handle (and null buffers) before any CUDA call and
+    reports HEAT1D_ERR_INVAL with a message; destroy accepts NULL."""
+    buf = ctypes.create_string_buffer(64)
+    o = heat1d.default_opts()
+    calls = {
+        "heat1d_set_stream": (None, None),
+        "heat1d_set_snapshots": (None, None, 1, 1),
+        "heat1d_set_opts": (None, ctypes.byref(o)),
+        "heat1d_get_opts": (None, ctypes.byref(o)),
+        "heat1d_num_segments": (None, None),
+        "heat1d_set_u": (None, buf, 0),
+        "heat1d_get_u": (None, buf, 0),
+        "heat1d_run_sync": (None, 10),
+        "heat1d_run_async": (None, 10, None, 0),
+        "heat1d_trace_bytes": (None, 10),
+        "heat1d_replay": (None, 10, buf, 0),
+        "heat1d_sync": (None,),
+        "heat1d_run_async_blocked": (None, 10, None, 0),
+        "heat1d_replay_blocked": (None, 10, buf, 0),
+        "heat1d_blocked_trace_bytes": (None, 10),
+        "heat1d_adjoint": (None, 10, None, 0, buf, 0, buf, None, None),
+        "heat1d_vjp": (None, 10, None, 0, buf, 0, buf, None),
+        "heat1d_batch_run": (None, buf, None),
+        "heat1d_batch_sync": (None,),
+        "heat1d_batch_describe": (None, buf),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == heat1d.ERR_INVAL, name
+        assert heat1d.last_error(), name
+    lib.heat1d_destroy(None)
+    lib.heat1d_batch_destroy(None)
+
+
+def test_buffer_and_batch_arguments_are_checked_without_a_gpu(lib):
+    a = ctypes.create_string_buffer(64)
+    b = ctypes.create_string_buffer(64)
+    f = lib.heat1d_run_sync_noalloc
+    assert f(None, b, 10, 0.25, 0.0, 1.0, heat1d.F64, 5, 0, None, None) == heat1d.ERR_INVAL
+    assert f(a, a, 10, 0.25, 0.0, 1.0, heat1d.F64, 5, 0, None, None) == heat1d.ERR_INVAL
+    assert "differ" in heat1d.last_error()
+    assert f(a, b, 2, 0.25, 0.0, 1.0, heat1d.F64, 5, 0, None, None) == heat1d.ERR_INVAL
+    assert not lib.heat1d_batch_create(None, 5, heat1d.F64, None)
+    rod = heat1d.RodSpec(0, 100, 10, 0.25, 0.0, 1.0)
+    assert not lib.heat1d_batch_create(ctypes.byref(rod), 1, 7, None)
+    assert "dtype" in heat1d.last_error()
+    assert lib.heat1d_adjoint_batched(0, 100, 10, None, None, None, heat1d.F64, None, None, 0, 0, 3, None, 0,
+                                      None, None, None, None, None) == heat1d.ERR_INVAL
