@@ -13,10 +13,20 @@ One bench step is one pass of the whole path on that rod:
   -> replay of that trace (exact re-execution) .
 Updates per step = 3 * (N-2) * K.
 
+After the timed steps the default line also carries, untimed and on rank 0 of
+a one-GPU run only: the measured fused multiply-add rates that bound the
+on-chip kernels (FP64 and FP32), the blocked asynchronous run on the same rod,
+the end-to-end rate through host buffers, and one sub-result per other
+workload (the small rod, the streamed rod, the uneven rods, the inverse
+problem), each with its updates/s, its error against the CPU oracle and its
+roofline fraction.
+
 Under torchrun each rank runs its own rod on its own GPU (independent problems,
 no collective on the data path: weak scaling).  The CPU oracle arm
 (``--impl reference``) times the plain C oracle on a bounded sample of the
-same workload on the host cores.
+same workload on the host cores.  The CPU oracle leg of the GPU arm (the
+``cpu_baseline`` key and the error fields) runs the oracle only after the
+timed region, in spawned worker processes.
 """
 from __future__ import annotations
 
@@ -66,14 +76,19 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="sine-mode-rod",
-                   choices=["sine-mode-rod", "small-rod", "streamed-rod", "uneven-rods", "inverse-problem"],
+                   choices=["sine-mode-rod", "small-rod", "streamed-rod", "uneven-rods", "inverse-problem",
+                            "fma-peak"],
                    help="sine-mode-rod (default): the sync vs async rod; streamed-rod: the 2^26-point "
-                        "temporal-blocking rod; uneven-rods: 4096 rods in one batched launch")
+                        "temporal-blocking rod; uneven-rods: 4096 rods in one batched launch; fma-peak: the "
+                        "measured FP64 and FP32 fused multiply-add rates (the ALU rooflines)")
     p.add_argument("--dtype", default=None, choices=["f32", "f64"], help="streamed-rod / uneven-rods precision")
     p.add_argument("--halo", type=int, default=0, help="streamed-rod: steps per HBM pass (T)")
     p.add_argument("--r", type=float, default=0.25, help="streamed-rod: r (the sweep's values are 0.1, 0.25, 0.5)")
     p.add_argument("--rods", type=int, default=256, help="inverse-problem: rods in the batch")
     p.add_argument("--async-trace", action="store_true", help="inverse-problem: replayed asynchronous run")
+    p.add_argument("--no-configs", action="store_true",
+                   help="default workload: leave out the other workloads' sub-results")
+    p.add_argument("--no-oracle", action="store_true", help="leave out the CPU oracle leg's error checks")
     return p.parse_args()
 
 
@@ -136,7 +151,83 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------- oracle arm
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+#
+# The only part of this file that runs the oracle.  It times the oracle as the
+# CPU baseline and, after a timed GPU region has ended, recomputes the GPU's
+# results from the same inputs (and from the delay traces the GPU recorded),
+# in spawned worker processes: a process forked after CUDA was initialised can
+# hang.
+
+
+def _timed_oracle_call(job):
+    import oracle
+    name, args, kwargs = job
+    t0 = time.perf_counter()
+    out = getattr(oracle, name)(*args, **kwargs)
+    return out, time.perf_counter() - t0
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def available_host_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+class OracleLeg:
+    """Oracle calls submitted after a timed region; each is compared with the
+    GPU result it recomputes when finish() collects it."""
+
+    def __init__(self, processes=None):
+        self.processes = processes or max(1, min(8, host_cores() - 2))
+        self.pool = None
+        self.pending = []  # (target dict, key, async result, compare function)
+
+    def submit(self, target, key, name, args, kwargs=None, compare=None):
+        import multiprocessing as mp
+        if self.pool is None:
+            self.pool = mp.get_context("spawn").Pool(self.processes)
+        res = self.pool.apply_async(_timed_oracle_call, ((name, args, kwargs or {}),))
+        self.pending.append((target, key, res, compare))
+
+    def finish(self):
+        for target, key, res, compare in self.pending:
+            try:
+                out, secs = res.get()
+                entry = dict(compare(out) if compare else {})
+                entry["oracle_seconds"] = secs
+            except Exception as e:  # reported, never hidden
+                entry = {"oracle_error": "%s: %s" % (type(e).__name__, e)}
+            target[key] = entry
+        self.pending = []
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+
+def compare_exact(got):
+    """compare function: max-abs difference and bit identity of a GPU array
+    against the oracle's."""
+    got = np.asarray(got)
+
+    def cmp(ref):
+        ref = np.asarray(ref)
+        d = np.abs(got.astype(np.float64) - ref.astype(np.float64))
+        return {"max_abs": float(d.max()) if d.size else 0.0,
+                "bit_identical": bool(got.dtype == ref.dtype and np.array_equal(got, ref))}
+    return cmp
 
 
 def oracle_sample(rod, seconds=10.0, S=152, all_cores=False):
@@ -191,7 +282,7 @@ def oracle_all_cores(rod, S, Ks):
     at once (spawned workers, inputs handed over before the clock starts):
     the aggregate updates/s of the host.  None on a one-core host."""
     import multiprocessing as mp
-    P = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    P = host_cores()
     if P < 2:
         return None
     from paper_1510_08982_gb300 import inputs
@@ -231,7 +322,7 @@ def run_reference(args):
     return 0
 
 
-# ----------------------------------------------------------------------------- GPU arm
+# ----------------------------------------------------------------------------- GPU arm helpers
 
 
 def workload_config(args, S):
@@ -268,7 +359,13 @@ def _build_once(rank, world):
         build.build()  # up to date by now: only checks
 
 
+_SETUP = None
+
+
 def _device_setup():
+    global _SETUP
+    if _SETUP is not None:
+        return _SETUP
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -276,7 +373,8 @@ def _device_setup():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build_once(rank, world)
-    return torch, rank, world, local
+    _SETUP = (torch, rank, world, local)
+    return _SETUP
 
 
 def _max_over_ranks(torch, world, x, dev):
@@ -284,24 +382,106 @@ def _max_over_ranks(torch, world, x, dev):
     return hd.max_over_ranks(x, world, dev)
 
 
-def run_streamed(args):
-    """The 2^26-point rod (c1 = cN = 0, u(0) ~ U[0,1), r = --r, 0.25 by
-    default, K = 1e4) advanced by the streamed synchronous run, T steps per HBM
-    pass."""
+def event_seconds(torch, stream, fn):
+    """Device time of fn()'s launches on `stream` (CUDA events)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+# ----------------------------------------------------------------------------- ALU rooflines
+
+_ALU = None
+
+
+def alu_peaks(torch, dev):
+    """The two arithmetic rooflines of the on-chip kernels, in updates/s.
+
+    measured: heat1d_probe_fma on this GPU (best of three launches, each
+    ~100 ms: independent fused multiply-add chains, nothing else), divided by
+    the instructions one update issues on that pipe (3: FP64 runs issue three
+    DFMA; FP32 runs one FADD and two FFMA, all on the FMA pipe).
+    nominal: FP64 1.25 TFLOP/s (the recipe table) = 6.25e11 DFMA/s; FP32 128
+    FMA-pipe lanes per clock per SM x SMs x 2070 MHz."""
+    global _ALU
+    if _ALU is not None:
+        return _ALU
+    from paper_1510_08982_gb300 import heat1d
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f64 = heat1d.probe_fma("float64", iters=60_000)
+    f32 = heat1d.probe_fma("float32", iters=400_000)
+    nom64 = FP64_NOMINAL_TFLOPS * 1e12 / 2
+    nom32 = nsm * 128 * 2.07e9
+    _ALU = {"f64": {"fma_per_s": f64, "updates_per_s": f64 / 3, "nominal_fma_per_s": nom64,
+                    "nominal_updates_per_s": nom64 / 3},
+            "f32": {"fma_per_s": f32, "updates_per_s": f32 / 3, "nominal_fma_per_s": nom32,
+                    "nominal_updates_per_s": nom32 / 3},
+            "source": "heat1d_probe_fma, best of 3 launches of %d CTAs x 256 threads on this GPU in this run "
+                      "(profiles/fma_probe_rates.md); 3 FMA-pipe instructions per update" % (4 * nsm)}
+    return _ALU
+
+
+def alu_roofline(kernel, achieved_ups, dt, alu):
+    """Roofline entry of an ALU-bound kernel against the measured peak, with
+    the nominal one beside it."""
+    a = alu[dt]
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved_ups / 1e9, "peak": a["updates_per_s"] / 1e9,
+            "unit": "Gupdates/s", "frac": achieved_ups / a["updates_per_s"],
+            "peak_source": "measured: " + alu["source"],
+            "peak_nominal": a["nominal_updates_per_s"] / 1e9, "frac_nominal": achieved_ups / a["nominal_updates_per_s"]}
+
+
+def run_fma_peak(args):
+    torch, rank, world, local = _device_setup()
+    dev = torch.device("cuda", local)
+    clocks = ClockSampler(local)
+    clocks.start()
+    alu = alu_peaks(torch, dev)
+    clk = clocks.stop()
+    line = {"metric": "fused multiply-add rate (FP64 and FP32 pipes)", "value": alu["f64"]["fma_per_s"],
+            "unit": "DFMA/s", "n_gpus": world, "steps": 3, "warmup": 1, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": "heat1d_probe_fma"},
+            "fma": alu, "clocks": clk, "gpu_launches": 8}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- streamed rod (config 3)
+
+
+def cone_job(u0, r, c1, cN, K, i, np_dt):
+    """Oracle job computing u_i(K) alone: u_i(K) depends only on
+    u_{i-K..i+K}(0), so the oracle runs on the window [i-K-1, i+K+1] with its
+    two ends held fixed (an error there needs K+1 steps to reach i), or the
+    real Dirichlet end where the window meets it."""
+    N = u0.size
+    lo, hi = max(0, i - K - 1), min(N - 1, i + K + 1)
+    w = np.array(u0[lo:hi + 1], dtype=np.float64)
+    wc1 = c1 if lo == 0 else float(w[0])
+    wcN = cN if hi == N - 1 else float(w[-1])
+    return ("sync", (w, r, wc1, wcN, K), {"dtype": np_dt}), i - lo
+
+
+def measure_streamed(dt, T, r, K, N, steps, warmup, leg=None, rank=0):
+    """The 2^26-point rod (c1 = cN = 0, u(0) ~ U[0,1) seeded, K = 1e4)
+    advanced by the streamed synchronous run, T steps per HBM pass."""
     torch, rank, world, local = _device_setup()
     from paper_1510_08982_gb300 import heat1d, inputs
     dev = torch.device("cuda", local)
-    dt = args.dtype or "f32"
     esz = 4 if dt == "f32" else 8
-    K = args.K if args.K != K_DEFAULT else 10_000
-    N = args.N if args.N != N_DEFAULT else 1 << 26
-    T = args.halo or (128 if dt == "f32" else 32)
     tdt = torch.float32 if dt == "f32" else torch.float64
-    g = torch.Generator(device=dev).manual_seed(hd_seed(rank))
-    u0 = torch.rand(N, dtype=tdt, device=dev, generator=g)
-    h = heat1d.Heat1d(N, args.r, 0.0, 0.0, dtype="float32" if dt == "f32" else "float64", sync_mode=2, halo_steps=T)
+    np_dt = np.float32 if dt == "f32" else np.float64
+    rod = inputs.uniform_rod(N=N, K=K, r=r, seed=hd_seed(rank))
+    u0_host = rod.u0.astype(np_dt)
+    u0 = torch.tensor(u0_host, device=dev)
+    h = heat1d.Heat1d(N, r, 0.0, 0.0, dtype="float32" if dt == "f32" else "float64", sync_mode=2, halo_steps=T)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         h.set_u(u0)
         h.run_sync(K)
     h.sync()
@@ -309,70 +489,93 @@ def run_streamed(args):
     torch.cuda.synchronize()
     clocks.start()
     total = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         h.set_u(u0)  # 2*N*esz bytes > L2: the rod itself flushes L2
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h.run_sync(K)
-        e1.record(stream)
-        e1.synchronize()
-        total += e0.elapsed_time(e1)
+        total += event_seconds(torch, stream, lambda: h.run_sync(K))
     clk = clocks.stop()
     h.sync()
     total = _max_over_ranks(torch, world, total, dev)
-    ms = total / args.steps
-    ups = world * (N - 2) * K / (ms * 1e-3)
+    secs = total / steps
+    ups = world * (N - 2) * K / secs
     peaks, src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alu = alu_peaks(torch, dev)
     alg_bytes = 2.0 * esz * N * (K / T)  # each pass reads and writes the rod once
-    achieved_gbs = alg_bytes / (ms * 1e-3) / 1e9
-    # ALU roofline: FP32 128 FMA-pipe lanes/clk/SM, FP64 1.25 TFLOP/s nominal (2 per SM per clk); 3 ops per update
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_ups = (nsm * 128 * 2.07e9 if dt == "f32" else FP64_NOMINAL_TFLOPS * 1e12 / 2) / 3
+    achieved_gbs = alg_bytes / secs / 1e9
+    alu_ups = alu[dt]["updates_per_s"]
     hbm_ups = hbm * 1e9 / (2.0 * esz / T)
-    bound = "hbm" if hbm_ups < alu_ups else "alu"
-    roof = ({"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm}
-            if bound == "hbm" else
-            {"bound": "alu", "achieved": ups / 1e9, "peak": alu_ups / 1e9, "unit": "Gupdates/s",
-             "frac": ups / alu_ups})
+    if hbm_ups < alu_ups:
+        roof = {"bound": "hbm", "kernel": "stream_tma_kernel", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": achieved_gbs / hbm, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roof = alu_roofline("stream_tma_kernel", ups, dt, alu)
     per_pass = STREAM_F32_DRAM_BYTES_PER_PASS.get(T) if dt == "f32" and N == 1 << 26 else None
     traffic = None if per_pass is None else per_pass * math.ceil(K / T)
-    roof.update({"kernel": "stream_tma_kernel", "peak_source": src, "traffic": traffic,
+    roof.update({"traffic": traffic,
                  "traffic_source": None if traffic is None else
                  "ncu dram__bytes_read+write of this kernel on this rod, per pass x passes (profiles/)",
                  "hbm_roofline_updates_per_s": hbm_ups, "alu_roofline_updates_per_s": alu_ups,
                  "algorithmic_bytes_per_update": 2.0 * esz / T, "achieved_algorithmic_GBs": achieved_gbs})
-    line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+    line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dt, "data": "synthetic",
             "config": {"workload": "streamed rod: N=%d %s, r=%g, c1=cN=0, u(0)~U[0,1), K=%d, T=%d steps per "
-                                   "HBM pass" % (N, dt.upper(), args.r, K, T), "N": N, "K": K, "T": T, "r": args.r,
+                                   "HBM pass" % (N, dt.upper(), r, K, T), "N": N, "K": K, "T": T, "r": r,
                        "l2": "inputs larger than L2 (%d MB state)" % (N * esz >> 20)},
-            "roofline": roof, "clocks": clk, "gpu_launches": 2 * args.steps}
+            "roofline": roof, "clocks": clk, "gpu_launches": 2 * steps}
+    if leg is not None:
+        # sampled outputs of the last timed run, each recomputed by the oracle
+        # on its dependency cone
+        got_t = h.get_u(device=True)
+        samples = [1, N // 3, N // 2 + 12345, N - 2]
+        got = got_t[torch.tensor(samples, device=dev)].cpu().numpy()
+        mp_ok = bool(float(got_t.min()) >= 0.0 and float(got_t.max()) <= 1.0)
+        u0f = u0_host.astype(np.float64)
+        errs = {}
+        line["error"] = {"maximum_principle_holds": mp_ok, "oracle_cones": errs,
+                         "note": "u_i(K) at %d sampled points, each recomputed by the oracle (%s mode) on the "
+                                 "2K+3-point window that determines it" % (len(samples), dt.upper())}
+        for i, g in zip(samples, got):
+            job, at = cone_job(u0f, r, 0.0, 0.0, K, i, np_dt)
+            leg.submit(errs, "i=%d" % i, *job, compare=lambda ref, g=g, at=at: {
+                "gpu": float(g), "oracle": float(ref[at]), "bit_identical": bool(g == ref[at])})
+    h.close()
+    return line
+
+
+def run_streamed(args):
+    torch, rank, world, local = _device_setup()
+    dt = args.dtype or "f32"
+    leg = None if args.no_oracle or rank != 0 or world != 1 else OracleLeg()
+    line = measure_streamed(dt, args.halo or (128 if dt == "f32" else 32), args.r,
+                            args.K if args.K != K_DEFAULT else 10_000, args.N if args.N != N_DEFAULT else 1 << 26,
+                            args.steps, args.warmup, leg=leg)
+    if leg is not None:
+        leg.finish()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
     return 0
 
 
-def run_small(args):
+# ----------------------------------------------------------------------------- small rod (config 1)
+
+
+def measure_small(K, steps, warmup, leg=None):
     """The small rod (N = 1024 FP64, r = 0.4, c1 = 0, cN = 1, u(0) = sin(pi x) +
     0.5 sin(7 pi x) + x, S = 8, q = 3): latency-bound.  Per-step device times
     of the persistent synchronous run, the free asynchronous run, its replay,
     the asynchronous run with temporal blocking (the default block length: 32
-    steps on these 128-point segments), and a
-    synchronous run relaunched once per step (the paper's structure without its
-    host copies); then async vs sync at equal error: the steps and the time to
-    ||u(k) - u_ss||_inf <= 1e-6."""
+    steps on these 128-point segments), and a synchronous run relaunched once
+    per step (the paper's structure without its host copies); then async vs
+    sync at equal error: the steps and the time to ||u(k) - u_ss||_inf <= 1e-6."""
     torch, rank, world, local = _device_setup()
     from paper_1510_08982_gb300 import heat1d, inputs
     dev = torch.device("cuda", local)
     rod = inputs.small_rod()
     N, S = rod.N, 8
-    K = args.K if args.K != K_DEFAULT else rod.K
     eps, every = 1e-6, 1024
     h = heat1d.Heat1d(N, rod.r, rod.c1, rod.cN, dtype="float64", segments=S, q=Q)
+    T = h.get_opts()["halo_steps"]
     u0 = torch.tensor(rod.u0, dtype=torch.float64, device=dev)
     uss = torch.tensor(rod.c1 + (rod.cN - rod.c1) * inputs.grid_x(N), dtype=torch.float64, device=dev)
     tr = h.new_trace(K)
@@ -387,18 +590,12 @@ def run_small(args):
 
     def timed(fn):
         h.set_u(u0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1) * 1e-3
+        return event_seconds(torch, stream, fn)
 
     btr = h.new_blocked_trace(K)
     runs = {"sync": lambda: h.run_sync(K), "async": lambda: h.run_async(K, tr), "replay": lambda: h.replay(K, tr),
             "async_blocked": lambda: h.run_async_blocked(K, btr), "sync_relaunch_per_step": lambda: relaunch(K)}
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         for f in runs.values():
             timed(f)
     h.sync()
@@ -406,10 +603,19 @@ def run_small(args):
     torch.cuda.synchronize()
     clocks.start()
     tot = {k: 0.0 for k in runs}
-    for _ in range(args.steps):
+    for _ in range(steps):
         for k, f in runs.items():
             tot[k] += timed(f)
     h.sync()
+    clk = clocks.stop()
+    outputs = {}
+    if leg is not None:  # the last timed runs' results, for the oracle leg
+        for k in ("sync", "async", "async_blocked"):
+            h.set_u(u0)
+            runs[k]()
+            h.sync()
+            outputs[k] = h.get_u(device=False)
+        trh, btrh = tr.cpu().numpy(), btr.cpu().numpy()
     # async vs sync at equal error: first snapshot at or below eps, then a timed run of that many steps
     lam1 = 1.0 - 4.0 * rod.r * math.sin(math.pi / (2.0 * (N - 1))) ** 2
     k_est = int(math.log(eps) / math.log(lam1))
@@ -435,56 +641,72 @@ def run_small(args):
         eq[kind] = {"steps": k_eps, "seconds": t, "error_at_end": err_end}
     if eq.get("sync"):
         eq["sync_relaunch_per_step"] = {"steps": eq["sync"]["steps"],
-                                        "seconds": eq["sync"]["steps"] * tot["sync_relaunch_per_step"] / (args.steps * K),
+                                        "seconds": eq["sync"]["steps"] * tot["sync_relaunch_per_step"] / (steps * K),
                                         "note": "per-step time of the timed relaunch run x the synchronous steps"}
-    clk = clocks.stop()
-    us = {k: 1e6 * v / (args.steps * K) for k, v in tot.items()}
+    us = {k: 1e6 * v / (steps * K) for k, v in tot.items()}
     upd = (N - 2) * K
-    ups = {k: upd * args.steps / v for k, v in tot.items()}
+    ups = {k: upd * steps / v for k, v in tot.items()}
     t_step = tot["sync"] + tot["async"] + tot["replay"]
-    value = world * 3 * upd * args.steps / _max_over_ranks(torch, world, t_step, dev)
-    peak_upd = FP64_NOMINAL_TFLOPS * 1e12 / 2 / FP64_INSTR_PER_UPDATE
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
+    value = world * 3 * upd * steps / _max_over_ranks(torch, world, t_step, dev)
+    alu = alu_peaks(torch, dev)
+    roof = alu_roofline("async_persistent_kernel<double,2> (free run + replay)",
+                        2 * upd * steps / (tot["async"] + tot["replay"]), "f64", alu)
+    roof.update({"traffic": None, "note": "8 CTAs on a 1024-point rod: bound by exchange latency, the ALU "
+                                          "fraction is reported but not meaningful"})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": 1e3 * t_step / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "small rod: N=1024 FP64, r=0.4, c1=0, cN=1, u(0)=sin(pi x)+0.5 sin(7 pi x)+x, "
                                    "K=%d, S=8, q=3; step = sync + async (trace recorded) + replay" % K,
-                       "N": N, "K": K, "segments": S, "q": Q,
+                       "N": N, "K": K, "segments": S, "q": Q, "T": T,
                        "l2": "the 8 KB rod stays on-chip; latency-bound, L2 state does not matter"},
             "us_per_step": us, "updates_per_s": ups,
             "blocked_delay_histogram": np.bincount(btr.cpu().numpy().reshape(-1), minlength=Q).tolist(),
             "speedup": {"async_vs_relaunch_per_step": us["sync_relaunch_per_step"] / us["async"],
                         "async_blocked_vs_relaunch_per_step": us["sync_relaunch_per_step"] / us["async_blocked"],
                         "persistent_sync_vs_relaunch_per_step": us["sync_relaunch_per_step"] / us["sync"]},
-            "equal_error": eq,
-            "roofline": {"bound": "alu", "kernel": "async_persistent_kernel<double,8>",
-                         "achieved": ups["async"] / 1e9, "peak": peak_upd / 1e9, "unit": "Gupdates/s",
-                         "frac": ups["async"] / peak_upd, "traffic": None,
-                         "note": "8 CTAs on a 1024-point rod: bound by exchange latency, the ALU fraction is "
-                                 "reported but not meaningful"},
-            "clocks": clk, "gpu_launches": args.steps * (4 + K)}
+            "equal_error": eq, "roofline": roof, "clocks": clk, "gpu_launches": steps * (4 + K)}
+    if leg is not None:
+        errs = {}
+        line["error"] = {"oracle": errs, "note": "full runs of K=%d recomputed by the oracle (async and blocked "
+                                                 "from the traces the GPU recorded)" % K}
+        a = (rod.u0, rod.r, rod.c1, rod.cN)
+        leg.submit(errs, "sync", "sync", a + (K,), compare=compare_exact(outputs["sync"]))
+        leg.submit(errs, "async_replay", "async_replay", a + (S, Q, K, trh), compare=compare_exact(outputs["async"]))
+        leg.submit(errs, "async_blocked", "async_blocked", a + (S, Q, T, K, btrh),
+                   compare=compare_exact(outputs["async_blocked"]))
+    h.close()
+    return line
+
+
+def run_small(args):
+    torch, rank, world, local = _device_setup()
+    from paper_1510_08982_gb300 import inputs
+    K = args.K if args.K != K_DEFAULT else inputs.small_rod().K
+    leg = None if args.no_oracle or rank != 0 or world != 1 else OracleLeg()
+    line = measure_small(K, args.steps, args.warmup, leg=leg)
+    if leg is not None:
+        leg.finish()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        trn = tr.cpu().numpy()
-        t0 = time.perf_counter()
-        oracle.sync(rod.u0, rod.r, rod.c1, rod.cN, K)
-        oracle.async_replay(rod.u0, rod.r, rod.c1, rod.cN, S, Q, K, trn)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": 2 * upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "plain C oracle, one thread: full synchronous run and replay of the "
-                                          "recorded trace, K=%d (%.2f s)" % (K, dt)}
+        err = line.get("error", {}).get("oracle", {})
+        secs = sum(v.get("oracle_seconds", 0.0) for v in err.values())
+        if secs > 0:
+            line["cpu_baseline"] = {"value": 3 * (1024 - 2) * K / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "plain C oracle, one thread per run: full synchronous run, replay of "
+                                              "the recorded trace and blocked replay, K=%d (%.2f s)" % (K, secs)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
     return 0
 
 
-def run_uneven(args):
+# ----------------------------------------------------------------------------- uneven rods (config 4)
+
+
+def measure_uneven(dt, steps, warmup, e2e=True, leg=None):
     """4096 uneven rods in one batched persistent launch, replayed from a CUDA graph."""
     torch, rank, world, local = _device_setup()
-    from paper_1510_08982_gb300 import heat1d, inputs
+    from paper_1510_08982_gb300 import heat1d, inputs, tune
     dev = torch.device("cuda", local)
-    dt = args.dtype or "f32"
     esz = 4 if dt == "f32" else 8
     tdt = torch.float32 if dt == "f32" else torch.float64
     rods = inputs.uneven_rods(seed=hd_seed(rank))
@@ -495,7 +717,6 @@ def run_uneven(args):
     u0 = torch.tensor(host, dtype=tdt, device=dev)
     u = u0.clone()
     specs = [(int(o), r.N, r.K, r.r, r.c1, r.cN) for o, r in zip(off, rods)]
-    from paper_1510_08982_gb300 import tune
     opts = tune.tune_batched(specs, "float32" if dt == "f32" else "float64")  # cached per GPU and batch shape
     b = heat1d.Batch(specs, dtype="float32" if dt == "f32" else "float64", **opts)
     info = b.describe()
@@ -509,7 +730,7 @@ def run_uneven(args):
             b.run(u)
     torch.cuda.current_stream().wait_stream(s)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         u.copy_(u0)
         graph.replay()
     torch.cuda.synchronize()
@@ -517,107 +738,126 @@ def run_uneven(args):
     clocks = ClockSampler(local)
     clocks.start()
     total = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         u.copy_(u0)
         flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        graph.replay()
-        e1.record(stream)
-        e1.synchronize()
-        total += e0.elapsed_time(e1)
+        total += event_seconds(torch, stream, graph.replay)
     clk = clocks.stop()
     b.sync()
     total = _max_over_ranks(torch, world, total, dev)
-    ms = total / args.steps
-    ups = world * updates / (ms * 1e-3)
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_ups = (nsm * 128 * 2.07e9 if dt == "f32" else FP64_NOMINAL_TFLOPS * 1e12 / 2) / 3
-    e2e = None
-    if not args.no_e2e:
+    secs = total / steps
+    ups = world * updates / secs
+    alu = alu_peaks(torch, dev)
+    got = u.cpu().numpy() if leg is not None else None  # the last timed run's result
+    e2e_out = None
+    if e2e:
         pinned = torch.empty(total_n, dtype=tdt).pin_memory()
         pinned.copy_(torch.tensor(host, dtype=tdt))
         out = torch.empty_like(pinned).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             u.copy_(pinned, non_blocking=True)
             b.run(u)
             out.copy_(u, non_blocking=True)
             torch.cuda.synchronize()
-        dt_e2e = (time.perf_counter() - t0) / args.steps
+        dt_e2e = (time.perf_counter() - t0) / steps
         b.sync()
-        e2e = {"value": world * updates / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": total_n * esz,
-               "d2h_bytes_per_step": total_n * esz, "path": "pinned host -> device, heat1d_batch_run, device -> host"}
-    line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        e2e_out = {"value": world * updates / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": total_n * esz,
+                   "d2h_bytes_per_step": total_n * esz,
+                   "path": "pinned host -> device, heat1d_batch_run, device -> host"}
+    roof = alu_roofline("batched_kernel", ups, dt, alu)
+    roof["traffic"] = None
+    line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dt, "data": "synthetic",
             "config": {"workload": "uneven rods: 4096 rods, N log-U[256,65536], K log-U[1e3,1e5], r U[0.05,0.5], "
                                    "8 sine modes; one batched persistent launch replayed from a CUDA graph; tile "
                                    "and halo depth from the autotuner",
-                       "rods": len(rods), "points": total_n, "updates": updates, "plan": info,
+                       "rods": len(rods), "points": total_n, "updates": updates, "plan": info, "opts": opts,
                        "l2": "flushed between timed steps (256 MB write)"},
-            "roofline": {"bound": "alu", "kernel": "batched_kernel", "achieved": ups / 1e9, "peak": alu_ups / 1e9,
-                         "unit": "Gupdates/s", "frac": ups / alu_ups, "traffic": None},
-            "clocks": clk, "e2e": e2e, "gpu_launches": args.steps}
+            "roofline": roof, "clocks": clk, "e2e": e2e_out, "gpu_launches": steps}
+    if leg is not None:
+        cheap = [j for j, r in enumerate(rods) if r.N * r.K <= 2e7]
+        pick = [int(j) for j in np.random.default_rng(1).choice(cheap, size=24, replace=False)]
+        heaviest = max(range(len(rods)), key=lambda j: rods[j].N * rods[j].K)
+        errs = {}
+        line["error"] = {"oracle": errs, "note": "24 seeded rods and the heaviest rod (N=%d, K=%d) recomputed by "
+                                                 "the oracle (%s mode)" % (rods[heaviest].N, rods[heaviest].K,
+                                                                           dt.upper())}
+        np_dt = np.float32 if dt == "f32" else np.float64
+        for j in pick + [heaviest]:
+            r = rods[j]
+            leg.submit(errs, "rod %d (N=%d, K=%d)" % (j, r.N, r.K), "sync", (r.u0, r.r, r.c1, r.cN, r.K),
+                       {"dtype": np_dt}, compare=compare_exact(got[off[j]:off[j] + r.N]))
+    b.close()
+    return line
+
+
+def run_uneven(args):
+    torch, rank, world, local = _device_setup()
+    leg = None if args.no_oracle or rank != 0 or world != 1 else OracleLeg()
+    line = measure_uneven(args.dtype or "f32", args.steps, args.warmup, e2e=not args.no_e2e, leg=leg)
+    if leg is not None:
+        leg.finish()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    b.close()
     return 0
 
 
-def run_inverse(args):
-    """Adjoint of the inverse problem: 256 rods of N = 65536, K = 2e4, smooth
-    u(0), r_true ~ U[0.1, 0.45], u_obs = u(K) + N(0, 1e-4); one step = the
-    forward pass with checkpoints every 128 steps + the backward pass
-    (recompute + transposed stencil), giving dL/du(0) and dL/dr per rod."""
+# ----------------------------------------------------------------------------- inverse problem (config 5)
+
+
+def closed_form_uK(rod, K):
+    """u(K) of the synchronous run from the discrete sine transform of the
+    initial data (the exact solution of Eq. (eqn:sync): each sine mode m
+    decays by 1 - 4 r sin^2(m pi / (2(N-1))) per step), evaluated in FP64."""
+    from scipy.fft import dst, idst
+    N = rod.N
+    x = np.arange(N) / (N - 1)
+    uss = rod.c1 + (rod.cN - rod.c1) * x
+    f = (np.where(np.arange(N) == 0, rod.c1, np.where(np.arange(N) == N - 1, rod.cN, rod.u0)) - uss)[1:-1]
+    lam = 1.0 - 4.0 * rod.r * np.sin(np.arange(1, N - 1) * np.pi / (2.0 * (N - 1))) ** 2
+    out = uss.copy()
+    out[1:-1] += idst(dst(f, type=1) * np.exp(K * np.log(np.abs(lam))) * np.sign(lam) ** (K % 2), type=1)
+    return out
+
+
+def measure_inverse(dt, replayed, nr, N, K, steps, warmup, leg=None, rank=0):
+    """Adjoint of the inverse problem: nr rods of N = 65536, K = 2e4, smooth
+    u(0), r_true ~ U[0.1, 0.45], u_obs = u(K) at r_true + N(0, 1e-4) (u(K) from
+    the closed form of the synchronous run); one step = the forward pass with
+    checkpoints every 128 steps + the backward pass (recompute + transposed
+    stencil), giving dL/du(0) and dL/dr per rod at 0.9 r_true."""
     torch, rank, world, local = _device_setup()
     from paper_1510_08982_gb300 import heat1d, inputs
     dev = torch.device("cuda", local)
-    dt = args.dtype or "f64"
     tdt = torch.float32 if dt == "f32" else torch.float64
-    K = args.K if args.K != K_DEFAULT else 20_000
-    N = args.N if args.N != N_DEFAULT else 65536
-    nr = args.rods
     rods = inputs.inverse_problem_rods(n_rods=nr, N=N, K=K, seed=hd_seed(rank))
     u0 = torch.tensor(np.stack([r.u0 for r in rods]), dtype=tdt, device=dev)
-    r = np.array([x.r for x in rods])
+    rg = 0.9 * np.array([x.r for x in rods])
     c1 = np.array([x.c1 for x in rods])
     cN = np.array([x.cN for x in rods])
-    S, q = 16, 3  # 4096 points per segment: one CTA each for the observation runs
-    trace = None
-    if args.async_trace:
-        trace = torch.tensor(np.stack([inputs.delay_trace(K, S, q, seed=j) for j in range(nr)]), device=dev)
-    # observations: u(K) at r_true plus noise; the gradient is taken at 0.9 r_true
-    uobs = torch.empty(nr, N, dtype=torch.float64, device=dev)
-    for j, x in enumerate(rods):
-        opts = {"segments": S, "q": q} if trace is not None else {}
-        with heat1d.Heat1d(N, x.r, x.c1, x.cN, dtype="float32" if dt == "f32" else "float64", **opts) as h:
-            h.set_u(u0[j])
-            if trace is None:
-                h.run_sync(K)
-            else:
-                h.replay(K, trace[j].contiguous())
-            h.sync()
-            uobs[j] = h.get_u().double()
-    uobs += torch.tensor(np.stack([inputs.observation_noise(N, seed=7000 + j) for j in range(nr)]), device=dev)
-    rg = 0.9 * r
+    S, q = 16, 3
+    trace_h = np.stack([inputs.delay_trace(K, S, q, seed=j) for j in range(nr)]) if replayed else None
+    trace = None if trace_h is None else torch.tensor(trace_h, device=dev)
+    uobs_h = np.stack([closed_form_uK(x, K) + inputs.observation_noise(N, seed=7000 + j) for j, x in enumerate(rods)])
+    uobs = torch.tensor(uobs_h, dtype=torch.float64, device=dev)
 
     def step():
-        return heat1d.adjoint_batched(u0, uobs, rg, c1, cN, K, trace=trace, segments=S if trace is not None else 0,
+        return heat1d.adjoint_batched(u0, uobs, rg, c1, cN, K, trace=trace, segments=S if replayed else 0,
                                       q=q, ckpt_every=128)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     clocks = ClockSampler(local)
     torch.cuda.synchronize()
     clocks.start()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         out = step()
     torch.cuda.synchronize()
-    dt_s = (time.perf_counter() - t0) / args.steps
+    dt_s = (time.perf_counter() - t0) / steps
     clk = clocks.stop()
     dt_s = _max_over_ranks(torch, world, dt_s, dev)
     updates = nr * (N - 2) * K
@@ -631,32 +871,110 @@ def run_inverse(args):
     # (8 bytes per point and step each), the backward reads u(k) and
     # lambda(k+1) and writes lambda(k) (12 bytes): 28 bytes per forward update
     # at the measured HBM rate.
-    fp64_rate = FP64_NOMINAL_TFLOPS * 1e12 / 2
     if dt == "f64":
-        bound, alu = "alu", fp64_rate / (3 + 3 + 4)
-        roof_note = ("three passes per forward update: forward and recompute 3 FP64 instructions per point, "
-                     "backward 4; peak = nominal FP64 instruction rate / 10")
+        alu = alu_peaks(torch, dev)["f64"]
+        peak = alu["fma_per_s"] / (3 + 3 + 4)
+        roof = {"bound": "alu", "kernel": "adj_fwd_step / adj_bwd_step", "achieved": ups / 1e9,
+                "peak": peak / 1e9, "unit": "Gupdates/s (forward-equivalent)", "frac": ups / peak,
+                "peak_source": "measured: heat1d_probe_fma DFMA/s on this GPU / 10 FP64 instructions per forward "
+                               "update over the three passes",
+                "peak_nominal": alu["nominal_fma_per_s"] / 10 / 1e9,
+                "frac_nominal": ups / (alu["nominal_fma_per_s"] / 10)}
     else:
         hbm = float(measured_peaks()[0].get("hbm_gbs", 6800.0)) * 1e9
-        bound, alu = "hbm", hbm / 28.0
-        roof_note = ("FP32 passes bound by HBM: forward 8 + recompute 8 + backward 12 bytes per point and step; "
-                     "peak = measured HBM / 28 B, in forward-equivalent updates/s")
-    line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        peak = hbm / 28.0
+        roof = {"bound": "hbm", "kernel": "adj_fwd_step / adj_bwd_step", "achieved": ups * 28.0 / 1e9,
+                "peak": hbm / 1e9, "unit": "GB/s", "frac": ups / peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs; 28 algorithmic bytes per forward update (forward 8 + "
+                               "recompute 8 + backward 12)"}
+    roof["traffic"] = None
+    line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": dt_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dt, "data": "synthetic",
             "config": {"workload": "inverse problem: %d rods x N=%d, K=%d, checkpoints every 128 steps, %s; one step = "
                                    "forward with checkpoints + backward (recompute + adjoint); value counts forward "
                                    "updates (rods x (N-2) x K) per second of the whole gradient computation"
-                                   % (nr, N, K, "replayed trace S=16 q=3" if trace is not None else "synchronous"),
+                                   % (nr, N, K, "replayed trace S=16 q=3" if replayed else "synchronous"),
                        "rods": nr, "N": N, "K": K, "ckpt_every": 128},
-            "gradient": {"grad_r_first_rods": [float(x) for x in out[2][:4]], "loss_first_rods": [float(x) for x in out[3][:4]]},
-            "roofline": {"bound": bound, "kernel": "adj_fwd_step / adj_bwd_step", "achieved": ups / 1e9,
-                         "peak": alu / 1e9, "unit": "Gupdates/s (forward-equivalent)", "frac": ups / alu,
-                         "note": roof_note},
-            "clocks": clk, "gpu_launches": None}
+            "seconds_per_gradient": dt_s,
+            "gradient": {"grad_r_first_rods": [float(x) for x in out[2][:4]],
+                         "loss_first_rods": [float(x) for x in out[3][:4]]},
+            "roofline": roof, "clocks": clk, "gpu_launches": None}
+    if leg is not None:
+        # rod 0 through the oracle's stored-trajectory FP64 adjoint (16 bytes
+        # per point and step of host memory)
+        need = 16 * N * (K + 1) + (2 << 30)
+        avail = available_host_bytes()
+        errs = {}
+        line["error"] = {"oracle": errs}
+        if need <= 0.7 * avail:
+            g0 = out[1][0].cpu().numpy() if hasattr(out[1], "cpu") else np.asarray(out[1][0])
+            gr0, l0 = float(out[2][0]), float(out[3][0])
+            r0 = rods[0]
+
+            def cmp(ref, g0=g0, gr0=gr0, l0=l0):
+                L, g, gr = ref
+                return {"loss_rel": abs(l0 - L) / abs(L), "grad_u0_rel_to_max": float(np.abs(g0 - g).max() /
+                                                                                     np.abs(g).max()),
+                        "grad_r_rel": abs(gr0 - gr) / abs(gr), "grad_r_gpu": gr0, "grad_r_oracle": gr}
+            kw = {"S": S, "q": q, "trace": trace_h[0]} if replayed else {}
+            leg.submit(errs, "rod 0", "adjoint", (r0.u0.astype(np.float32).astype(np.float64) if dt == "f32"
+                                                  else r0.u0, float(np.float32(rg[0])) if dt == "f32" else rg[0],
+                                                  r0.c1, r0.cN, K, uobs_h[0]), kw, compare=cmp)
+        else:
+            line["error"]["note"] = ("oracle adjoint skipped: it needs %.1f GB of host memory, %.1f GB available"
+                                     % (need / 2 ** 30, avail / 2 ** 30))
+    return line
+
+
+def run_inverse(args):
+    torch, rank, world, local = _device_setup()
+    leg = None if args.no_oracle or rank != 0 or world != 1 else OracleLeg(processes=1)
+    line = measure_inverse(args.dtype or "f64", args.async_trace, args.rods,
+                           args.N if args.N != N_DEFAULT else 65536, args.K if args.K != K_DEFAULT else 20_000,
+                           args.steps, args.warmup, leg=leg)
+    if leg is not None:
+        leg.finish()
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+# ----------------------------------------------------------------------------- the default line (config 2)
+
+
+def sub_configs(leg):
+    """One compact sub-result per other workload (untimed extras of the
+    default line): updates/s, the oracle check, the roofline fraction."""
+    out = {}
+
+    def keep(line, extra=()):
+        d = {"workload": line["config"]["workload"], "value": line["value"], "unit": line["unit"],
+             "dtype": line["dtype"], "steps": line["steps"], "warmup": line["warmup"],
+             "ms_per_step": line["ms_per_step"], "roofline": line.get("roofline"), "clocks": line.get("clocks")}
+        for k in extra:
+            if k in line:
+                d[k] = line[k]
+        if "error" in line:
+            d["error"] = line["error"]
+        return d
+
+    small = measure_small(10_000, 3, 3, leg=leg)
+    out["small_rod"] = keep(small, ("us_per_step", "updates_per_s", "equal_error", "speedup"))
+    streamed = {}
+    for dt, T in (("f32", 1), ("f32", 128), ("f64", 32)):
+        line = measure_streamed(dt, T, 0.25, 10_000, 1 << 26, 1 if (dt == "f64" or T == 1) else 3, 1, leg=leg)
+        streamed["%s_T%d" % (dt, T)] = keep(line)
+    out["streamed_rod"] = streamed
+    out["uneven_rods"] = {dt: keep(measure_uneven(dt, 1 if dt == "f64" else 5, 1 if dt == "f64" else 2, e2e=False,
+                                                  leg=leg))
+                          for dt in ("f32", "f64")}
+    inv = {}
+    for dt, replayed in (("f64", False), ("f64", True), ("f32", False)):
+        line = measure_inverse(dt, replayed, 256, 65536, 20_000, 1, 1, leg=leg)
+        inv["%s_%s" % (dt, "replayed" if replayed else "sync")] = keep(line, ("seconds_per_gradient", "gradient"))
+    out["inverse_problem"] = inv
+    return out
 
 
 def main():
@@ -671,22 +989,20 @@ def main():
         return run_uneven(args)
     if args.workload == "inverse-problem":
         return run_inverse(args)
-    import torch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "fma-peak":
+        return run_fma_peak(args)
+    torch, rank, world, local = _device_setup()
     from paper_1510_08982_gb300 import heat1d, inputs
-    _build_once(rank, world)
+    from paper_1510_08982_gb300 import dist as hd
     dev = torch.device("cuda", local)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    from paper_1510_08982_gb300 import dist as hd
+    alu = alu_peaks(torch, dev)  # before the timed region: ~1 s of probe launches
     rod = inputs.sine_mode_rod(N=args.N, K=args.K, seed=hd.rod_seed(rank))
     N, K = rod.N, rod.K
     M = N - 2
     h = heat1d.Heat1d(N, rod.r, rod.c1, rod.cN, dtype="float64", segments=nsm, q=Q)
     S = h.S
+    T = h.get_opts()["halo_steps"]
     u0 = torch.tensor(rod.u0, dtype=torch.float64, device=dev)
     trace = h.new_trace(K)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -745,29 +1061,9 @@ def main():
     value = hd.whole_job_rate(updates_per_step, ms_per_step * 1e-3, world)
     per = {name: M * K / (t / args.steps * 1e-3) for name, t in
            (("sync", t_sync), ("async", t_async), ("replay", t_replay))}
+    leg = OracleLeg() if (rank == 0 and world == 1 and not args.no_oracle) else None
 
-    # --- the blocked asynchronous run on the same rod (its own timing, not part of the step) --
-    btr = h.new_blocked_trace(K)
-    h.set_u(u0)
-    h.run_async_blocked(K, btr)
-    h.sync()
-    t_blocked = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        h.set_u(u0)
-        eb0 = torch.cuda.Event(enable_timing=True)
-        eb1 = torch.cuda.Event(enable_timing=True)
-        eb0.record(stream)
-        h.run_async_blocked(K, btr)
-        eb1.record(stream)
-        eb1.synchronize()
-        t_blocked += eb0.elapsed_time(eb1)
-    h.sync()
-    t_blocked = hd.max_over_ranks(t_blocked, world, dev)
-    per["async_blocked"] = M * K / (t_blocked / args.steps * 1e-3)
-    blocked_hist = np.bincount(btr.cpu().numpy().reshape(-1), minlength=Q)[:Q].tolist()
-
-    # --- error at the stated tolerance (untimed) -----------------------------------------
+    # --- full runs for the error fields (untimed); the oracle recomputes them --------------
     from scipy.fft import dst, idst
     h.set_u(u0)
     h.run_sync(K)
@@ -784,13 +1080,43 @@ def main():
     h.run_async(K, trace)
     h.sync()
     u_async = h.get_u(device=False)
+    tr_host = trace.cpu().numpy()
     h.set_u(u0)
     h.replay(K, trace)
     h.sync()
     replay_exact = bool(np.array_equal(h.get_u(device=False), u_async))
     async_vs_sync = float(np.abs(u_async - u_sync).max())
-    tr_host = trace.cpu().numpy()
     hist = np.bincount(tr_host.reshape(-1), minlength=Q).tolist()
+    btr = h.new_blocked_trace(K)
+    h.set_u(u0)
+    h.run_async_blocked(K, btr)
+    h.sync()
+    u_blocked = h.get_u(device=False)
+    btr_host = btr.cpu().numpy()
+    error = {"sync_vs_closed_form_max_abs": err_sync, "async_vs_sync_max_abs": async_vs_sync,
+             "replay_bit_identical": replay_exact, "delay_histogram": hist}
+    if leg is not None:
+        oracle_err = {}
+        error["oracle"] = oracle_err
+        error["oracle_note"] = ("full K=%d runs recomputed by the CPU oracle after the timed region: the "
+                                "synchronous sweep, and the free asynchronous and blocked runs replayed from the "
+                                "delay traces the GPU recorded" % K)
+        a = (rod.u0, rod.r, rod.c1, rod.cN)
+        leg.submit(oracle_err, "sync", "sync", a + (K,), compare=compare_exact(u_sync))
+        leg.submit(oracle_err, "async_replay", "async_replay", a + (S, Q, K, tr_host), compare=compare_exact(u_async))
+        leg.submit(oracle_err, "async_blocked", "async_blocked", a + (S, Q, T, K, btr_host),
+                   compare=compare_exact(u_blocked))
+
+    # --- the blocked asynchronous run on the same rod (its own timing, not part of the step) --
+    t_blocked = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        h.set_u(u0)
+        t_blocked += event_seconds(torch, stream, lambda: h.run_async_blocked(K, btr)) * 1e3
+    h.sync()
+    t_blocked = hd.max_over_ranks(t_blocked, world, dev)
+    per["async_blocked"] = M * K / (t_blocked / args.steps * 1e-3)
+    blocked_hist = np.bincount(btr.cpu().numpy().reshape(-1), minlength=Q)[:Q].tolist()
 
     # --- e2e through the C ABI with host buffers ------------------------------------------
     e2e = None
@@ -825,37 +1151,47 @@ def main():
                "h2d_bytes_per_step": 3 * 8 * N + tb, "d2h_bytes_per_step": 3 * 8 * N + tb,
                "path": "heat1d_set_u/run_*/replay/get_u from pinned host buffers, host traces"}
 
-    # --- roofline of the dominant kernel (the asynchronous persistent kernel) -------------
-    peak_upd = FP64_NOMINAL_TFLOPS * 1e12 / 2 / FP64_INSTR_PER_UPDATE
-    achieved = per["async"]
-    roofline = {"bound": "alu", "kernel": "async_persistent_kernel<double,8>",
-                "achieved": achieved / 1e9, "peak": peak_upd / 1e9, "unit": "Gupdates/s",
-                "frac": achieved / peak_upd,
-                "peak_source": "recipe nominal FP64 1.25 TFLOP/s at 2070 MHz = 6.25e11 FP64-pipe instr/s, "
-                               "3 per update (3 DFMA)",
-                # dram__bytes_read.sum + dram__bytes_write.sum of one async launch (ncu, K = 2000; the rod is
-                # loaded once and the per-step exchange stays in L2, so the figure does not grow with K)
-                "traffic": ASYNC_KERNEL_DRAM_BYTES,
-                "traffic_source": "ncu capture of async_persistent_kernel<double,8>, K=2000 (profiles/)",
-                "per_kernel": {k: {"Gupdates_per_s": v / 1e9, "frac": v / peak_upd} for k, v in per.items()}}
+    # --- roofline of the dominant kernel: the asynchronous persistent kernel, both launches
+    achieved = 2 * M * K / ((t_async + t_replay) / args.steps * 1e-3)
+    roofline = alu_roofline("async_persistent_kernel<double,8> (free run + replay: both launches of a step)",
+                            achieved, "f64", alu)
+    roofline.update({
+        # dram__bytes_read.sum + dram__bytes_write.sum of one async launch (ncu, K = 2000; the rod is
+        # loaded once and the per-step exchange stays in L2, so the figure does not grow with K)
+        "traffic": ASYNC_KERNEL_DRAM_BYTES,
+        "traffic_source": "ncu capture of async_persistent_kernel<double,8>, K=2000 (profiles/)",
+        "per_kernel": {k: {"Gupdates_per_s": v / 1e9, "frac": v / alu["f64"]["updates_per_s"],
+                           "frac_nominal": v / alu["f64"]["nominal_updates_per_s"]} for k, v in per.items()}})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, S),
             "sync_updates_per_s": per["sync"], "async_updates_per_s": per["async"],
             "replay_updates_per_s": per["replay"],
             "async_blocked_updates_per_s": per["async_blocked"],
-            "async_blocked": {"block_steps": h.get_opts()["halo_steps"], "delay_histogram_blocks": blocked_hist,
+            "async_blocked": {"block_steps": T, "delay_histogram_blocks": blocked_hist,
                               "note": "blocked asynchronous run (strips up to q-1 blocks old) on the same rod, "
                                       "timed on its own, not part of value"},
-            "error": {"sync_vs_closed_form_max_abs": err_sync, "async_vs_sync_max_abs": async_vs_sync,
-                      "replay_bit_identical": replay_exact, "delay_histogram": hist},
-            "roofline": roofline, "clocks": clk, "e2e": e2e,
+            "error": error, "roofline": roofline, "fma_rates": alu, "clocks": clk, "e2e": e2e,
             "gpu_launches": 6 * args.steps}
+    if rank == 0 and world == 1 and not args.no_configs:
+        line["configs"] = sub_configs(leg)
+    h.close()
+    if leg is not None:
+        leg.finish()
+        full = line["error"]["oracle"]
+        line["error"]["oracle_bit_identical"] = all(v.get("bit_identical") for v in full.values())
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(rod, seconds=10.0, S=S, all_cores=True)
+        if leg is not None:
+            full = line["error"]["oracle"]
+            secs = {k: v.get("oracle_seconds") for k, v in full.items()}
+            line["cpu_baseline"]["full_workload"] = {
+                "updates_per_s": {k: (M * K / s if s else None) for k, s in secs.items()},
+                "seconds": secs,
+                "note": "the oracle's full K runs of this line's error check, one thread each, run in parallel "
+                        "worker processes"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -304,30 +304,53 @@ int heat1d_adjoint_batched(int64_t nrods, int64_t N, int64_t K, const double* r,
  * after start-up.  The handle API allocates state and scratch at
  * heat1d_create(), which such callers cannot do.
  *
- * Computes the same K steps as heat1d_run_sync() (same kernel, same result
- * bit for bit) from u_in to u_out: two distinct device buffers of N values of
+ * Computes the same K steps as heat1d_run_sync() with the handle's default
+ * options (same kernel, same halo depth and launch shape, same result bit for
+ * bit) from u_in to u_out: two distinct device buffers of N values of
  * `dtype`, owned by the caller.  u_out[0] and u_out[N-1] receive c1 and cN.
  * segments: S, in [1, 256], or 0 for one per SM (at most 256); each segment
- * must fit one CTA (about 16K points in F32 and 8K in F64).  The halo width is
- * min(32, N/S).  The run is enqueued on `stream` (a cudaStream_t, NULL for the
- * legacy default stream).  If status_out is not NULL it must be a device int;
- * it receives the run's device status (HEAT1D_OK or HEAT1D_ERR_TIMEOUT) when
- * the run completes on the stream.
+ * must fit one CTA (about 16K points in F32 and 8K in F64).  The halo depth is
+ * the handle's default (F32 128 steps; F64 64 on segments of 4096 points or
+ * more, else 32), at most N/S.  The run is enqueued on `stream` (a
+ * cudaStream_t, NULL for the legacy default stream).  If status_out is not
+ * NULL it must be a device int; it receives the run's device status
+ * (HEAT1D_OK or HEAT1D_ERR_TIMEOUT) when the run completes on the stream.
  *
  * The kernel's scratch (halo buffers, barrier counter, status word, segment
- * offsets; about 260 KB) lives in one fixed __device__ array inside the
+ * offsets; about 530 KB) lives in one fixed __device__ array inside the
  * library: every GPU that loads the library holds it until the process exits.
  * Calls reuse it: each call clears what must start at zero, so results never
  * depend on an earlier call, but two calls that overlap on the GPU (different
  * streams, or different host threads, without ordering between them) race on
- * that array and give wrong results.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture begins.  No call allocates device or
- * pinned memory.  Returns HEAT1D_ERR_INVAL (message in heat1d_last_error())
- * for sizes beyond these limits, HEAT1D_ERR_NOT_RESIDENT if the segments cannot
- * all be resident, HEAT1D_ERR_CUDA on a launch failure. */
+ * that array and give wrong results.  The call makes the current device's
+ * primary context current (cudaSetDevice) unless another context already is.
+ * The first call in each CUDA context looks up the array's device address
+ * there (cudaGetSymbolAddress) and caches it under the context's id; an
+ * address is only valid in its own context, so a device reset, which
+ * destroys the context, makes the next call look it up again.  Make that
+ * first call on each device before any stream capture begins.  No call
+ * allocates device or pinned memory.  Returns HEAT1D_ERR_INVAL (message in
+ * heat1d_last_error()) for sizes beyond these limits, HEAT1D_ERR_NOT_RESIDENT
+ * if the segments cannot all be resident, HEAT1D_ERR_CUDA when a CUDA call or
+ * the launch fails. */
 int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N, double r, double c1, double cN, int dtype,
                             int64_t K, int64_t segments, void* stream, int* status_out);
+
+/* ------------------------------------------------------------ roofline probe
+ *
+ * Throughput probe of the fused multiply-add pipe that bounds the on-chip runs
+ * (the paper has no counterpart: it measures the arithmetic roofline the FTCS
+ * kernels are held against, three FP64 fused multiply-adds per update in F64
+ * runs).  Enqueues one launch of `blocks` CTAs of `threads` threads (a
+ * multiple of 32, at most 1024) on `stream`; every thread advances 8 (F64) or
+ * 16 (F32) independent chains a <- fma(a, b, c) for `iters` iterations and
+ * writes one value to out (device, blocks * threads values of the dtype,
+ * owned by the caller).  *fma_per_launch (may be NULL) receives the number of
+ * fused multiply-adds the launch executes; the caller times the launch (CUDA
+ * events on the stream) and divides.  HEAT1D_ERR_INVAL for a bad shape or
+ * dtype, HEAT1D_ERR_CUDA if the launch fails. */
+int heat1d_probe_fma(int dtype, int64_t iters, int64_t blocks, int threads, void* out, void* stream,
+                     int64_t* fma_per_launch);
 
 #ifdef __cplusplus
 }

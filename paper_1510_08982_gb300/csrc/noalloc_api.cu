@@ -16,7 +16,9 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
+#include <cuda.h>  // CUcontext and the driver's function types only; nothing is linked from libcuda
 #include <cuda_runtime.h>
 
 #include "heat1d.h"
@@ -24,23 +26,35 @@
 
 namespace {
 
-// Limits of the shared scratch array.
+// Limits of the shared scratch array.  The halo buffers hold kNoallocHaloBytes
+// per segment side and parity: 128 FP32 or 64 FP64 points, the handle API's
+// default halo depths.
 constexpr int kNoallocMaxSegments = 256;
-constexpr int kNoallocMaxHalo = 32;
+constexpr int kNoallocHaloBytes = 512;
 // Layout (bytes): [0, 256) control words (barrier counter at 0, status at 128);
 // [256, 256 + 8*(S+1)) segment offsets; then the halo buffers [2][S][2T] values.
 constexpr size_t kCtlBytes = 256;
 constexpr size_t kOffBytes = 8 * (kNoallocMaxSegments + 1);
 constexpr size_t kEdgeOffset = (kCtlBytes + kOffBytes + 255) / 256 * 256;
-constexpr size_t kEdgeBytes = size_t(2) * kNoallocMaxSegments * 2 * kNoallocMaxHalo * sizeof(double);
+constexpr size_t kEdgeBytes = size_t(2) * kNoallocMaxSegments * 2 * kNoallocHaloBytes;
 constexpr size_t kScratchBytes = kEdgeOffset + kEdgeBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Per-device address of g_noalloc_scratch, looked up once per device.
-constexpr int kMaxDevices = 64;
+// The array's device address is valid in the CUDA context in which it was
+// looked up; it is cached per context, keyed by the context's unique id (ids
+// are never reused within a process, so a context destroyed by a device reset
+// and a later one at the same handle value are told apart).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  void* addr;
+};
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+std::vector<ScratchEntry> g_scratch;  // grows by one entry per context; reserved up front
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
 
 // Clears the control words and writes the segment offsets (the first N mod S
 // segments hold one point more), so that nothing depends on an earlier call.
@@ -66,21 +80,48 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
-// Looks up the scratch array's device address for the current device.
-int scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(HEAT1D_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fail(HEAT1D_ERR_INVAL, "device index out of range");
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(HEAT1D_ERR_CUDA, std::string("heat1d_run_sync_noalloc: ") + what + ": " + cudaGetErrorString(e));
+}
+
+// Looks up the scratch array's device address in the calling thread's current
+// context (the current device's primary context unless the caller made
+// another one current), once per context.
+int scratch_address(int dev, unsigned char** out) {
+  // Makes the device's primary context current on this thread and
+  // initialises it if needed (a no-op when the caller already uses it).
+  cudaError_t e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(HEAT1D_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || !f1)
+      return fail(HEAT1D_ERR_CUDA, "heat1d_run_sync_noalloc: driver entry point cuCtxGetCurrent not found");
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess || !f2)
+      return fail(HEAT1D_ERR_CUDA, "heat1d_run_sync_noalloc: driver entry point cuCtxGetId not found");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    g_scratch.reserve(64);
   }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_get_id(ctx, &id) != CUDA_SUCCESS)
+    return fail(HEAT1D_ERR_CUDA, "heat1d_run_sync_noalloc: no current CUDA context");
+  for (const ScratchEntry& s : g_scratch) {
+    if (s.ctx_id == id) {
+      *out = static_cast<unsigned char*>(s.addr);
+      return HEAT1D_OK;
+    }
+  }
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress");
+  g_scratch.push_back({id, p});
+  *out = static_cast<unsigned char*>(p);
   return HEAT1D_OK;
 }
 
@@ -99,28 +140,42 @@ extern "C" int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N,
     return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: segments must be in [0, 256] (the size of the "
                                   "library's fixed scratch array)");
 
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  if (nsm < 1) return fail(HEAT1D_ERR_CUDA, "heat1d_run_sync_noalloc: device reports no multiprocessors");
+
   unsigned char* scratch = nullptr;
-  int rc = scratch_address(&scratch);
+  int rc = scratch_address(dev, &scratch);
   if (rc) return rc;
 
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int64_t S = segments ? segments : std::min<int64_t>(nsm, kNoallocMaxSegments);
   S = std::min<int64_t>(S, N);
+  if (S < 1) return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: no segments");
   const int64_t Lmin = N / S, Lmax = N / S + (N % S ? 1 : 0);
-  const int T = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kNoallocMaxHalo, Lmin)));
-  const size_t esize = dtype == HEAT1D_F64 ? 8 : 4;
+  const int esize = dtype == HEAT1D_F64 ? 8 : 4;
+  // The handle API's default halo depth (FP32 128 steps; FP64 64 on segments
+  // of 4096 points or more, else 32), at most the shortest segment; the
+  // array holds exactly that depth.
+  const int Tdef = esize == 4 ? 128 : (Lmin >= 4096 ? 64 : 32);
+  const int T = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(Tdef, Lmin)));
+  static_assert(kNoallocHaloBytes >= 128 * 4 && kNoallocHaloBytes >= 64 * 8, "halo buffers too small");
 
-  // Launch shape: fewest points per thread that fit one CTA.
+  // Launch shape: the handle API's rule -- the fewest points per thread that
+  // fit one CTA, FP32 trying 16 points per thread first on tiles of at least
+  // 8 warps of 16 points.
   const int64_t slots = Lmax + 2 * T;
-  int E = 0, threads = 0;
+  const bool prefer16 = esize == 4 && slots >= 8 * 32 * 16;
   const int Es[4] = {2, 4, 8, 16};
+  const int Es16[4] = {16, 2, 4, 8};
+  int E = 0, threads = 0;
   for (int i = 0; i < 4 && !E; ++i) {
-    const int64_t t =
-        32 * heat1d_impl::window_warps(slots, Es[i], heat1d_impl::sync_window_halo(static_cast<int>(esize), Es[i]));
-    if (t <= heat1d_impl::max_tile_threads(static_cast<int>(esize), Es[i])) {
-      E = Es[i];
+    const int e = prefer16 ? Es16[i] : Es[i];
+    const int64_t t = 32 * heat1d_impl::window_warps(slots, e, heat1d_impl::sync_window_halo(esize, e));
+    if (t <= heat1d_impl::max_tile_threads(esize, e)) {
+      E = e;
       threads = static_cast<int>(t);
     }
   }
@@ -129,8 +184,8 @@ extern "C" int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N,
                                       " points per segment exceed one CTA; pass more segments (at most 256)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   noalloc_prepare_kernel<<<1, 256, 0, st>>>(scratch, N, static_cast<int>(S));
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(HEAT1D_ERR_CUDA, std::string("prepare: ") + cudaGetErrorString(e));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "prepare");
 
   {
     // K = 0 still launches: the kernel then only copies u(0), ends forced.
@@ -153,15 +208,12 @@ extern "C" int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N,
     rc = heat1d_impl::launch_sync_persistent(a, dtype, E, threads, st);
     if (rc == HEAT1D_ERR_NOT_RESIDENT)
       return fail(rc, "heat1d_run_sync_noalloc: " + std::to_string(S) + " CTAs cannot all be resident");
-    if (rc) {
-      e = cudaGetLastError();
-      return fail(HEAT1D_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
-    }
+    if (rc) return cuda_fail(cudaGetLastError(), "launch");
   }
   if (status_out) {
     noalloc_status_kernel<<<1, 32, 0, st>>>(scratch, status_out);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(HEAT1D_ERR_CUDA, std::string("status: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return cuda_fail(e, "status");
   }
   return HEAT1D_OK;
 }

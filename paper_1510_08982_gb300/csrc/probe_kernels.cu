@@ -1,0 +1,67 @@
+// probe_kernels.cu -- throughput probe of the fused multiply-add pipes.
+//
+// The on-chip FTCS kernels are bound by the FP64 pipe (FP64 runs: three DFMA
+// per update) or by the FP32 FMA pipe (FP32 runs).  Their roofline is the rate
+// at which one GB300 retires those instructions; this probe measures it: every
+// thread advances independent chains a <- fma(a, b, c), so nothing but the
+// pipe limits the rate.  The caller times one launch with CUDA events.
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "heat1d.h"
+#include "impl.h"
+
+namespace {
+
+template <typename real, int kChains>
+__global__ void fma_rate_kernel(int64_t iters, real b, real c, real* out) {
+  real a[kChains];
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) a[j] = static_cast<real>(threadIdx.x + j) * static_cast<real>(1e-3);
+#pragma unroll 4
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = fma(a[j], b, c);
+  }
+  real s = static_cast<real>(0);
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) s += a[j];
+  out[static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x] = s;
+}
+
+// Independent chains per thread: enough to cover the pipe's latency with a
+// few warps per scheduler.
+constexpr int kChains64 = 8;
+constexpr int kChains32 = 16;
+
+}  // namespace
+
+extern "C" int heat1d_probe_fma(int dtype, int64_t iters, int64_t blocks, int threads, void* out, void* stream,
+                                int64_t* fma_per_launch) {
+  if (dtype != HEAT1D_F32 && dtype != HEAT1D_F64) {
+    heat1d_impl::set_last_error("heat1d_probe_fma: dtype must be HEAT1D_F32 or HEAT1D_F64");
+    return HEAT1D_ERR_INVAL;
+  }
+  if (iters < 1 || blocks < 1 || blocks > (1 << 20) || threads < 32 || threads > 1024 || threads % 32 || !out) {
+    heat1d_impl::set_last_error("heat1d_probe_fma: bad launch shape or null output");
+    return HEAT1D_ERR_INVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // b < 1 and c small keep every chain finite (it converges to c / (1 - b)).
+  if (dtype == HEAT1D_F64) {
+    fma_rate_kernel<double, kChains64><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
+        iters, 0.999999, 1e-6, static_cast<double*>(out));
+  } else {
+    fma_rate_kernel<float, kChains32><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
+        iters, 0.999f, 1e-3f, static_cast<float*>(out));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    heat1d_impl::set_last_error(std::string("heat1d_probe_fma: ") + cudaGetErrorString(e));
+    return HEAT1D_ERR_CUDA;
+  }
+  if (fma_per_launch) *fma_per_launch = blocks * threads * iters * (dtype == HEAT1D_F64 ? kChains64 : kChains32);
+  return HEAT1D_OK;
+}

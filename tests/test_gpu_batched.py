@@ -4,8 +4,8 @@ Every rod of a batch must come out bit-identical to the oracle run on that rod
 alone.  Small batches cover all three kinds of work item (warp batches,
 single-CTA rods, multi-CTA parts) and degenerate rods; the uneven-rods
 workload (4096 rods, N log-uniform in [256, 65536], K log-uniform in
-[1e3, 1e5]) is checked on a seeded subset against the oracle and on its
-largest rods against the single-rod GPU path.
+[1e3, 1e5]) is checked against the oracle on a seeded subset and on its six
+heaviest rods.
 """
 from __future__ import annotations
 
@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from paper_1510_08982_gb300 import inputs
+from tests import oracle_pool
 
 pytestmark = pytest.mark.gpu
 
@@ -66,8 +67,8 @@ def test_batched_all_item_kinds(H, dtype):
 
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
 def test_batched_uneven_rods_workload(H, dtype):
-    """4096 uneven rods in one launch: a seeded subset of 64 cheap rods against
-    the oracle, the 6 largest against the single-rod GPU path."""
+    """4096 uneven rods in one launch: a seeded subset of 64 cheap rods and
+    the 6 heaviest rods against the oracle."""
     rods = inputs.uneven_rods(seed=0)
     specs, u, off = pack(H, rods, dtype)
     with H.Batch(specs, dtype=dtype) as b:
@@ -81,14 +82,15 @@ def test_batched_uneven_rods_workload(H, dtype):
     for j in pick:
         r = rods[j]
         assert np.array_equal(got[off[j]:off[j] + r.N], oracle_rod(r, dtype)), j
+    # the six heaviest rods (N up to 65536, K up to 1e5, split into parts
+    # over several CTAs) against the oracle, in parallel worker processes
     big = sorted(range(len(rods)), key=lambda j: rods[j].N * rods[j].K)[-6:]
-    for j in big:
+    odt = np.float32 if dtype == "float32" else np.float64
+    refs = oracle_pool.run([("sync", (rods[j].u0, rods[j].r, rods[j].c1, rods[j].cN, rods[j].K), {"dtype": odt})
+                            for j in big])
+    for j, ref in zip(big, refs):
         r = rods[j]
-        with H.Heat1d(r.N, r.r, r.c1, r.cN, dtype=dtype) as h:
-            h.set_u(r.u0)
-            h.run_sync(r.K)
-            h.sync()
-            ref = h.get_u(device=False)
+        assert r.N > 8192 and r.K > 20_000
         assert np.array_equal(got[off[j]:off[j] + r.N], ref), j
 
 
