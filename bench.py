@@ -412,16 +412,16 @@ def alu_peaks(torch, dev):
         return _ALU
     from paper_1510_08982_gb300 import heat1d
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    f64 = heat1d.probe_fma("float64", iters=60_000)
-    f32 = heat1d.probe_fma("float32", iters=400_000)
+    f64, shapes64 = heat1d.probe_fma("float64")
+    f32, shapes32 = heat1d.probe_fma("float32")
     nom64 = FP64_NOMINAL_TFLOPS * 1e12 / 2
     nom32 = nsm * 128 * 2.07e9
     _ALU = {"f64": {"fma_per_s": f64, "updates_per_s": f64 / 3, "nominal_fma_per_s": nom64,
-                    "nominal_updates_per_s": nom64 / 3},
+                    "nominal_updates_per_s": nom64 / 3, "shapes": shapes64},
             "f32": {"fma_per_s": f32, "updates_per_s": f32 / 3, "nominal_fma_per_s": nom32,
-                    "nominal_updates_per_s": nom32 / 3},
-            "source": "heat1d_probe_fma, best of 3 launches of %d CTAs x 256 threads on this GPU in this run "
-                      "(profiles/fma_probe_rates.md); 3 FMA-pipe instructions per update" % (4 * nsm)}
+                    "nominal_updates_per_s": nom32 / 3, "shapes": shapes32},
+            "source": "heat1d_probe_fma on this GPU in this run: best over 4 launch shapes of 3 timed launches "
+                      "each (profiles/fma_probe_rates.md); 3 FMA-pipe instructions per update"}
     return _ALU
 
 

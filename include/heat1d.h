@@ -342,14 +342,14 @@ int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N, double r, 
  * (the paper has no counterpart: it measures the arithmetic roofline the FTCS
  * kernels are held against, three FP64 fused multiply-adds per update in F64
  * runs).  Enqueues one launch of `blocks` CTAs of `threads` threads (a
- * multiple of 32, at most 1024) on `stream`; every thread advances 8 (F64) or
- * 16 (F32) independent chains a <- fma(a, b, c) for `iters` iterations and
- * writes one value to out (device, blocks * threads values of the dtype,
+ * multiple of 32, at most 1024) on `stream`; every thread advances `chains`
+ * (4, 8 or 16) independent chains a <- fma(a, b, c) for `iters` iterations
+ * and writes one value to out (device, blocks * threads values of the dtype,
  * owned by the caller).  *fma_per_launch (may be NULL) receives the number of
  * fused multiply-adds the launch executes; the caller times the launch (CUDA
- * events on the stream) and divides.  HEAT1D_ERR_INVAL for a bad shape or
- * dtype, HEAT1D_ERR_CUDA if the launch fails. */
-int heat1d_probe_fma(int dtype, int64_t iters, int64_t blocks, int threads, void* out, void* stream,
+ * events on the stream) and divides.  HEAT1D_ERR_INVAL for a bad shape, chain
+ * count or dtype, HEAT1D_ERR_CUDA if the launch fails. */
+int heat1d_probe_fma(int dtype, int chains, int64_t iters, int64_t blocks, int threads, void* out, void* stream,
                      int64_t* fma_per_launch);
 
 #ifdef __cplusplus

@@ -323,6 +323,8 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
     if (!per_step) {
       if (mode == kTileFree)
         warp_steps<real, E, kTileFree>(v, fixed, coef, n);
+      else if (mode == kTileEnds)
+        warp_steps<real, E, kTileEnds>(v, fixed, coef, n);
       else if (mode == kTileMasked)
         warp_steps<real, E, kTileMasked>(v, fixed, coef, n);
     } else {
@@ -355,6 +357,8 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
         }
         if (mode == kTileFree) {
           warp_step_to<real, E, kTileFree>(in, out, fixed, coef);
+        } else if (mode == kTileEnds) {
+          warp_step_to<real, E, kTileEnds>(in, out, fixed, coef);
         } else if (mode == kTileMasked) {
           warp_step_to<real, E, kTileMasked>(in, out, fixed, coef);
         } else {

@@ -60,12 +60,13 @@ __device__ void run_warp_rod(const BatchRod& rd, real* u, int lane) {
     if (p == 0) y = c1;
     if (p == N - 1) y = cN;
     v[e] = y;
-    if (p == 0 || p >= N - 1) fixed |= 1u << e;
+    // only the Dirichlet ends are held: positions past u_N never reach it
+    if (p == 0 || p == N - 1) fixed |= 1u << e;
   }
   const int mode = tile_mode<E>(fixed);
-  if (mode == kTileFree) {
-    warp_steps<real, E, kTileFree>(v, fixed, coef, rd.K);
-  } else if (mode == kTileMasked) {
+  if (mode == kTileEnds) {
+    warp_steps<real, E, kTileEnds>(v, fixed, coef, rd.K);
+  } else {
     warp_steps<real, E, kTileMasked>(v, fixed, coef, rd.K);
   }
 #pragma unroll
@@ -111,9 +112,10 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         if (p == 0) y = c1;
         if (p == N - 1) y = cN;
         v[e] = y;
-        if (p == 0 || p >= N - 1) fixed |= 1u << e;
+        if (p == 0 || p == N - 1) fixed |= 1u << e;  // the Dirichlet ends only
       }
-      const int mode = tile_mode<E>(fixed);
+      // warps wholly past u_N idle; the others step every position
+      const int mode = Win::pos(warp, 0, 0) >= N ? static_cast<int>(kTileIdle) : tile_mode<E>(fixed);
       for (int64_t k0 = 0; k0 < rd.K; k0 += (1 << 30)) {
         const int steps = static_cast<int>(std::min<int64_t>(rd.K - k0, 1 << 30));
         warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, steps);
@@ -124,12 +126,21 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         if (p < N && Win::owner(warp, lane, e, nwarps)) x[p] = v[e];
       }
     } else {
-      // One part: positions [0, L+2T) hold rod points a0 - T + p.
+      // One part: position p holds rod point a0 - lo + p, owned points
+      // [lo, hi), halos [lo - T, lo) and [hi, hi + T).  As in the synchronous
+      // kernel the first part starts at u_1 (lo = 0) and the last part ends at
+      // u_N in the CTA's last position, so that both Dirichlet ends sit in
+      // slots known at compile time.
       const BatchRod rd = a.rods[it.rod];
       real* x = u + rd.offset;
       const int64_t N = rd.N;
-      const int T = it.T, L = it.L, Lh = L + 2 * T;
+      const int T = it.T, L = it.L;
       const int64_t a0 = it.a0;
+      const bool first = it.part == 0, last = it.part + 1 == it.nparts;
+      const int P = nwarps * Win::D + 2 * Win::H;
+      const int lo = first ? 0 : (last ? P - L : T);
+      const int hi = lo + L;
+      const int tile_end = last ? hi : hi + T;
       const real c1 = static_cast<real>(rd.c1), cN = static_cast<real>(rd.cN);
       const Coef<real> coef{static_cast<real>(rd.r), static_cast<real>(rd.N > 0)};
       const size_t estride = static_cast<size_t>(4) * a.Tmax;
@@ -139,15 +150,15 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        const int64_t g = a0 - T + p;
+        const int64_t g = a0 - lo + p;
         real y = static_cast<real>(0);
-        if (p < Lh && g >= 0 && g < N) y = x[g];
+        if (p < tile_end && g >= 0 && g < N) y = x[g];
         if (g == 0) y = c1;
         if (g == N - 1) y = cN;
         v[e] = y;
-        if (p >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
+        if (p < tile_end && (g == 0 || g == N - 1)) fixed |= 1u << e;
       }
-      const int mode = tile_mode<E>(fixed);
+      const int mode = Win::pos(warp, 0, 0) >= tile_end ? static_cast<int>(kTileIdle) : tile_mode<E>(fixed);
       __syncthreads();
       if (tid == 0) st_release_gpu(myflag, 1);  // loaded: neighbours may now overwrite their own points
       bool ok = true;
@@ -161,8 +172,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         for (int e = 0; e < E; ++e) {
           const int p = Win::pos(warp, lane, e);
           if (!Win::owner(warp, lane, e, nwarps)) continue;
-          if (p >= T && p < 2 * T) st_cg(mine + (p - T), v[e]);
-          if (p >= L && p < L + T) st_cg(mine + a.Tmax + (p - L), v[e]);
+          if (p >= lo && p < lo + T) st_cg(mine + (p - lo), v[e]);
+          if (p >= hi - T && p < hi) st_cg(mine + a.Tmax + (p - (hi - T)), v[e]);
         }
         __syncthreads();
         if (tid == 0) {
@@ -184,7 +195,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int p = Win::pos(warp, lane, e);
-            if (p < T) v[e] = ld_cg(left + a.Tmax + p);
+            if (p >= lo - T && p < lo) v[e] = ld_cg(left + a.Tmax + (p - (lo - T)));
           }
         }
         if (it.part + 1 < it.nparts) {
@@ -192,7 +203,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int p = Win::pos(warp, lane, e);
-            if (p >= L + T && p < Lh) v[e] = ld_cg(right + (p - L - T));
+            if (p >= hi && p < hi + T) v[e] = ld_cg(right + (p - hi));
           }
         }
         ++epoch;
@@ -210,7 +221,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) x[a0 - T + p] = v[e];
+        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) x[a0 - lo + p] = v[e];
       }
     }
     __syncthreads();

@@ -66,15 +66,15 @@ __device__ int strip_version(const SegmentRun& a, const int* nb_prog, int j, siz
 // (one thread, after the CTA barrier) release-stores the version counter.
 template <typename real, int E, typename Win>
 __device__ __forceinline__ void publish_strips(const real (&v)[E], real* strips, int* my_prog, int s, int R, int T,
-                                               int L, int ver, bool stalled, int warp, int lane, int nwarps,
+                                               int lo, int hi, int ver, bool stalled, int warp, int lane, int nwarps,
                                                int tid) {
   real* mine = strips + (static_cast<size_t>(s) * R + (ver & (R - 1))) * 2 * T;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = Win::pos(warp, lane, e);
     if (!Win::owner(warp, lane, e, nwarps)) continue;
-    if (p >= T && p < 2 * T) st_cg(mine + (p - T), v[e]);
-    if (p >= L && p < L + T) st_cg(mine + T + (p - L), v[e]);
+    if (p >= lo && p < lo + T) st_cg(mine + (p - lo), v[e]);
+    if (p >= hi - T && p < hi) st_cg(mine + T + (p - (hi - T)), v[e]);
   }
   __syncthreads();
   // A release at GPU scope after the CTA barrier orders every thread's strip
@@ -93,7 +93,6 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
   const int64_t a0 = a.seg_off[s];
   const int L = static_cast<int>(a.seg_off[s + 1] - a0);
   const int T = a.T, R = a.R, S = a.S;
-  const int Lh = L + 2 * T;
   const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
   const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};  // one = 1 at run time
   const real* __restrict__ uin = static_cast<const real*>(a.u_in);
@@ -107,36 +106,43 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
   const int nbnd = periodic ? S : S - 1;                    // boundaries: S on the ring
   const int bl = periodic ? (s + S - 1) % S : s - 1;        // boundary read on the left (side 1)
 
-  // Position p of the CTA holds global point a0 - T + p (block 0: every
-  // strip is version 0, the initial state itself).
+  // Tile layout as in the synchronous kernel: position p holds global point
+  // a0 - lo + p, owned points [lo, hi), halos [lo - T, lo) and [hi, hi + T);
+  // the first segment starts at u_1 (lo = 0) and the last one ends at u_N in
+  // the CTA's last position, so that both Dirichlet ends sit in slots known
+  // at compile time (block 0: every strip is version 0, the initial state).
+  const bool first = !periodic && s == 0, last = !periodic && s == S - 1;
+  const int P = nwarps * Win::D + 2 * Win::H;
+  const int lo = first ? 0 : (last ? P - L : T);
+  const int hi = lo + L;
+  const int tile_end = last ? hi : hi + T;
   real v[E];
   unsigned fixed = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = Win::pos(warp, lane, e);
-    const int64_t g = a0 - T + p;
+    const int64_t g = a0 - lo + p;
     real x = static_cast<real>(0);
     if (periodic) {  // halos wrap around the ring
-      if (p < Lh) x = uin[((g % N) + N) % N];
-      if (p >= Lh) fixed |= 1u << e;
+      if (p < tile_end) x = uin[((g % N) + N) % N];
     } else {
-      if (p < Lh && g >= 0 && g < N) x = uin[g];
+      if (p < tile_end && g >= 0 && g < N) x = uin[g];
       if (g == 0) x = c1;
       if (g == N - 1) x = cN;
-      if (p >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
+      if (p < tile_end && (g == 0 || g == N - 1)) fixed |= 1u << e;
     }
     v[e] = x;
   }
-  const int mode = tile_mode<E>(fixed);
+  const int mode = Win::pos(warp, 0, 0) >= tile_end ? static_cast<int>(kTileIdle) : tile_mode<E>(fixed);
 
   if (a.snap) {  // row 0: the state at step 0
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
-      if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) static_cast<real*>(a.snap)[a0 + (p - T)] = v[e];
+      if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) static_cast<real*>(a.snap)[a0 + (p - lo)] = v[e];
     }
   }
-  publish_strips<real, E, Win>(v, strips, my_prog, s, R, T, L, 0, stalled, warp, lane, nwarps, tid);
+  publish_strips<real, E, Win>(v, strips, my_prog, s, R, T, lo, hi, 0, stalled, warp, lane, nwarps, tid);
   int parity = 0;
   int j = 0;
   for (int64_t k0 = 0; k0 < a.K; k0 += T, ++j) {
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int p = Win::pos(warp, lane, e);
-          if (p < T) v[e] = ld_cg(left + T + p);
+          if (p >= lo - T && p < lo) v[e] = ld_cg(left + T + (p - (lo - T)));
         }
       }
       if (sr >= 0) {
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int p = Win::pos(warp, lane, e);
-          if (p >= L + T && p < L + 2 * T) v[e] = ld_cg(right + (p - L - T));
+          if (p >= hi && p < hi + T) v[e] = ld_cg(right + (p - hi));
         }
       }
     }
@@ -187,18 +193,18 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) row[a0 + (p - T)] = v[e];
+        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) row[a0 + (p - lo)] = v[e];
       }
     }
     if (k0 + tb >= a.K) break;
     // The barrier inside also keeps sh_v stable until every thread has read it.
-    publish_strips<real, E, Win>(v, strips, my_prog, s, R, T, L, j + 1, stalled, warp, lane, nwarps, tid);
+    publish_strips<real, E, Win>(v, strips, my_prog, s, R, T, lo, hi, j + 1, stalled, warp, lane, nwarps, tid);
   }
 
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = Win::pos(warp, lane, e);
-    if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) uout[a0 + (p - T)] = v[e];
+    if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) uout[a0 + (p - lo)] = v[e];
   }
 }
 

@@ -176,15 +176,23 @@ struct WindowShared {
   real to_left[2][32][H];   // lane 0's positions [H, 2H): the previous warp's right halo
 };
 
-// How a warp steps: every point updated, some points fixed (select), or every
-// point fixed (padding warps: no arithmetic).
-enum TileMode { kTileFree = 0, kTileMasked = 1, kTileIdle = 2 };
+// How a warp steps: every point updated; the first and/or last slot of some
+// lanes held (a Dirichlet end placed at a slot known at compile time: two
+// selects per step); any other points held (a select per point); or every
+// point held (padding warps: no arithmetic).
+enum TileMode { kTileFree = 0, kTileMasked = 1, kTileIdle = 2, kTileEnds = 3 };
 
+// Kernels hold only the Dirichlet ends: positions outside the rod or past the
+// tile are stepped like any other (their values are never stored and reach no
+// stored point before they are overwritten or the tile ends), so that no warp
+// pays per-point selects for padding.
 template <int E>
 __device__ __forceinline__ int tile_mode(unsigned fixed) {
   const unsigned all = (E >= 32) ? 0xffffffffu : ((1u << E) - 1u);
   if (__all_sync(kFullMask, fixed == all)) return kTileIdle;
-  return __any_sync(kFullMask, fixed != 0u) ? kTileMasked : kTileFree;
+  if (!__any_sync(kFullMask, fixed != 0u)) return kTileFree;
+  const unsigned ends = 1u | (1u << (E - 1));
+  return __any_sync(kFullMask, (fixed & ~ends) != 0u) ? kTileMasked : kTileEnds;
 }
 
 // One step of one warp (no other warp involved).
@@ -199,7 +207,7 @@ __device__ __forceinline__ void warp_step(real (&v)[E], unsigned fixed, Coef<rea
     const real cur = v[e];
     const real nxt = (e + 1 < E) ? v[e + 1] : right;
     const real nv = ftcs(c.r, c.one, prev, cur, nxt);
-    if (kMode == kTileMasked) {
+    if (kMode == kTileMasked || (kMode == kTileEnds && (e == 0 || e == E - 1))) {
       v[e] = ((fixed >> e) & 1u) ? cur : nv;
     } else {
       v[e] = nv;
@@ -218,7 +226,7 @@ __device__ __forceinline__ void warp_step_to(const real (&in)[E], real (&out)[E]
     const real prev = e > 0 ? in[e - 1] : left;
     const real nxt = (e + 1 < E) ? in[e + 1] : right;
     const real nv = ftcs(c.r, c.one, prev, in[e], nxt);
-    if (kMode == kTileMasked) {
+    if (kMode == kTileMasked || (kMode == kTileEnds && (e == 0 || e == E - 1))) {
       out[e] = ((fixed >> e) & 1u) ? in[e] : nv;
     } else {
       out[e] = nv;
@@ -247,6 +255,8 @@ template <typename real, int E>
 __device__ __forceinline__ void warp_step_any(int mode, real (&v)[E], unsigned fixed, Coef<real> c) {
   if (mode == kTileFree)
     warp_step<real, E, kTileFree>(v, fixed, c);
+  else if (mode == kTileEnds)
+    warp_step<real, E, kTileEnds>(v, fixed, c);
   else if (mode == kTileMasked)
     warp_step<real, E, kTileMasked>(v, fixed, c);
   else
@@ -294,6 +304,8 @@ __device__ __forceinline__ void warp_advance(int mode, real (&v)[E], unsigned fi
     const int n = min(H, steps - done);
     if (mode == kTileFree) {
       warp_steps<real, E, kTileFree>(v, fixed, c, n);
+    } else if (mode == kTileEnds) {
+      warp_steps<real, E, kTileEnds>(v, fixed, c, n);
     } else if (mode == kTileMasked) {
       warp_steps<real, E, kTileMasked>(v, fixed, c, n);
     }

@@ -31,17 +31,16 @@ __global__ void fma_rate_kernel(int64_t iters, real b, real c, real* out) {
   out[static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x] = s;
 }
 
-// Independent chains per thread: enough to cover the pipe's latency with a
-// few warps per scheduler.
-constexpr int kChains64 = 8;
-constexpr int kChains32 = 16;
-
 }  // namespace
 
-extern "C" int heat1d_probe_fma(int dtype, int64_t iters, int64_t blocks, int threads, void* out, void* stream,
-                                int64_t* fma_per_launch) {
+extern "C" int heat1d_probe_fma(int dtype, int chains, int64_t iters, int64_t blocks, int threads, void* out,
+                                void* stream, int64_t* fma_per_launch) {
   if (dtype != HEAT1D_F32 && dtype != HEAT1D_F64) {
     heat1d_impl::set_last_error("heat1d_probe_fma: dtype must be HEAT1D_F32 or HEAT1D_F64");
+    return HEAT1D_ERR_INVAL;
+  }
+  if (chains != 4 && chains != 8 && chains != 16) {
+    heat1d_impl::set_last_error("heat1d_probe_fma: chains must be 4, 8 or 16");
     return HEAT1D_ERR_INVAL;
   }
   if (iters < 1 || blocks < 1 || blocks > (1 << 20) || threads < 32 || threads > 1024 || threads % 32 || !out) {
@@ -49,19 +48,24 @@ extern "C" int heat1d_probe_fma(int dtype, int64_t iters, int64_t blocks, int th
     return HEAT1D_ERR_INVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const dim3 grid(static_cast<unsigned>(blocks)), block(threads);
   // b < 1 and c small keep every chain finite (it converges to c / (1 - b)).
   if (dtype == HEAT1D_F64) {
-    fma_rate_kernel<double, kChains64><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
-        iters, 0.999999, 1e-6, static_cast<double*>(out));
+    double* o = static_cast<double*>(out);
+    if (chains == 4) fma_rate_kernel<double, 4><<<grid, block, 0, st>>>(iters, 0.999999, 1e-6, o);
+    if (chains == 8) fma_rate_kernel<double, 8><<<grid, block, 0, st>>>(iters, 0.999999, 1e-6, o);
+    if (chains == 16) fma_rate_kernel<double, 16><<<grid, block, 0, st>>>(iters, 0.999999, 1e-6, o);
   } else {
-    fma_rate_kernel<float, kChains32><<<static_cast<unsigned>(blocks), threads, 0, st>>>(
-        iters, 0.999f, 1e-3f, static_cast<float*>(out));
+    float* o = static_cast<float*>(out);
+    if (chains == 4) fma_rate_kernel<float, 4><<<grid, block, 0, st>>>(iters, 0.999f, 1e-3f, o);
+    if (chains == 8) fma_rate_kernel<float, 8><<<grid, block, 0, st>>>(iters, 0.999f, 1e-3f, o);
+    if (chains == 16) fma_rate_kernel<float, 16><<<grid, block, 0, st>>>(iters, 0.999f, 1e-3f, o);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     heat1d_impl::set_last_error(std::string("heat1d_probe_fma: ") + cudaGetErrorString(e));
     return HEAT1D_ERR_CUDA;
   }
-  if (fma_per_launch) *fma_per_launch = blocks * threads * iters * (dtype == HEAT1D_F64 ? kChains64 : kChains32);
+  if (fma_per_launch) *fma_per_launch = blocks * threads * iters * chains;
   return HEAT1D_OK;
 }

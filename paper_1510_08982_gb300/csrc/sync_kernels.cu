@@ -57,41 +57,53 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
   const int64_t a0 = a.seg_off[s];
   const int L = static_cast<int>(a.seg_off[s + 1] - a0);
   const int T = a.T;
-  const int Lh = L + 2 * T;
   const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
   const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};  // one = 1 at run time
   const real* __restrict__ uin = static_cast<const real*>(a.u_in);
   real* __restrict__ uout = static_cast<real*>(a.u_out);
   real* edges = static_cast<real*>(a.edges);
+  const bool first = !a.periodic && s == 0;        // holds the Dirichlet end u_1
+  const bool last = !a.periodic && s == a.S - 1;   // holds the Dirichlet end u_N
 
-  // Position p of the CTA holds global point a0 - T + p.
+  // Tile layout: position p holds global point a0 - lo + p; the owned points
+  // are [lo, hi), the left halo [lo - T, lo), the right halo [hi, hi + T).
+  // Interior segments: lo = T.  The first segment has no left halo (lo = 0),
+  // so that u_1 sits in slot 0 of lane 0 of warp 0; the last segment ends at
+  // the last position the CTA covers, so that u_N sits in slot E-1 of lane 31
+  // of the last warp (its positions left of the halo are stepped but never
+  // read by an owned point within a block).  Both ends are then held by two
+  // selects per step in those two warps instead of a select per point.  With
+  // a single segment u_N falls wherever the rod ends.
+  const int P = nwarps * Win::D + 2 * Win::H;  // positions the CTA covers
+  const int lo = first ? 0 : (last ? P - L : T);
+  const int hi = lo + L;
+  const int tile_end = last ? hi : hi + T;     // positions past it are padding
   real v[E];
   unsigned fixed = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = Win::pos(warp, lane, e);
-    const int64_t g = a0 - T + p;
+    const int64_t g = a0 - lo + p;
     real x = static_cast<real>(0);
     if (a.periodic) {  // halos wrap around the ring
-      if (p < Lh) x = uin[((g % N) + N) % N];
-      if (p >= Lh) fixed |= 1u << e;
+      if (p < tile_end) x = uin[((g % N) + N) % N];
     } else {
-      if (p < Lh && g >= 0 && g < N) x = uin[g];
+      if (p < tile_end && g >= 0 && g < N) x = uin[g];
       if (g == 0) x = c1;
       if (g == N - 1) x = cN;
-      if (p >= Lh || g <= 0 || g >= N - 1) fixed |= 1u << e;
+      if (p < tile_end && (g == 0 || g == N - 1)) fixed |= 1u << e;
     }
     v[e] = x;
   }
   const int sl = s > 0 ? s - 1 : (a.periodic ? a.S - 1 : -1);      // left neighbour segment
   const int sr = s + 1 < a.S ? s + 1 : (a.periodic ? 0 : -1);       // right neighbour segment
-  const int mode = tile_mode<E>(fixed);
+  const int mode = Win::pos(warp, 0, 0) >= tile_end ? static_cast<int>(kTileIdle) : tile_mode<E>(fixed);
 
   if (a.snap) {  // row 0: the state at step 0
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
-      if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) static_cast<real*>(a.snap)[a0 + (p - T)] = v[e];
+      if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) static_cast<real*>(a.snap)[a0 + (p - lo)] = v[e];
     }
   }
   int parity = 0;
@@ -104,7 +116,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) row[a0 + (p - T)] = v[e];
+        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) row[a0 + (p - lo)] = v[e];
       }
     }
     if (k0 + tb >= a.K) break;
@@ -115,8 +127,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
       if (!Win::owner(warp, lane, e, nwarps)) continue;
-      if (p >= T && p < 2 * T) st_cg(mine + (p - T), v[e]);
-      if (p >= L && p < L + T) st_cg(mine + T + (p - L), v[e]);
+      if (p >= lo && p < lo + T) st_cg(mine + (p - lo), v[e]);
+      if (p >= hi - T && p < hi) st_cg(mine + T + (p - (hi - T)), v[e]);
     }
     __syncthreads();
     if (tid == 0) {
@@ -132,7 +144,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p < T) v[e] = ld_cg(left + T + p);
+        if (p >= lo - T && p < lo) v[e] = ld_cg(left + T + (p - (lo - T)));
       }
     }
     if (sr >= 0) {
@@ -140,7 +152,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= L + T && p < L + 2 * T) v[e] = ld_cg(right + (p - L - T));
+        if (p >= hi && p < hi + T) v[e] = ld_cg(right + (p - hi));
       }
     }
     ++epoch;
@@ -149,7 +161,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = Win::pos(warp, lane, e);
-    if (p >= T && p < T + L && Win::owner(warp, lane, e, nwarps)) uout[a0 + (p - T)] = v[e];
+    if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) uout[a0 + (p - lo)] = v[e];
   }
 }
 

@@ -87,7 +87,7 @@ def load():
         "heat1d_replay_blocked": (i32, [vp, i64, vp, i32]),
         "heat1d_blocked_trace_bytes": (i64, [vp, i64]),
         "heat1d_run_sync_noalloc": (i32, [vp, vp, i64, dbl, dbl, dbl, i32, i64, i64, vp, vp]),
-        "heat1d_probe_fma": (i32, [i32, i64, i64, i32, vp, vp, ctypes.POINTER(i64)]),
+        "heat1d_probe_fma": (i32, [i32, i32, i64, i64, i32, vp, vp, ctypes.POINTER(i64)]),
         "heat1d_batch_create": (vp, [ctypes.POINTER(RodSpec), i64, i32, ctypes.POINTER(Opts)]),
         "heat1d_batch_run": (i32, [vp, vp, vp]),
         "heat1d_batch_sync": (i32, [vp]),
@@ -364,30 +364,41 @@ def run_sync_noalloc(u_in, u_out, r, c1, cN, K, segments=0, status_out=None):
                                        int(K), int(segments), st, sp))
 
 
-def probe_fma(dtype="float64", iters=200_000, blocks_per_sm=4, threads=256, repeats=3):
+def probe_fma(dtype="float64", iters=None, shapes=None, repeats=3):
     """heat1d_probe_fma: the fused multiply-add rate of the device (FMA per
-    second, best of `repeats` launches timed with CUDA events on the current
-    stream)."""
+    second).  Each launch shape (chains per thread, CTAs per SM, threads per
+    CTA) is launched once untimed and `repeats` times timed with CUDA events
+    on the current stream; returns (best rate, {shape: best rate})."""
     torch = _torch()
     lib = load()
     dev = torch.cuda.current_device()
-    blocks = torch.cuda.get_device_properties(dev).multi_processor_count * blocks_per_sm
-    tdt = torch.float64 if dtype in ("float64", torch.float64) else torch.float32
-    out = torch.empty(blocks * threads, dtype=tdt, device="cuda")
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f64 = dtype in ("float64", torch.float64)
+    tdt = torch.float64 if f64 else torch.float32
+    if shapes is None:
+        shapes = [(8, 4, 256), (16, 2, 512), (4, 8, 256), (16, 1, 1024)]
+    if iters is None:
+        iters = 40_000 if f64 else 400_000
     st = torch.cuda.current_stream()
     n = ctypes.c_int64(0)
-    best = 0.0
-    for i in range(repeats + 1):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        _check(lib.heat1d_probe_fma(_dtype_code(tdt), int(iters), blocks, threads, ctypes.c_void_p(out.data_ptr()),
-                                    ctypes.c_void_p(st.cuda_stream), ctypes.byref(n)))
-        e1.record(st)
-        e1.synchronize()
-        if i > 0:  # the first launch is a warm-up
-            best = max(best, n.value / (e0.elapsed_time(e1) * 1e-3))
-    return best
+    rates = {}
+    for chains, per_sm, threads in shapes:
+        blocks = nsm * per_sm
+        out = torch.empty(blocks * threads, dtype=tdt, device="cuda")
+        best = 0.0
+        for i in range(repeats + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _check(lib.heat1d_probe_fma(_dtype_code(tdt), chains, int(iters * 8 // chains), blocks, threads,
+                                        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream),
+                                        ctypes.byref(n)))
+            e1.record(st)
+            e1.synchronize()
+            if i > 0:  # the first launch is a warm-up
+                best = max(best, n.value / (e0.elapsed_time(e1) * 1e-3))
+        rates["chains=%d ctas_per_sm=%d threads=%d" % (chains, per_sm, threads)] = best
+    return max(rates.values()), rates
 
 
 # ---------------------------------------------------------------------------- batched rods

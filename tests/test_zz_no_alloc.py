@@ -110,7 +110,7 @@ def test_noalloc_one_segment_per_sm_zero_steps_and_no_status(lib):
     check(c(rod.K, 0, with_status=False), oracle_result(rod, rod.K, "float64"))
     # K = 0: u(0) with the ends forced
     check(c(0, 0), oracle_result(rod, 0, "float64"))
-    check(c(0, 5, with_status=False), oracle_result(rod, 0, "float64"))
+    check(c(0, 100, with_status=False), oracle_result(rod, 0, "float64"))
     assert min(nsm, 256) <= rod.N
 
 
