@@ -187,6 +187,16 @@ int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_devi
  * Periodic runs (boundary = 1) need S >= 2; with S = 2 both halos come from
  * the one neighbour, each strip its own copy. */
 
+/* Rods too long for on-chip segments (sync_mode 2, or sync_mode 0 when a
+ * segment does not fit one CTA) run the same model streamed through HBM: the
+ * tiles of the streamed synchronous run are the segments (tile j holds points
+ * [jW, min((j+1)W, N)); only the last tile may be shorter than T), each block
+ * of T = the streamed halo depth steps reads a tile's own points from the
+ * state, advances them in registers and writes them back in place, and the
+ * tiles' edge strips travel through version rings in HBM.  Such runs need
+ * Dirichlet ends (boundary 0).  heat1d_blocked_segments() gives the split
+ * and the block length a trace refers to. */
+
 /* Free-running blocked run of K steps: each segment publishes its two edge
  * strips once per block and starts the next block with its neighbours'
  * newest strips not newer than that block, waiting only while one is more
@@ -199,8 +209,16 @@ int heat1d_run_async_blocked(heat1d_t h, int64_t K, uint8_t* trace_out, int trac
 int heat1d_replay_blocked(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device);
 
 /* Size in bytes of a blocked trace of K steps: ceil(K/T) * (S-1) * 2
- * (ceil(K/T) * S * 2 on the periodic ring). */
+ * (ceil(K/T) * S * 2 on the periodic ring), S and T as heat1d_blocked_segments
+ * reports them. */
 int64_t heat1d_blocked_trace_bytes(heat1d_t h, int64_t K);
+
+/* The segments of the blocked asynchronous run: returns their number S (the
+ * handle's segments on chip, the tiles when streamed) and, if offsets is not
+ * NULL, writes the S+1 offsets (host array, segment s = [offsets[s],
+ * offsets[s+1])); *block_steps (may be NULL) receives T, the steps per block.
+ * Negative on a NULL handle. */
+int64_t heat1d_blocked_segments(heat1d_t h, int64_t* offsets, int32_t* block_steps);
 
 /* Waits for the handle's stream and returns the device-side status of the
  * runs enqueued since the previous heat1d_sync(): HEAT1D_OK,

@@ -24,6 +24,9 @@ non-zero status from C):
 * ``async_blocked(u0, r, c1, cN, S, q, T, K, trace, dtype)`` -- the bounded-delay
   model applied to blocks of T steps: segments exchange T-wide edge strips once
   per block, each strip up to q-1 blocks old (trace uint8[ceil(K/T)][S-1][2]).
+* ``async_blocked_split(u0, r, c1, cN, offsets, q, T, K, trace, dtype)`` -- the same
+  model on a given split of the rod into segments (S+1 offsets; every segment but
+  the first and the last holds at least T points).
 * ``async_blocked_periodic(u0, r, S, q, T, K, trace, dtype)`` -- the same model on
   the periodic ring of Section 5.3 (trace uint8[ceil(K/T)][S][2]).
 * ``segments(N, S)`` -- the contiguous split of the N points into S segments.
@@ -81,12 +84,15 @@ def _load():
         lib.oracle_async_periodic_f32.argtypes = [i64, flt, i64, i32, vp, i64, vp, vp]
         lib.oracle_async_blocked_f64.argtypes = [i64, dbl, dbl, dbl, i64, i32, i64, vp, i64, vp, vp]
         lib.oracle_async_blocked_f32.argtypes = [i64, flt, flt, flt, i64, i32, i64, vp, i64, vp, vp]
+        lib.oracle_async_blocked_split_f64.argtypes = [i64, dbl, dbl, dbl, i64, vp, i32, i64, vp, i64, vp, vp]
+        lib.oracle_async_blocked_split_f32.argtypes = [i64, flt, flt, flt, i64, vp, i32, i64, vp, i64, vp, vp]
         lib.oracle_async_blocked_periodic_f64.argtypes = [i64, dbl, i64, i32, i64, vp, i64, vp, vp]
         lib.oracle_async_blocked_periodic_f32.argtypes = [i64, flt, i64, i32, i64, vp, i64, vp, vp]
         for f in (lib.oracle_segments, lib.oracle_sync_f64, lib.oracle_sync_f32, lib.oracle_async_f64,
                   lib.oracle_async_f32, lib.oracle_adjoint_f64, lib.oracle_sync_periodic_f64,
                   lib.oracle_sync_periodic_f32, lib.oracle_async_periodic_f64, lib.oracle_async_periodic_f32,
                   lib.oracle_async_blocked_f64, lib.oracle_async_blocked_f32,
+                  lib.oracle_async_blocked_split_f64, lib.oracle_async_blocked_split_f32,
                   lib.oracle_async_blocked_periodic_f64, lib.oracle_async_blocked_periodic_f32):
             f.restype = ctypes.c_int
         _lib = lib
@@ -208,6 +214,28 @@ def async_blocked(u0, r, c1, cN, S, q, T, K, trace, dtype=np.float64) -> np.ndar
     fn = lib.oracle_async_blocked_f64 if dt == np.float64 else lib.oracle_async_blocked_f32
     _check(fn(u0.size, float(r), float(c1), float(cN), int(S), int(q), int(T), _ptr(u0), int(K), _ptr(tr), _ptr(out)),
            "oracle_async_blocked")
+    return out
+
+
+def async_blocked_split(u0, r, c1, cN, offsets, q, T, K, trace, dtype=np.float64) -> np.ndarray:
+    """u(K) of the blocked asynchronous model on the segments given by
+    ``offsets`` (S+1 int64 values from 0 to N); trace uint8, shape
+    (ceil(K/T), S-1, 2) or flat."""
+    dt = _np_dtype(dtype)
+    u0 = np.ascontiguousarray(u0, dtype=dt)
+    out = np.empty_like(u0)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    S = off.size - 1
+    nb = (int(K) + int(T) - 1) // int(T)
+    tr = None
+    if trace is not None:
+        tr = np.ascontiguousarray(trace, dtype=np.uint8).reshape(-1)
+        if tr.size != nb * (S - 1) * 2:
+            raise ValueError("trace has %d entries, expected ceil(K/T)*(S-1)*2 = %d" % (tr.size, nb * (S - 1) * 2))
+    lib = _load()
+    fn = lib.oracle_async_blocked_split_f64 if dt == np.float64 else lib.oracle_async_blocked_split_f32
+    _check(fn(u0.size, float(r), float(c1), float(cN), S, _ptr(off), int(q), int(T), _ptr(u0), int(K), _ptr(tr),
+              _ptr(out)), "oracle_async_blocked_split")
     return out
 
 

@@ -168,28 +168,35 @@ int SUF(oracle_async_periodic)(int64_t N, REAL r, int64_t S, int q, const REAL* 
  *    outermost points and the Dirichlet ends are held), and its own points
  *    after the last sweep are its part of W_{b+1}.  Own points lie at least
  *    T >= tb points inside the tile, so no held tile edge reaches them.
- *  - A halo must lie within the adjacent segment: T may not exceed the
- *    shortest segment when S > 1.
+ *  - A halo must lie within the adjacent segment: every segment other than
+ *    the first and the last holds at least T points (the first and the last
+ *    may be shorter: a halo reaching past a rod end is clipped there).
+ *  - The segments are given by S+1 offsets, off[0] = 0 < off[1] < ... <
+ *    off[S] = N (oracle_async_blocked_split), or are the standard split of
+ *    oracle_segments (oracle_async_blocked, which also asks every segment to
+ *    hold at least T points).
  *
  * With every delay 0 this is the synchronous run; with T = 1 it is
  * Eq. (eqn:async) with the same trace.  The last q+1 block states are kept
  * (block b reads W_{b-q+1} .. W_b and writes W_{b+1} into the slot of
  * W_{b-q}).  trace holds ceil(K/T)*(S-1)*2 entries. */
-int SUF(oracle_async_blocked)(int64_t N, REAL r, REAL c1, REAL cN, int64_t S, int q, int64_t T,
-                              const REAL* u0, int64_t K, const uint8_t* trace, REAL* out) {
-  if (N < 3 || K < 0 || S < 1 || S > N || q < 1 || q > 255 || T < 1 || !u0 || !out) return ORACLE_EINVAL;
+int SUF(oracle_async_blocked_split)(int64_t N, REAL r, REAL c1, REAL cN, int64_t S, const int64_t* off, int q,
+                                    int64_t T, const REAL* u0, int64_t K, const uint8_t* trace, REAL* out) {
+  if (N < 3 || K < 0 || S < 1 || S > N || q < 1 || q > 255 || T < 1 || !off || !u0 || !out) return ORACLE_EINVAL;
+  if (off[0] != 0 || off[S] != N) return ORACLE_EINVAL;
+  for (int64_t s = 0; s < S; ++s) {
+    if (off[s + 1] <= off[s]) return ORACLE_EINVAL;
+    if (s > 0 && s + 1 < S && off[s + 1] - off[s] < T) return ORACLE_EINVAL;
+  }
   int64_t nb = (K + T - 1) / T;
-  if (S > 1 && T > N / S) return ORACLE_EINVAL; /* N / S is the shortest segment */
   if (S > 1 && nb > 0 && !trace) return ORACLE_EINVAL;
   for (int64_t j = 0; S > 1 && j < nb * (S - 1) * 2; ++j)
     if (trace[j] >= q) return ORACLE_ETRACE;
   int64_t Q = (int64_t)q + 1;
-  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S + 1));
   REAL* W = (REAL*)malloc(sizeof(REAL) * (size_t)N * (size_t)Q);
   REAL* ta = (REAL*)malloc(sizeof(REAL) * (size_t)N);
   REAL* tb_ = (REAL*)malloc(sizeof(REAL) * (size_t)N);
-  if (!off || !W || !ta || !tb_) { free(off); free(W); free(ta); free(tb_); return ORACLE_ENOMEM; }
-  oracle_segments(N, S, off);
+  if (!W || !ta || !tb_) { free(W); free(ta); free(tb_); return ORACLE_ENOMEM; }
 #define WB(b, i) W[(size_t)((b) % Q) * (size_t)N + (size_t)(i)]
   for (int64_t i = 0; i < N; ++i) WB(0, i) = u0[i];
   WB(0, 0) = c1;
@@ -227,11 +234,22 @@ int SUF(oracle_async_blocked)(int64_t N, REAL r, REAL c1, REAL cN, int64_t S, in
   }
   for (int64_t i = 0; i < N; ++i) out[i] = WB(nb, i);
 #undef WB
-  free(off);
   free(W);
   free(ta);
   free(tb_);
   return ORACLE_OK;
+}
+
+int SUF(oracle_async_blocked)(int64_t N, REAL r, REAL c1, REAL cN, int64_t S, int q, int64_t T,
+                              const REAL* u0, int64_t K, const uint8_t* trace, REAL* out) {
+  if (N < 3 || S < 1 || S > N || T < 1) return ORACLE_EINVAL;
+  if (S > 1 && T > N / S) return ORACLE_EINVAL; /* N / S is the shortest segment */
+  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S + 1));
+  if (!off) return ORACLE_ENOMEM;
+  oracle_segments(N, S, off);
+  int rc = SUF(oracle_async_blocked_split)(N, r, c1, cN, S, off, q, T, u0, K, trace, out);
+  free(off);
+  return rc;
 }
 
 /* The blocked asynchronous model on the periodic ring (Section 5.3): as

@@ -230,7 +230,8 @@ int run_streamed(heat1d* h, int64_t K) {
 // whose warp count (overlapping warp windows of 32E points, see common.cuh)
 // fits the kernel's CTA limit minus `reserved` threads (the asynchronous
 // kernel's communication warp), unless E or the thread count is forced.
-int pick_shape(const heat1d* h, int64_t slots, int reserved, bool async_kernel, int* E, int* threads) {
+// Returns false (setting nothing) when no shape fits.
+bool try_shape(const heat1d* h, int64_t slots, int reserved, bool async_kernel, int* E, int* threads) {
   const int forced_E = h->opts.elems_per_thread;
   // FP32 tries 16 points per thread first when the tile still spreads over
   // at least 8 warps: per update it then issues half the shuffles and halo
@@ -253,12 +254,27 @@ int pick_shape(const heat1d* h, int64_t slots, int reserved, bool async_kernel, 
     if (t <= limit) {
       *E = e;
       *threads = static_cast<int>(t);
-      return HEAT1D_OK;
+      return true;
     }
   }
+  return false;
+}
+
+int pick_shape(const heat1d* h, int64_t slots, int reserved, bool async_kernel, int* E, int* threads) {
+  if (try_shape(h, slots, reserved, async_kernel, E, threads)) return HEAT1D_OK;
   return fail(HEAT1D_ERR_INVAL,
               "segments too long for the on-chip kernels (" + std::to_string(slots) +
                   " points per CTA); use more segments");
+}
+
+// Whether the blocked asynchronous run streams through HBM (tiles as
+// segments): asked for with sync_mode 2, or chosen when a segment does not
+// fit one CTA (sync_mode 0) on a rod with Dirichlet ends.
+bool blocked_streamed(const heat1d* h) {
+  if (h->opts.sync_mode == 2) return true;
+  if (h->opts.sync_mode == 1 || h->opts.boundary == 1) return false;
+  int E = 0, threads = 0;
+  return !try_shape(h, h->Lmax + 2 * h->T, 0, false, &E, &threads);
 }
 
 SegmentRun base_run(heat1d* h, int64_t K) {
@@ -360,11 +376,71 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   return HEAT1D_OK;
 }
 
+// The blocked asynchronous run streamed through HBM: the tiles of the
+// streamed synchronous run (W points each, the last one shorter) are the
+// segments, Ts steps per block.
+int run_blocked_streamed(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device, const uint8_t* trace_in,
+                         int in_on_device) {
+  if (h->opts.boundary == 1) return fail(HEAT1D_ERR_INVAL, "streamed runs have Dirichlet ends only");
+  if (h->ntiles <= 0 || (h->sE != 4 && h->sE != 8 && h->sE != 16) ||
+      h->sthreads > heat1d_impl::kStreamMaxThreads)
+    return fail(HEAT1D_ERR_INVAL,
+                "streamed run: invalid tile shape (elems_per_thread must be 4, 8 or 16; block_threads at most 512)");
+  if (h->snap) return fail(HEAT1D_ERR_INVAL, "snapshots are recorded by on-chip runs only");
+  const int64_t nb = (K + h->Ts - 1) / h->Ts;
+  if (nb >= INT_MAX) return fail(HEAT1D_ERR_INVAL, "K out of range");
+  const size_t sbytes = h->esize * static_cast<size_t>(h->ntiles) * h->R * 2 * h->Th;
+  if (sbytes > h->strips_bytes) {
+    cudaFree(h->strips);
+    h->strips = nullptr;
+    h->strips_bytes = 0;
+    HEAT1D_CUDA(cudaMalloc(&h->strips, sbytes));
+    h->strips_bytes = sbytes;
+  }
+  const size_t tbytes = static_cast<size_t>(nb) * (h->ntiles - 1) * 2;
+  uint8_t* out_dev = nullptr;
+  const uint8_t* in_dev = nullptr;
+  int rc;
+  if ((rc = stage_traces(h, tbytes, trace_out, out_on_device, trace_in, in_on_device, &out_dev, &in_dev))) return rc;
+  heat1d_impl::StreamAsyncRun a{};
+  a.N = h->N;
+  a.K = K;
+  a.T = h->Ts;
+  a.Th = h->Th;
+  a.W = h->W;
+  a.ntiles = h->ntiles;
+  a.u = h->u[h->cur];  // updated in place
+  a.r = h->r;
+  a.c1 = h->c1;
+  a.cN = h->cN;
+  a.q = h->q;
+  a.R = h->R;
+  a.strips = h->strips;
+  a.ver = h->done;
+  a.trace_out = out_dev;
+  a.trace_in = in_dev;
+  a.status = h->status();
+  a.spin_limit_ns = h->opts.spin_limit_ns;
+  a.stall_tile = h->opts.stall_segment;
+  const int resident = heat1d_impl::max_resident_stream_async(h->dtype, h->sE, h->sthreads, h->W + 2 * h->Th);
+  if (resident <= 0) return fail(HEAT1D_ERR_NOT_RESIDENT, "streamed asynchronous run: kernel cannot be resident");
+  const int grid = static_cast<int>(std::min<int64_t>(h->ntiles, resident));
+  if (heat1d_impl::launch_stream_async_setup(a, h->dtype, h->stream))
+    return cuda_fail(cudaGetLastError(), "launch_stream_async_setup");
+  rc = heat1d_impl::launch_stream_async(a, h->dtype, h->sE, h->sthreads, grid, h->stream);
+  if (rc == HEAT1D_ERR_NOT_RESIDENT) return fail(rc, "streamed asynchronous run: grid cannot be resident");
+  if (rc) return cuda_fail(cudaGetLastError(), "launch_stream_async");
+  if (out_dev && !out_on_device)
+    HEAT1D_CUDA(cudaMemcpyAsync(trace_out, out_dev, tbytes, cudaMemcpyDeviceToHost, h->stream));
+  return HEAT1D_OK;
+}
+
 // The asynchronous run with temporal blocking (blocks of T = h->T steps).
 int run_blocked_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device, const uint8_t* trace_in,
                        int in_on_device) {
   if (K < 0 || K >= INT_MAX) return fail(HEAT1D_ERR_INVAL, "K out of range");
   if (K == 0) return HEAT1D_OK;
+  if (blocked_streamed(h)) return run_blocked_streamed(h, K, trace_out, out_on_device, trace_in, in_on_device);
   const bool periodic = h->opts.boundary == 1;
   if (periodic && h->S < 2) return fail(HEAT1D_ERR_INVAL, "periodic blocked runs need at least 2 segments");
   int E = 0, threads = 0;
@@ -583,7 +659,21 @@ int heat1d_replay_blocked(heat1d_t h, int64_t K, const uint8_t* trace, int trace
 
 int64_t heat1d_blocked_trace_bytes(heat1d_t h, int64_t K) {
   if (!h || K < 0) return fail(HEAT1D_ERR_INVAL, "bad argument");
+  if (blocked_streamed(h)) return (K + h->Ts - 1) / h->Ts * std::max<int64_t>(h->ntiles - 1, 0) * 2;
   return (K + h->T - 1) / h->T * (h->opts.boundary == 1 ? h->S : h->S - 1) * 2;
+}
+
+int64_t heat1d_blocked_segments(heat1d_t h, int64_t* offsets, int32_t* block_steps) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  if (!blocked_streamed(h)) {
+    if (offsets) std::memcpy(offsets, h->off.data(), sizeof(int64_t) * (h->S + 1));
+    if (block_steps) *block_steps = h->T;
+    return h->S;
+  }
+  if (offsets)
+    for (int64_t j = 0; j <= h->ntiles; ++j) offsets[j] = std::min<int64_t>(j * h->W, h->N);
+  if (block_steps) *block_steps = h->Ts;
+  return h->ntiles;
 }
 
 int64_t heat1d_trace_bytes(heat1d_t h, int64_t K) {

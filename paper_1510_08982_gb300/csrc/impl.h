@@ -65,8 +65,13 @@ struct StreamRun {
 
 // Largest CTA (threads) of the register-tile kernels for a dtype and E: a
 // tile of more than 64 bytes per thread needs more than 64 registers per
-// thread, so it is limited to 512 threads.
-constexpr int max_tile_threads(int elem_bytes, int E) { return elem_bytes * E > 64 ? 512 : 1024; }
+// thread, so it is limited to 512 threads (up to 128 registers).  So is the
+// FP32 tile of 16 points: its two register arrays of 16 floats and the loop
+// state did not fit 64 registers (ptxas spilled 112-324 bytes per thread in
+// the synchronous and batched kernels).
+constexpr int max_tile_threads(int elem_bytes, int E) {
+  return (elem_bytes * E > 64 || (elem_bytes == 4 && E == 16)) ? 512 : 1024;
+}
 // The asynchronous kernel adds its communication warps to the compute
 // threads (within the 1024-thread CTA limit).
 constexpr int max_async_threads(int elem_bytes, int E) {
@@ -107,6 +112,36 @@ void set_last_error(const std::string& msg);
 constexpr int kStreamMaxThreads = 512;
 int launch_stream_tma(const StreamRun& a, int dtype, int E, int threads, int grid, cudaStream_t st);
 int max_resident_stream_tma(int dtype, int E, int threads, int Wt);
+
+// Arguments of one asynchronous run with temporal blocking streamed through
+// HBM: the tiles are the segments of the blocked model (tile j = points
+// [jW, min((j+1)W, N))), each advanced T steps per block on its own points
+// and two halo strips taken from its neighbours' published versions.
+struct StreamAsyncRun {
+  int64_t N;
+  int64_t K;
+  int T;                   // steps per block
+  int Th;                  // halo points kept per side (>= T, 16-byte multiple)
+  int W;                   // tile width, 16-byte multiple
+  int64_t ntiles;
+  void* u;                 // state, updated in place (each tile reads and writes only its own points)
+  double r, c1, cN;
+  int q;                   // delay window in blocks
+  int R;                   // strip versions kept per tile (power of two, >= 2q)
+  void* strips;            // [ntiles][R][2*Th]: first Th and last Th points of a tile per version
+  int* ver;                // [ntiles] newest version published (set to 0 by the set-up kernel)
+  uint8_t* trace_out;      // device [ceil(K/T)][ntiles-1][2] or NULL
+  const uint8_t* trace_in; // replay: device, same layout
+  int* status;
+  int64_t spin_limit_ns;
+  int64_t stall_tile;      // -1: off; else that tile never publishes (failure test)
+};
+// Publishes version 0 of every tile's strips (the initial state) and sets the
+// version counters to 0; then the persistent launch (cooperative, `grid` CTAs
+// of `threads` compute threads plus a loader and a releaser warp).
+int launch_stream_async_setup(const StreamAsyncRun& a, int dtype, cudaStream_t st);
+int launch_stream_async(const StreamAsyncRun& a, int dtype, int E, int threads, int grid, cudaStream_t st);
+int max_resident_stream_async(int dtype, int E, int threads, int Wt);
 
 // ------------------------------------------------------------ batched rods
 

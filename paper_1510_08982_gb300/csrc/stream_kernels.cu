@@ -21,6 +21,7 @@
 // a thread's run of E points lies inside the rod.
 #include <algorithm>
 
+#include "bulk.cuh"
 #include "common.cuh"
 #include "impl.h"
 
@@ -28,19 +29,6 @@ namespace heat1d_impl {
 using namespace heat1d_dev;
 
 namespace {
-
-template <typename real>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using type = float4;
-  static constexpr int n = 4;
-};
-template <>
-struct Vec16<double> {
-  using type = double2;
-  static constexpr int n = 2;
-};
 
 // Waits until the pass counter of a neighbouring tile reaches `want`.
 __device__ bool wait_tile(const int* done, int want, int* status, int64_t limit_ns) {
@@ -63,7 +51,7 @@ __device__ bool wait_tile(const int* done, int want, int* status, int64_t limit_
 // ------------------------------------------------------------ the pipeline
 //
 // Tile loads and pass-counter releases are taken off the compute warps' path
-// by two extra warps:
+// by two extra warps (the stage ring and its mbarriers are in bulk.cuh):
 //  - the loader (one thread) waits for a tile's previous pass and its
 //    neighbours', then copies the tile and its halos from HBM into one of
 //    kStages shared-memory stages with a single bulk copy (cp.async.bulk, the
@@ -77,56 +65,6 @@ __device__ bool wait_tile(const int* done, int want, int* status, int64_t limit_
 // compute warps with plain loads (the stage is then only a signal).  Every
 // wait is bounded; on a failure the loader waits for its own copies before it
 // returns.
-
-constexpr int kStages = 4;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for the phase of `bar` with the given parity to complete.  Gives up
-// after limit_ns (raising a timeout) or, when `watch` is set, as soon as the
-// run has failed elsewhere.
-__device__ bool mbar_wait(uint64_t* bar, unsigned parity, int* status, int64_t limit_ns, bool watch) {
-  if (mbar_test(bar, parity)) return true;
-  const uint64_t t0 = global_timer_ns();
-  unsigned spins = 0;
-  while (!mbar_test(bar, parity)) {
-    if ((++spins & 15u) == 0) {
-      if (watch && status_failed(status)) return false;
-      if (static_cast<int64_t>(global_timer_ns() - t0) > limit_ns) {
-        raise_status(status, HEAT1D_ERR_TIMEOUT);
-        return false;
-      }
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void bulk_copy_to_shared(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
 
 template <typename real, int E>
 __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_tma_kernel(StreamRun a) {

@@ -28,7 +28,7 @@ STATUS_NAMES = {OK: "HEAT1D_OK", ERR_INVAL: "HEAT1D_ERR_INVAL", ERR_CUDA: "HEAT1
 EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_last_error", "heat1d_set_stream",
            "heat1d_set_snapshots", "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
            "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync",
-           "heat1d_run_async_blocked", "heat1d_replay_blocked", "heat1d_blocked_trace_bytes",
+           "heat1d_run_async_blocked", "heat1d_replay_blocked", "heat1d_blocked_trace_bytes", "heat1d_blocked_segments",
            "heat1d_batch_create", "heat1d_batch_run", "heat1d_batch_sync", "heat1d_batch_describe",
            "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_adjoint", "heat1d_vjp",
            "heat1d_adjoint_batched", "heat1d_run_sync_noalloc", "heat1d_probe_fma"]
@@ -86,6 +86,7 @@ def load():
         "heat1d_run_async_blocked": (i32, [vp, i64, vp, i32]),
         "heat1d_replay_blocked": (i32, [vp, i64, vp, i32]),
         "heat1d_blocked_trace_bytes": (i64, [vp, i64]),
+        "heat1d_blocked_segments": (i64, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
         "heat1d_run_sync_noalloc": (i32, [vp, vp, i64, dbl, dbl, dbl, i32, i64, i64, vp, vp]),
         "heat1d_probe_fma": (i32, [i32, i32, i64, i64, i32, vp, vp, ctypes.POINTER(i64)]),
         "heat1d_batch_create": (vp, [ctypes.POINTER(RodSpec), i64, i32, ctypes.POINTER(Opts)]),
@@ -278,12 +279,26 @@ class Heat1d:
     def blocked_trace_bytes(self, K) -> int:
         return int(self.lib.heat1d_blocked_trace_bytes(self.h, int(K)))
 
+    def blocked_segments(self):
+        """(offsets, T): the segments of the blocked asynchronous run (the
+        handle's segments on chip, the HBM tiles when streamed) and its block
+        length."""
+        n = int(self.lib.heat1d_blocked_segments(self.h, None, None))
+        if n < 0:
+            raise Heat1dError(n, last_error())
+        off = np.zeros(n + 1, dtype=np.int64)
+        T = ctypes.c_int32(0)
+        self.lib.heat1d_blocked_segments(self.h, off.ctypes.data_as(ctypes.c_void_p), ctypes.byref(T))
+        return off, int(T.value)
+
     def new_blocked_trace(self, K, device=True):
-        """A trace buffer for a blocked run of K steps: (ceil(K/T), S-1, 2) uint8."""
+        """A trace buffer for a blocked run of K steps: (ceil(K/T), S-1, 2)
+        uint8 (S segments of blocked_segments(); S on the periodic ring)."""
         torch = _torch()
         o = self.get_opts()
-        T = o["halo_steps"]
-        shape = ((int(K) + T - 1) // T, self.S if o.get("boundary", 0) == 1 else max(self.S - 1, 0), 2)
+        off, T = self.blocked_segments()
+        S = off.size - 1
+        shape = ((int(K) + T - 1) // T, S if o.get("boundary", 0) == 1 else max(S - 1, 0), 2)
         if device:
             return torch.empty(shape, dtype=torch.uint8, device="cuda")
         return np.empty(shape, dtype=np.uint8)

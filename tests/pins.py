@@ -85,7 +85,14 @@ def brute_sync_fraction(u0, r, c1, cN, K):
     return u
 
 
-def segment_of(N, S):
+def segment_of(N, S, offsets=None):
+    """Segment index of every point: the standard split (the first N mod S
+    segments one point longer), or the split given by S+1 offsets."""
+    if offsets is not None:
+        seg = []
+        for s in range(len(offsets) - 1):
+            seg += [s] * (int(offsets[s + 1]) - int(offsets[s]))
+        return seg
     base, extra = divmod(N, S)
     seg, s, count = [], 0, 0
     for s in range(S):
@@ -93,7 +100,7 @@ def segment_of(N, S):
     return seg
 
 
-def async_step_matrix(N, r, S, q, dk):
+def async_step_matrix(N, r, S, q, dk, offsets=None):
     """Block matrix (qN x qN) for one step of Eq. (eqn:async).
 
     dk has shape (S-1, 2): dk[b][0] is the delay of segment b's read of its
@@ -101,7 +108,7 @@ def async_step_matrix(N, r, S, q, dk):
     neighbour.  Block j of z holds u(k-j).  Delays must already be clamped to
     at most q-1 (the augmented state has q blocks)."""
     r = _frac(r)
-    seg = segment_of(N, S)
+    seg = segment_of(N, S, offsets)
     M = [[Fraction(0)] * (q * N) for _ in range(q * N)]
     M[0][0] = Fraction(1)
     M[N - 1][N - 1] = Fraction(1)
@@ -117,8 +124,9 @@ def async_step_matrix(N, r, S, q, dk):
     return M
 
 
-def brute_async_fraction(u0, r, c1, cN, S, q, trace):
-    """Exact u(K) of the switched system driven by trace (K, S-1, 2)."""
+def brute_async_fraction(u0, r, c1, cN, S, q, trace, offsets=None):
+    """Exact u(K) of the switched system driven by trace (K, S-1, 2); the
+    segments are the standard split or the one given by offsets."""
     N = len(u0)
     u = [_frac(v) for v in u0]
     u[0] = _frac(c1)
@@ -126,7 +134,7 @@ def brute_async_fraction(u0, r, c1, cN, S, q, trace):
     z = u * q
     trace = np.asarray(trace)
     for k in range(trace.shape[0]):
-        M = async_step_matrix(N, r, S, q, trace[k])
+        M = async_step_matrix(N, r, S, q, trace[k], offsets)
         z = matvec(M, z)
     return z[:N]
 
@@ -191,7 +199,7 @@ def async_periodic_step_matrix(N, r, S, q, dk):
     """Block matrix for one periodic asynchronous step; dk has shape (S, 2):
     boundary b joins segment b and (b+1) mod S."""
     r = _frac(r)
-    seg = segment_of(N, S)
+    seg = segment_of(N, S, offsets)
     M = [[Fraction(0)] * (q * N) for _ in range(q * N)]
     for i in range(N):
         il, ir = (i - 1) % N, (i + 1) % N
@@ -218,7 +226,7 @@ def brute_async_periodic_fraction(u0, r, S, q, trace):
 # ----------------------------------------------------------------------------- asynchronous, temporally blocked
 
 
-def brute_async_blocked_fraction(u0, r, c1, cN, S, q, T, K, trace):
+def brute_async_blocked_fraction(u0, r, c1, cN, S, q, T, K, trace, offsets=None):
     """Exact state after K steps of the blocked asynchronous run, written as
     matrix powers on whole vectors: for block b and segment s the composite
     vector z = W_b, with the T points left of the segment taken from W_{b-dL}
@@ -232,10 +240,13 @@ def brute_async_blocked_fraction(u0, r, c1, cN, S, q, T, K, trace):
     u[0] = _frac(c1)
     u[-1] = _frac(cN)
     A = sync_matrix_fraction(N, r)
-    off = [0]
-    base, extra = divmod(N, S)
-    for s in range(S):
-        off.append(off[-1] + base + (1 if s < extra else 0))
+    if offsets is not None:
+        off = [int(x) for x in offsets]
+    else:
+        off = [0]
+        base, extra = divmod(N, S)
+        for s in range(S):
+            off.append(off[-1] + base + (1 if s < extra else 0))
     W = [u]
     trace = np.asarray(trace)
     nb = (K + T - 1) // T

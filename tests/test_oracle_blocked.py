@@ -160,3 +160,92 @@ def test_blocked_periodic_sum_drifts_only_with_delays():
     assert abs(oracle.async_blocked_periodic(u0, 0.5, S, q, T, K, z).sum() - u0.sum()) < 1e-10
     tr = inputs.periodic_delay_trace(nblocks(K, T), S, q, seed=1)
     assert abs(oracle.async_blocked_periodic(u0, 0.5, S, q, T, K, tr).sum() - u0.sum()) > 1e-6
+
+
+# --------------------------------------------------------------------------- given splits
+
+
+def random_split(rng, N, S, T):
+    """S+1 offsets with every segment but the first and the last >= T points;
+    the first and the last may be shorter (down to one point)."""
+    while True:
+        inner = rng.integers(T, T + 6, size=S - 2) if S > 2 else np.zeros(0, dtype=np.int64)
+        ends = rng.integers(1, T + 4, size=2)
+        lens = np.concatenate([[ends[0]], inner, [ends[1]]]) if S > 1 else np.array([N])
+        if lens.sum() == N:
+            return np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        if S > 1:
+            lens[1 if S > 2 else 0] += N - lens.sum()
+            if lens.min() >= 1 and (S <= 2 or lens[1:-1].min() >= T):
+                return np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+
+
+def test_split_with_the_standard_offsets_is_the_standard_model():
+    rod = inputs.small_rod(K=400)
+    tr = inputs.delay_trace(nblocks(400, 16), 8, 3, seed=7)
+    a = oracle.async_blocked(rod.u0, rod.r, rod.c1, rod.cN, 8, 3, 16, 400, tr)
+    b = oracle.async_blocked_split(rod.u0, rod.r, rod.c1, rod.cN, oracle.segments(1024, 8), 3, 16, 400, tr)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_split_zero_trace_equals_sync_bitwise(seed):
+    """Any split with all strips current is the synchronous run, also with a
+    first or last segment shorter than T."""
+    rng = np.random.default_rng(seed)
+    T, S = int(rng.integers(2, 9)), int(rng.integers(2, 7))
+    N = int(T * S + rng.integers(3, 20))
+    off = random_split(rng, N, S, T)
+    K = int(rng.integers(5, 60))
+    u0 = rng.uniform(-1, 1, size=N)
+    tr = np.zeros((nblocks(K, T), S - 1, 2), dtype=np.uint8)
+    for dt in (np.float64, np.float32):
+        a = oracle.async_blocked_split(u0, 0.3, 0.5, -0.25, off, 3, T, K, tr, dtype=dt)
+        assert np.array_equal(a, oracle.sync(u0, 0.3, 0.5, -0.25, K, dtype=dt))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4, 5])
+def test_split_brute_force_exact(seed):
+    """Exact rational whole-vector matrix powers on a random split (first and
+    last segments may be shorter than T) against the oracle bit for bit
+    (dyadic data, r = 1/4)."""
+    rng = np.random.default_rng(100 + seed)
+    T, S, q = int(rng.integers(2, 5)), int(rng.integers(2, 5)), int(rng.integers(1, 4))
+    N = int(T * S + rng.integers(2, 6))
+    off = random_split(rng, N, S, T)
+    K = int(rng.integers(4, 13))
+    u0 = rng.integers(-16, 17, size=N) / 16.0
+    nb = nblocks(K, T)
+    tr = rng.integers(0, q, size=(nb, S - 1, 2)).astype(np.uint8)
+    trc = np.minimum(tr, np.arange(nb)[:, None, None]).astype(np.uint8)
+    exact = pins.brute_async_blocked_fraction(u0, Fraction(1, 4), 0.25, -0.75, S, q, T, K, trc, offsets=off)
+    got = oracle.async_blocked_split(u0, 0.25, 0.25, -0.75, off, q, T, K, tr)
+    assert [Fraction(float(x)) for x in got] == exact
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_split_T1_is_the_switched_system(seed):
+    """Blocks of one step on a given split are Eq. (eqn:async) on that split:
+    exact rational brute force of the augmented switched system."""
+    rng = np.random.default_rng(200 + seed)
+    S, q = int(rng.integers(2, 5)), int(rng.integers(1, 4))
+    N = int(S + rng.integers(3, 8))
+    off = random_split(rng, N, S, 1)
+    K = int(rng.integers(4, 11))
+    u0 = rng.integers(-16, 17, size=N) / 16.0
+    tr = rng.integers(0, q, size=(K, S - 1, 2)).astype(np.uint8)
+    trc = np.minimum(tr, np.arange(K)[:, None, None]).astype(np.uint8)
+    exact = pins.brute_async_fraction(u0, Fraction(1, 4), 0.25, -0.75, S, q, trc, offsets=off)
+    got = oracle.async_blocked_split(u0, 0.25, 0.25, -0.75, off, q, 1, K, tr)
+    assert [Fraction(float(x)) for x in got] == exact
+
+
+def test_split_rejects_bad_offsets():
+    u0 = np.zeros(20)
+    tr = np.zeros((2, 2, 2), dtype=np.uint8)
+    with pytest.raises(oracle.OracleError):   # an inner segment shorter than T
+        oracle.async_blocked_split(u0, 0.25, 0, 0, np.array([0, 9, 11, 20]), 2, 4, 8, tr)
+    with pytest.raises(oracle.OracleError):   # offsets not ending at N
+        oracle.async_blocked_split(u0, 0.25, 0, 0, np.array([0, 9, 14, 19]), 2, 4, 8, tr)
+    with pytest.raises(oracle.OracleError):   # an empty segment
+        oracle.async_blocked_split(u0, 0.25, 0, 0, np.array([0, 9, 9, 20]), 2, 4, 8, tr)

@@ -151,11 +151,11 @@ MUTATIONS = [
      "trace[(k * (S - 1) + seg[i]) * 2 + 0]", "trace[((k + 1 < K ? k + 1 : k) * (S - 1) + seg[i]) * 2 + 0]"),
     ("async: delayed read of the own point", "oracle_async", pins_async,
      "u = H(k, i)", "u = H(tL, i)"),
-    ("blocked: left strip always current", "oracle_async_blocked", pins_blocked,
+    ("blocked: left strip always current", "oracle_async_blocked_split", pins_blocked,
      "bl = b - (d < b ? d : b);", "bl = b;"),
-    ("blocked: halo one point too narrow", "oracle_async_blocked", pins_blocked,
+    ("blocked: halo one point too narrow", "oracle_async_blocked_split", pins_blocked,
      "lo - T > 0 ? lo - T : 0", "lo - T + 1 > 0 ? lo - T + 1 : 0"),
-    ("blocked: sides swapped", "oracle_async_blocked", pins_blocked,
+    ("blocked: sides swapped", "oracle_async_blocked_split", pins_blocked,
      "(s - 1)) * 2 + 1]", "(s - 1)) * 2 + 0]"),
     ("blocked periodic: left halo with the right side's delay", "oracle_async_blocked_periodic",
      pins_blocked_periodic, "(s + S - 1) % S) * 2 + 1]", "(s + S - 1) % S) * 2 + 0]"),
