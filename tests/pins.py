@@ -199,7 +199,7 @@ def async_periodic_step_matrix(N, r, S, q, dk):
     """Block matrix for one periodic asynchronous step; dk has shape (S, 2):
     boundary b joins segment b and (b+1) mod S."""
     r = _frac(r)
-    seg = segment_of(N, S, offsets)
+    seg = segment_of(N, S)
     M = [[Fraction(0)] * (q * N) for _ in range(q * N)]
     for i in range(N):
         il, ir = (i - 1) % N, (i + 1) % N
