@@ -327,7 +327,7 @@ int heat1d_adjoint_batched(int64_t nrods, int64_t N, int64_t K, const double* r,
  * bit) from u_in to u_out: two distinct device buffers of N values of
  * `dtype`, owned by the caller.  u_out[0] and u_out[N-1] receive c1 and cN.
  * segments: S, in [1, 256], or 0 for one per SM (at most 256); each segment
- * must fit one CTA (about 16K points in F32 and 8K in F64).  The halo depth is
+ * must fit one CTA (about 8K points in F32 and in F64).  The halo depth is
  * the handle's default (F32 128 steps; F64 64 on segments of 4096 points or
  * more, else 32), at most N/S.  The run is enqueued on `stream` (a
  * cudaStream_t, NULL for the legacy default stream).  If status_out is not
@@ -361,9 +361,11 @@ int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N, double r, 
  * kernels are held against, three FP64 fused multiply-adds per update in F64
  * runs).  Enqueues one launch of `blocks` CTAs of `threads` threads (a
  * multiple of 32, at most 1024) on `stream`; every thread advances `chains`
- * (4, 8 or 16) independent chains a <- fma(a, b, c) for `iters` iterations
- * and writes one value to out (device, blocks * threads values of the dtype,
- * owned by the caller).  *fma_per_launch (may be NULL) receives the number of
+ * (4, 8 or 16) independent chains a <- fma(a, b, c) for `iters` iterations,
+ * or, with chains = -P (P = 8 or 16), P points on a ring in registers by two
+ * FTCS steps per iteration (three fused multiply-adds per point and step, the
+ * stencil kernels' own operand pattern), and writes one value to out
+ * (device, blocks * threads values of the dtype, owned by the caller).  *fma_per_launch (may be NULL) receives the number of
  * fused multiply-adds the launch executes; the caller times the launch (CUDA
  * events on the stream) and divides.  HEAT1D_ERR_INVAL for a bad shape, chain
  * count or dtype, HEAT1D_ERR_CUDA if the launch fails. */

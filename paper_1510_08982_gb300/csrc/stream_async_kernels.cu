@@ -281,7 +281,11 @@ __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_async_kernel
     }
     // A failed wait ends the run for every compute warp (see the streamed
     // synchronous kernel: passes longer than H steps meet refresh barriers).
-    if (a.T > Win::H) {
+    // The last tile reads its own points straight from the state it updates
+    // in place, and adjacent warps both load the points their windows share:
+    // every warp must have loaded before any warp stores, so that tile always
+    // meets this barrier (the value is the same for the whole CTA).
+    if (a.T > Win::H || stage_plain[st]) {
       if (named_barrier_or(2, nthreads_c, failed)) return;
     } else if (failed) {
       return;

@@ -390,8 +390,8 @@ def probe_fma(dtype="float64", iters=None, shapes=None, repeats=3):
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     f64 = dtype in ("float64", torch.float64)
     tdt = torch.float64 if f64 else torch.float32
-    if shapes is None:
-        shapes = [(8, 4, 256), (16, 2, 512), (4, 8, 256), (16, 1, 1024)]
+    if shapes is None:  # (chains, CTAs per SM, threads); chains < 0: the stencil's pattern on -chains points
+        shapes = [(8, 4, 256), (16, 2, 512), (4, 8, 256), (16, 1, 1024), (-8, 4, 256), (-16, 2, 256)]
     if iters is None:
         iters = 40_000 if f64 else 400_000
     st = torch.cuda.current_stream()
@@ -405,14 +405,16 @@ def probe_fma(dtype="float64", iters=None, shapes=None, repeats=3):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            _check(lib.heat1d_probe_fma(_dtype_code(tdt), chains, int(iters * 8 // chains), blocks, threads,
+            per_iter = chains if chains > 0 else -chains * 6
+            _check(lib.heat1d_probe_fma(_dtype_code(tdt), chains, int(max(1, iters * 8 // per_iter)), blocks, threads,
                                         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream),
                                         ctypes.byref(n)))
             e1.record(st)
             e1.synchronize()
             if i > 0:  # the first launch is a warm-up
                 best = max(best, n.value / (e0.elapsed_time(e1) * 1e-3))
-        rates["chains=%d ctas_per_sm=%d threads=%d" % (chains, per_sm, threads)] = best
+        key = ("chains=%d" % chains) if chains > 0 else ("stencil points=%d" % -chains)
+        rates["%s ctas_per_sm=%d threads=%d" % (key, per_sm, threads)] = best
     return max(rates.values()), rates
 
 

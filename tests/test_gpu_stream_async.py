@@ -87,9 +87,9 @@ def test_streamed_async_seeded_trace_and_short_last_tile(H, dtype):
     """A seeded trace (delays i.i.d. in {0..q-1}), a last tile of 3 points and
     a block length that does not divide K."""
     T, E, threads, q = 16, 8, 64, 3
-    with H.Heat1d(10, 0.25, 0, 0, dtype=dtype, sync_mode=2, halo_steps=T, elems_per_thread=E,
+    with H.Heat1d(100_000, 0.25, 0, 0, dtype=dtype, sync_mode=2, halo_steps=T, elems_per_thread=E,
                   block_threads=threads) as h0:
-        W = int(h0.blocked_segments()[0][1])
+        W = int(h0.blocked_segments()[0][1])  # the tile width of this shape
     N = 7 * W + 3
     rng = np.random.default_rng(5)
     rod = inputs.Rod(N=N, K=203, r=0.33, c1=-0.2, cN=0.9, u0=rng.uniform(-1, 1, size=N))
@@ -105,6 +105,23 @@ def test_streamed_async_seeded_trace_and_short_last_tile(H, dtype):
     zero = np.zeros_like(tr)
     got0 = replay(H, rod, rod.K, zero, dtype, q=q, halo_steps=T, elems_per_thread=E, block_threads=threads)
     check(got0, oracle.sync(rod.u0, rod.r, rod.c1, rod.cN, rod.K, dtype=np_dt(dtype)))
+
+
+@pytest.mark.parametrize("dtype,T,K", [("float32", 1, 200), ("float32", 4, 300), ("float64", 2, 200),
+                                       ("float32", 8, 160)])
+def test_streamed_async_default_tiles_in_place_last_tile(H, dtype, T, K):
+    """The default tile shape on a 2^22-point rod, block lengths at or below
+    the warp-halo refresh depth (the compute warps then meet no barrier), a
+    last tile of 3600 points read and written in place: free run and replay
+    of its trace, both against the oracle."""
+    rod = inputs.uniform_rod(N=1 << 22, K=K, seed=4)
+    u0 = rod.u0.astype(np_dt(dtype)).astype(np.float64)
+    rod = inputs.Rod(N=rod.N, K=K, r=rod.r, c1=0.0, cN=0.0, u0=u0)
+    got, tr, off, Tb = free_run(H, rod, K, dtype, halo_steps=T)
+    assert off[-1] - off[-2] > 1000
+    ref = oracle_replay(rod, off, 3, T, K, tr, dtype)
+    check(got, ref)
+    check(replay(H, rod, K, tr, dtype, halo_steps=T), ref)
 
 
 def test_streamed_async_single_tile(H):
