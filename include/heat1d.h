@@ -75,8 +75,10 @@ typedef struct heat1d_opts {
                             4, 8 or 16).  0: automatic. */
   int64_t spin_limit_ns; /* bound on every device-side wait.  0: 2e9 (2 s). */
   int32_t stall_segment; /* fault injection for tests: when >= 0, that segment of an asynchronous
-                            run never publishes, so its neighbours' waits run out and the run
-                            ends with HEAT1D_ERR_TIMEOUT.  Default -1 (off). */
+                            run (that tile of a streamed run; that rod part, by its index among
+                            the batch's parts, of a batched run) never publishes, so its
+                            neighbours' waits run out and the run ends with HEAT1D_ERR_TIMEOUT.
+                            Default -1 (off). */
   int32_t sync_mode;     /* synchronous run: 0 automatic, 1 on-chip (one CTA per segment, the
                             segment in registers), 2 streamed (temporal blocking through HBM:
                             tiles of block_threads * elems_per_thread points, halo_steps steps

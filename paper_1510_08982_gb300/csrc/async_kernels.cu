@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
   const int L = static_cast<int>(a.seg_off[s + 1] - a0);
   const int K = static_cast<int>(a.K);
   const int S = a.S;
-  const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
-  const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};  // one = 1 at run time
+  const real c1 = kparam<real>(a.c1, a.c1_f), cN = kparam<real>(a.cN, a.cN_f);
+  const Coef<real> coef{kparam<real>(a.r, a.r_f), kparam<real>(a.one, a.one_f)};  // one = 1 at run time
   const real* __restrict__ uin = static_cast<const real*>(a.u_in);
   real* __restrict__ uout = static_cast<real*>(a.u_out);
   const bool periodic = a.periodic != 0;
@@ -322,11 +322,11 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
     const int n = min(kRefresh, K - k0);
     if (!per_step) {
       if (mode == kTileFree)
-        warp_steps<real, E, kTileFree>(v, fixed, coef, n);
+        warp_run<real, E, kTileFree, kRefresh>(v, fixed, coef, n);
       else if (mode == kTileEnds)
-        warp_steps<real, E, kTileEnds>(v, fixed, coef, n);
+        warp_run<real, E, kTileEnds, kRefresh>(v, fixed, coef, n);
       else if (mode == kTileMasked)
-        warp_steps<real, E, kTileMasked>(v, fixed, coef, n);
+        warp_run<real, E, kTileMasked, kRefresh>(v, fixed, coef, n);
     } else {
       // One step from `in` to `out`: the halo reads before it, the state
       // records and edge hand-offs after it.  Steps alternate between v and
@@ -418,6 +418,7 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
 template <typename real, int E>
 int launch_async_t(const SegmentRun& a, int threads, cudaStream_t st) {
   SegmentRun args = a;
+  set_run_params(args);
   void* params[] = {&args};
   cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(async_persistent_kernel<real, E>), dim3(a.S),
                                               dim3(threads + 32 * kCommWarps), params, 0, st);

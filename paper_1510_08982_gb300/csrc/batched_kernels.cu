@@ -28,6 +28,8 @@ using namespace heat1d_dev;
 
 namespace {
 
+// The waiting thread naps between polls: the batch runs two or more CTAs per
+// SM, and a tight spin takes issue slots from the other CTAs' compute warps.
 __device__ bool wait_flag_at_least(const int* flag, int want, int* status, int64_t limit_ns) {
   if (ld_acquire_gpu(flag) >= want) return true;
   const uint64_t t0 = global_timer_ns();
@@ -40,17 +42,18 @@ __device__ bool wait_flag_at_least(const int* flag, int want, int* status, int64
         return false;
       }
     }
+    __nanosleep(32);
   }
   return true;
 }
 
 // A small rod advanced by one warp: positions lane*E + e.
 template <typename real, int E>
-__device__ void run_warp_rod(const BatchRod& rd, real* u, int lane) {
+__device__ void run_warp_rod(const BatchRod& rd, real* u, int lane, double one, float one_f) {
   real* x = u + rd.offset;
   const int N = static_cast<int>(rd.N);
-  const real c1 = static_cast<real>(rd.c1), cN = static_cast<real>(rd.cN);
-  const Coef<real> coef{static_cast<real>(rd.r), static_cast<real>(rd.N > 0)};
+  const real c1 = kparam<real>(rd.c1, rd.c1_f), cN = kparam<real>(rd.cN, rd.cN_f);
+  const Coef<real> coef{kparam<real>(rd.r, rd.r_f), kparam<real>(one, one_f)};
   real v[E];
   unsigned fixed = 0;
 #pragma unroll
@@ -85,6 +88,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   real* u = static_cast<real*>(a.u);
   real* edges = static_cast<real*>(a.edges);
+  const double one = a.one;
+  const float one_f = a.one_f;
   int parity = 0;
 
   while (true) {
@@ -95,14 +100,14 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
     const BatchItem it = a.items[idx];
 
     if (it.kind == kBatchWarps) {
-      if (warp < it.count) run_warp_rod<real, E>(a.rods[a.warp_rods[it.rod + warp]], u, lane);
+      if (warp < it.count) run_warp_rod<real, E>(a.rods[a.warp_rods[it.rod + warp]], u, lane, one, one_f);
     } else if (it.kind == kBatchRod) {
       // The whole rod in this CTA; its ends are fixed, so nothing degrades.
       const BatchRod rd = a.rods[it.rod];
       real* x = u + rd.offset;
       const int N = static_cast<int>(rd.N);
-      const real c1 = static_cast<real>(rd.c1), cN = static_cast<real>(rd.cN);
-      const Coef<real> coef{static_cast<real>(rd.r), static_cast<real>(rd.N > 0)};
+      const real c1 = kparam<real>(rd.c1, rd.c1_f), cN = kparam<real>(rd.cN, rd.cN_f);
+      const Coef<real> coef{kparam<real>(rd.r, rd.r_f), kparam<real>(one, one_f)};
       real v[E];
       unsigned fixed = 0;
 #pragma unroll
@@ -141,8 +146,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
       const int lo = first ? 0 : (last ? P - L : T);
       const int hi = lo + L;
       const int tile_end = last ? hi : hi + T;
-      const real c1 = static_cast<real>(rd.c1), cN = static_cast<real>(rd.cN);
-      const Coef<real> coef{static_cast<real>(rd.r), static_cast<real>(rd.N > 0)};
+      const real c1 = kparam<real>(rd.c1, rd.c1_f), cN = kparam<real>(rd.cN, rd.cN_f);
+      const Coef<real> coef{kparam<real>(rd.r, rd.r_f), kparam<real>(one, one_f)};
       const size_t estride = static_cast<size_t>(4) * a.Tmax;
       int* myflag = a.flags + it.slot;
       real v[E];
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         if (tid == 0) {
           // A release at GPU scope after the CTA barrier orders every thread's
           // edge stores before the flag (cumulativity); no separate fence.
-          st_release_gpu(myflag, epoch + 2);
+          if (it.slot != a.stall_slot) st_release_gpu(myflag, epoch + 2);
           bool w = true;
           if (it.part > 0) w = wait_flag_at_least(myflag - 1, epoch + 2, a.status, a.spin_limit_ns);
           if (w && it.part + 1 < it.nparts) w = wait_flag_at_least(myflag + 1, epoch + 2, a.status, a.spin_limit_ns);

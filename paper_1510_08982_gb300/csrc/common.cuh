@@ -147,6 +147,19 @@ __device__ __forceinline__ float ftcs(float r, float /*one*/, float uL, float u,
 // [w*D + H, w*D + 32E - H); warp 0 and the last warp also own the CTA's outer
 // H positions) publishes or stores them.
 
+// A run parameter in the run's precision: F64 kernels take the double, F32
+// kernels the float the host rounded it to.  The kernels then never convert a
+// double to float, which runs on the FP64 pipe and which the compiler may
+// repeat wherever it recomputes the value instead of keeping it in a
+// register (measured: one conversion per warp and halo refresh in the FP32
+// synchronous kernel).
+template <typename real>
+__device__ __forceinline__ real kparam(double d, float f);
+template <>
+__device__ __forceinline__ double kparam<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float kparam<float>(double, float f) { return f; }
+
 // Stencil coefficients: r, and a run-time 1.0 (see ftcs).
 template <typename real>
 struct Coef {
@@ -251,6 +264,24 @@ __device__ __forceinline__ void warp_steps(real (&v)[E], unsigned fixed, Coef<re
   if (j < n) warp_step<real, E, kMode>(v, fixed, c);
 }
 
+// A run of n <= H steps between two halo refreshes.  A full run of H steps
+// (the common case) is unrolled completely, so that no step pays a loop
+// counter, a compare or a branch; a shorter run takes the loop.
+template <typename real, int E, int kMode, int H>
+__device__ __forceinline__ void warp_run(real (&v)[E], unsigned fixed, Coef<real> c, int n) {
+  if (kMode == kTileIdle || n != H) {
+    warp_steps<real, E, kMode>(v, fixed, c, n);
+    return;
+  }
+  real w[E];
+#pragma unroll
+  for (int j = 0; j + 1 < H; j += 2) {
+    warp_step_to<real, E, kMode>(v, w, fixed, c);
+    warp_step_to<real, E, kMode>(w, v, fixed, c);
+  }
+  if (H & 1) warp_step<real, E, kMode>(v, fixed, c);
+}
+
 template <typename real, int E>
 __device__ __forceinline__ void warp_step_any(int mode, real (&v)[E], unsigned fixed, Coef<real> c) {
   if (mode == kTileFree)
@@ -303,11 +334,11 @@ __device__ __forceinline__ void warp_advance(int mode, real (&v)[E], unsigned fi
   for (int done = 0; done < steps;) {
     const int n = min(H, steps - done);
     if (mode == kTileFree) {
-      warp_steps<real, E, kTileFree>(v, fixed, c, n);
+      warp_run<real, E, kTileFree, H>(v, fixed, c, n);
     } else if (mode == kTileEnds) {
-      warp_steps<real, E, kTileEnds>(v, fixed, c, n);
+      warp_run<real, E, kTileEnds, H>(v, fixed, c, n);
     } else if (mode == kTileMasked) {
-      warp_steps<real, E, kTileMasked>(v, fixed, c, n);
+      warp_run<real, E, kTileMasked, H>(v, fixed, c, n);
     }
     done += n;
     if (done < steps || final_refresh) {

@@ -213,6 +213,7 @@ int run_streamed(heat1d* h, int64_t K) {
   a.done = h->done;
   a.status = h->status();
   a.spin_limit_ns = h->opts.spin_limit_ns;
+  a.stall_tile = h->opts.stall_segment;
   // Pipelined kernel: tile loads by bulk copies from one extra producer warp.
   const int resident = heat1d_impl::max_resident_stream_tma(h->dtype, h->sE, h->sthreads, h->W + 2 * h->Th);
   if (resident <= 0) return fail(HEAT1D_ERR_NOT_RESIDENT, "streamed run: kernel cannot be resident");
@@ -712,6 +713,7 @@ struct heat1d_batch {
   int E = 8, threads = 256, grid = 0, T = 16;
   int64_t cap = 0;  // positions per CTA
   int64_t spin_limit_ns = 2000000000LL;
+  int stall_slot = -1;  // failure test: this rod part never publishes an epoch
   int64_t nrods = 0, nitems = 0, nparts = 0, counts[3] = {0, 0, 0};
   heat1d_impl::BatchRod* d_rods = nullptr;
   int* d_warp_rods = nullptr;
@@ -755,7 +757,8 @@ int batch_plan(heat1d_batch* b, const heat1d_rod* rods, int64_t nrods, std::vect
     if (r.N < 3 || r.K < 0 || r.offset < 0 || !(r.r > 0.0 && r.r <= 0.5))
       return fail(HEAT1D_ERR_INVAL, "batched rods: rod " + std::to_string(j) +
                                         " needs N >= 3, K >= 0, offset >= 0 and 0 < r <= 0.5");
-    out_rods[j] = heat1d_impl::BatchRod{r.offset, r.N, r.K, r.r, r.c1, r.cN};
+    out_rods[j] = heat1d_impl::BatchRod{r.offset, r.N, r.K, r.r, r.c1, r.cN, static_cast<float>(r.r),
+                                        static_cast<float>(r.c1), static_cast<float>(r.cN)};
     if (r.K == 0) continue;
     if (r.N <= warp_cap) {
       small.push_back(static_cast<int>(j));
@@ -834,6 +837,7 @@ heat1d_batch_t heat1d_batch_create(const heat1d_rod* rods, int64_t nrods, int dt
   b->threads = opts.block_threads ? opts.block_threads : 256;
   b->T = opts.halo_steps ? opts.halo_steps : (dtype == HEAT1D_F64 ? 16 : 32);
   if (opts.spin_limit_ns > 0) b->spin_limit_ns = opts.spin_limit_ns;
+  b->stall_slot = opts.stall_segment >= 0 && opts.stall_segment < INT_MAX ? static_cast<int>(opts.stall_segment) : -1;
   if ((b->E != 4 && b->E != 8 && b->E != 16) || b->threads % 32 != 0 || b->threads < 32 ||
       b->threads > heat1d_impl::max_tile_threads(static_cast<int>(b->esize), b->E) || b->T < 1) {
     fail(HEAT1D_ERR_INVAL, "heat1d_batch_create: elems_per_thread must be 4, 8 or 16 and block_threads a multiple "
@@ -908,8 +912,11 @@ int heat1d_batch_run(heat1d_batch_t b, void* u_packed, void* stream) {
   a.flags = b->d_flags;
   a.edges = b->d_edges;
   a.Tmax = b->T;
+  a.one = 1.0;
+  a.one_f = 1.0f;
   a.status = static_cast<int*>(b->d_ctl) + 32;
   a.spin_limit_ns = b->spin_limit_ns;
+  a.stall_slot = b->stall_slot;
   HEAT1D_CUDA(cudaMemsetAsync(b->d_ctl, 0, sizeof(unsigned), st));
   if (b->nparts > 0) HEAT1D_CUDA(cudaMemsetAsync(b->d_flags, 0, sizeof(int) * b->nparts, st));
   int rc = heat1d_impl::launch_batched(a, b->dtype, b->E, b->threads, b->grid, st);

@@ -26,6 +26,9 @@ struct SegmentRun {
   const void* u_in;        // device, N values
   void* u_out;             // device, N values (a different buffer)
   double r, c1, cN;
+  float r_f, c1_f, cN_f;   // the same rounded to float (FP32 runs; set at launch)
+  double one;              // 1.0 as a run-time value (see ftcs in common.cuh); one_f its float
+  float one_f;
   int* status;             // device status word (0 = healthy)
   int64_t spin_limit_ns;
   int periodic;            // 1: periodic ring (Section 5.3), no Dirichlet ends
@@ -58,9 +61,13 @@ struct StreamRun {
   void* u_a;               // state at pass 0 (read), then alternating
   void* u_b;
   double r, c1, cN;
+  float r_f, c1_f, cN_f;   // FP32 copies and the run-time 1.0, as in SegmentRun
+  double one;
+  float one_f;
   int* done;               // [ntiles] passes completed per tile, 0 at launch
   int* status;
   int64_t spin_limit_ns;
+  int64_t stall_tile;      // -1: off; else that tile never publishes a pass (failure test)
 };
 
 // Largest CTA (threads) of the register-tile kernels for a dtype and E: a
@@ -91,6 +98,18 @@ constexpr int async_window_halo(int /*elem_bytes*/, int E) { return E / 2; }
 constexpr int64_t window_width(int64_t nwarps, int E, int H) { return nwarps * (32 * E - 2 * H) + 2 * H; }
 constexpr int64_t window_warps(int64_t positions, int E, int H) {
   return positions <= 2 * H ? 1 : (positions - 2 * H + (32 * E - 2 * H) - 1) / (32 * E - 2 * H);
+}
+
+// Sets the FP32 copies of a run's parameters (round to nearest, as a device
+// conversion would) and the run-time 1.0.  Every launch function applies it
+// to its copy of the arguments.
+template <typename Run>
+inline void set_run_params(Run& a) {
+  a.r_f = static_cast<float>(a.r);
+  a.c1_f = static_cast<float>(a.c1);
+  a.cN_f = static_cast<float>(a.cN);
+  a.one = 1.0;
+  a.one_f = 1.0f;
 }
 
 // Launch the persistent kernels (cooperative launch: all S CTAs resident).
@@ -126,6 +145,9 @@ struct StreamAsyncRun {
   int64_t ntiles;
   void* u;                 // state, updated in place (each tile reads and writes only its own points)
   double r, c1, cN;
+  float r_f, c1_f, cN_f;   // FP32 copies and the run-time 1.0, as in SegmentRun
+  double one;
+  float one_f;
   int q;                   // delay window in blocks
   int R;                   // strip versions kept per tile (power of two, >= 2q)
   void* strips;            // [ntiles][R][2*Th]: first Th and last Th points of a tile per version
@@ -151,6 +173,7 @@ struct BatchRod {
   int64_t N;
   int64_t K;
   double r, c1, cN;
+  float r_f, c1_f, cN_f;  // the same rounded to float (FP32 batches)
 };
 
 // One work item: what one CTA does between two grabs from the queue.
@@ -177,8 +200,11 @@ struct BatchRun {
   int* flags;             // per part: 1 after loading, e+2 after publishing epoch e; zero at launch
   void* edges;            // per part: [2 parities][2][Tmax] values
   int Tmax;
+  double one;             // 1.0 as a run-time value; one_f its float
+  float one_f;
   int* status;
   int64_t spin_limit_ns;
+  int stall_slot;         // -1: off; else the part in that flag slot never publishes an epoch (failure test)
 };
 
 // Batched launch: `grid` CTAs (all resident) of `threads` threads, E points

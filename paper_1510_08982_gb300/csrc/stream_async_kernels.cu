@@ -231,8 +231,8 @@ __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_async_kernel
   }
 
   // ------------------------------------------------------------ compute warps
-  const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};
-  const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
+  const Coef<real> coef{kparam<real>(a.r, a.r_f), kparam<real>(a.one, a.one_f)};
+  const real c1 = kparam<real>(a.c1, a.c1_f), cN = kparam<real>(a.cN, a.cN_f);
   const int p0 = Win::pos(warp, lane, 0);
   const bool owns_all = Win::owner(warp, lane, 0, nwc) && Win::owner(warp, lane, E - 1, nwc);
   int parity = 0;
@@ -354,6 +354,7 @@ size_t async_smem_bytes(int Wt) {
 template <typename real, int E>
 int launch_t(const StreamAsyncRun& a, int threads, int grid, cudaStream_t st) {
   StreamAsyncRun args = a;
+  set_run_params(args);
   void* params[] = {&args};
   const size_t smem = async_smem_bytes<real>(a.W + 2 * a.Th);
   if (cudaFuncSetAttribute(stream_async_kernel<real, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,

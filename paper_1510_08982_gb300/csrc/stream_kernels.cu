@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_tma_kernel(S
       // CTA scope, acquired by the wait above), are ordered before the
       // counter by this release at GPU scope (cumulativity).  No separate
       // fence: it would wait a second time for the same stores.
-      st_release_gpu(a.done + j, p + 1);
+      if (j != a.stall_tile) st_release_gpu(a.done + j, p + 1);
       mbar_arrive(&freed[st]);
       j += gridDim.x;
       if (j >= a.ntiles) {
@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_tma_kernel(S
   }
 
   // ------------------------------------------------------------ compute warps
-  const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};
-  const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
+  const Coef<real> coef{kparam<real>(a.r, a.r_f), kparam<real>(a.one, a.one_f)};
+  const real c1 = kparam<real>(a.c1, a.c1_f), cN = kparam<real>(a.cN, a.cN_f);
   const int p0 = Win::pos(warp, lane, 0);
   const bool owns_all = Win::owner(warp, lane, 0, nwc) && Win::owner(warp, lane, E - 1, nwc);
   int parity = 0;
@@ -276,6 +276,7 @@ size_t tma_smem_bytes(int Wt) {
 template <typename real, int E>
 int launch_stream_tma_t(const StreamRun& a, int threads, int grid, cudaStream_t st) {
   StreamRun args = a;
+  set_run_params(args);
   void* params[] = {&args};
   const size_t smem = tma_smem_bytes<real, E>(a.W + 2 * a.Th);
   if (cudaFuncSetAttribute(stream_tma_kernel<real, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -57,8 +57,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
   const int64_t a0 = a.seg_off[s];
   const int L = static_cast<int>(a.seg_off[s + 1] - a0);
   const int T = a.T;
-  const real c1 = static_cast<real>(a.c1), cN = static_cast<real>(a.cN);
-  const Coef<real> coef{static_cast<real>(a.r), static_cast<real>(a.N > 0)};  // one = 1 at run time
+  const real c1 = kparam<real>(a.c1, a.c1_f), cN = kparam<real>(a.cN, a.cN_f);
+  const Coef<real> coef{kparam<real>(a.r, a.r_f), kparam<real>(a.one, a.one_f)};  // one = 1 at run time
   const real* __restrict__ uin = static_cast<const real*>(a.u_in);
   real* __restrict__ uout = static_cast<real*>(a.u_out);
   real* edges = static_cast<real*>(a.edges);
@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 template <typename real, int E>
 int launch_sync_t(const SegmentRun& a, int threads, cudaStream_t st) {
   SegmentRun args = a;
+  set_run_params(args);
   void* params[] = {&args};
   cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(sync_persistent_kernel<real, E>), dim3(a.S),
                                               dim3(threads), params, 0, st);

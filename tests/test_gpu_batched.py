@@ -123,3 +123,26 @@ def test_batched_rejects_bad_rods(H):
         H.Batch([(0, 100, 10, 0.75, 0.0, 0.0)], dtype="float64")
     with pytest.raises(H.Heat1dError):
         H.Batch([(0, 2, 10, 0.25, 0.0, 0.0)], dtype="float64")
+
+
+def test_batched_stalled_part_times_out(H):
+    """A rod part that never publishes its epochs (a flag set on the host)
+    makes its neighbours' bounded waits run out: HEAT1D_ERR_TIMEOUT; a batch
+    planned without the flag then runs correctly."""
+    rng = np.random.default_rng(4)
+    rods = [inputs.Rod(N=30_000, K=300, r=0.3, c1=0.1, cN=-0.2, u0=rng.uniform(-1, 1, size=30_000))
+            for _ in range(3)]
+    specs, u, off = pack(H, rods, "float64")
+    with H.Batch(specs, dtype="float64", stall_segment=2, spin_limit_ns=200_000_000) as b:
+        assert b.describe()["rod_parts"] > 3
+        b.run(u)
+        with pytest.raises(H.Heat1dError) as ei:
+            b.sync()
+        assert ei.value.code == H.ERR_TIMEOUT
+    specs, u, off = pack(H, rods, "float64")
+    with H.Batch(specs, dtype="float64") as b:
+        b.run(u)
+        b.sync()
+    got = u.cpu().numpy()
+    for o, r in zip(off, rods):
+        assert np.array_equal(got[o:o + r.N], oracle_rod(r, "float64"))

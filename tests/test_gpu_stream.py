@@ -96,3 +96,25 @@ def test_streamed_full_size_sampled(H, dtype, r, T):
     for i, g in zip(samples, got):
         ref = cone_sample(u0, rod.r, rod.c1, rod.cN, rod.K, i, np_dt)
         assert g == ref, (i, float(g), float(ref))
+
+
+def test_streamed_stalled_tile_times_out(H):
+    """A tile that never publishes its pass counter (a flag set on the host)
+    makes its neighbours' bounded waits run out: the run ends with
+    HEAT1D_ERR_TIMEOUT and the handle stays usable."""
+    rod = inputs.uniform_rod(N=200_000, K=400, seed=2)
+    with H.Heat1d(rod.N, rod.r, 0.0, 0.0, dtype="float32", sync_mode=2, halo_steps=16, stall_segment=5,
+                  spin_limit_ns=200_000_000) as h:
+        h.set_u(rod.u0.astype(np.float32))
+        h.run_sync(rod.K)
+        with pytest.raises(H.Heat1dError) as ei:
+            h.sync()
+        assert ei.value.code == H.ERR_TIMEOUT
+        h.set_opts(sync_mode=2, halo_steps=16)
+        h.set_u(rod.u0.astype(np.float32))
+        h.run_sync(rod.K)
+        h.sync()
+        got = h.get_u(device=False)
+    u0 = rod.u0.astype(np.float32)
+    for i in (7, 123_456, rod.N - 2):
+        assert got[i] == cone_sample(u0.astype(np.float64), rod.r, 0.0, 0.0, rod.K, i, np.float32)
