@@ -65,14 +65,14 @@ typedef struct heat1d_opts {
                             length q).  0: 3. */
   int32_t halo_steps;    /* T, steps advanced between two exchanges in the synchronous run
                             (overlapped halos of width T) and the block length of the blocked
-                            asynchronous run.  0: automatic (on-chip runs: FP64 64, or 32 when the
-                            shortest segment has fewer than 4096 points; FP32 128; at most the
-                            shortest segment.  Streamed runs 32 in FP64, 128 in FP32).
+                            asynchronous run.  0: automatic (on-chip runs: FP64 64 and FP32 256, or
+                            32 and 128 when the shortest segment has fewer than 4096 points; at most
+                            the shortest segment.  Streamed runs 32 in FP64, 128 in FP32).
                             1: exchange and grid barrier after every step, as in Section 2. */
   int32_t block_threads; /* threads per CTA for the compute warps (a multiple of 32; at most 512 in
                             streamed runs, which add a loader and a releaser warp).  0: automatic. */
-  int32_t elems_per_thread; /* points held in registers per thread (2, 4, 8 or 16; streamed runs
-                            4, 8 or 16).  0: automatic. */
+  int32_t elems_per_thread; /* points held in registers per thread (2, 4, 8 or 16, or 32 in F32
+                            synchronous and blocked runs; streamed runs 4, 8 or 16).  0: automatic. */
   int64_t spin_limit_ns; /* bound on every device-side wait.  0: 2e9 (2 s). */
   int32_t stall_segment; /* fault injection for tests: when >= 0, that segment of an asynchronous
                             run (that tile of a streamed run; that rod part, by its index among
@@ -167,6 +167,47 @@ int64_t heat1d_trace_bytes(heat1d_t h, int64_t K);
  * the run return HEAT1D_ERR_TRACE from heat1d_sync() and leave the state
  * unspecified. */
 int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_device);
+
+/* ------------------------------------------------------------ checkpoint / resume
+ *
+ * The asynchronous run of Section 3 is the switched system on the augmented
+ * state z(k) = [u(k); u(k-1); ...; u(k-q+1)] (Eq. (eqn:async): a read may
+ * return any of the q most recent steps).  Only values that cross a segment
+ * boundary can be read late, so the augmented state a run needs to continue
+ * is u(k) plus every segment's first and last point at the last q steps.
+ * After heat1d_run_async or heat1d_replay the handle holds that state; a
+ * following asynchronous run or replay continues from it (its step 0 is the
+ * global step k, delays are clamped to the global step, its trace covers
+ * steps k .. k+K-1), so a run split into several calls equals the run made
+ * by one call bit for bit.  Any other state change (heat1d_set_u, a
+ * synchronous, blocked or adjoint run, new options) starts over at step 0.
+ *
+ * State layout: a heat1d_state_header, then N values of u (the handle's
+ * dtype), then the history [S][2][q] values: [s][0][j] is segment s's first
+ * point and [s][1][j] its last point at global step k-q+1+j.  A state
+ * without history (has_history = 0, step 0) holds the current edge values in
+ * every history entry. */
+typedef struct heat1d_state_header {
+  int64_t magic;       /* identifies a heat1d state */
+  int64_t step;        /* global step k of the state */
+  int64_t N, S;        /* points and segments of the handle that wrote it */
+  int32_t q, dtype;    /* delay window and HEAT1D_F32 / HEAT1D_F64 */
+  int32_t has_history; /* 1: continues an asynchronous run */
+  int32_t reserved;
+} heat1d_state_header;
+
+/* Size in bytes of a state: sizeof(heat1d_state_header) + (N + 2*S*q) values. */
+int64_t heat1d_state_bytes(heat1d_t h);
+
+/* Copies the handle's state (layout above) into `state` (device or host per
+ * on_device, heat1d_state_bytes(h) bytes, owned by the caller); with a host
+ * buffer the call waits for the stream. */
+int heat1d_get_state(heat1d_t h, void* state, int on_device);
+
+/* Loads a state written by heat1d_get_state of a handle with the same N,
+ * segments, q and dtype (else HEAT1D_ERR_INVAL, nothing changed); the next
+ * asynchronous run or replay continues it. */
+int heat1d_set_state(heat1d_t h, const void* state, int on_device);
 
 /* ------------------------------------------------------------ asynchronous run, temporally blocked
  *
@@ -325,13 +366,14 @@ int heat1d_adjoint_batched(int64_t nrods, int64_t N, int64_t K, const double* r,
  * heat1d_create(), which such callers cannot do.
  *
  * Computes the same K steps as heat1d_run_sync() with the handle's default
- * options (same kernel, same halo depth and launch shape, same result bit for
- * bit) from u_in to u_out: two distinct device buffers of N values of
+ * options (same kernel and launch-shape rule, same result bit for bit; the
+ * halo depth is capped at what its scratch array holds) from u_in to u_out:
+ * two distinct device buffers of N values of
  * `dtype`, owned by the caller.  u_out[0] and u_out[N-1] receive c1 and cN.
  * segments: S, in [1, 256], or 0 for one per SM (at most 256); each segment
  * must fit one CTA (about 8K points in F32 and in F64).  The halo depth is
- * the handle's default (F32 128 steps; F64 64 on segments of 4096 points or
- * more, else 32), at most N/S.  The run is enqueued on `stream` (a
+ * F32 128 steps; F64 64 on segments of 4096 points or more, else 32; at most
+ * N/S.  The run is enqueued on `stream` (a
  * cudaStream_t, NULL for the legacy default stream).  If status_out is not
  * NULL it must be a device int; it receives the run's device status
  * (HEAT1D_OK or HEAT1D_ERR_TIMEOUT) when the run completes on the stream.

@@ -70,15 +70,18 @@ template <typename real>
 __device__ __forceinline__ bool fetch_halo(const SegmentRun& a, const int* avail, const real* ring, int k,
                                            const uint8_t* trace_in, uint8_t* trace_out, size_t tidx, int d_replay,
                                            real& value) {
+  // Step k of this launch is global step k0 + k of a resumed run; no read
+  // reaches before global step 0 (a delay is clamped to the global step).
+  const int kb = a.k0 < a.q ? static_cast<int>(a.k0) : a.q;
   int need;
   if (trace_in) {
     if (d_replay >= a.q) {
       raise_status(a.status, HEAT1D_ERR_TRACE);
       return false;
     }
-    need = k - min(d_replay, k);
+    need = k - min(d_replay, k + kb);
   } else {
-    need = max(k - a.q + 1, 0);
+    need = max(k - a.q + 1, -kb);
   }
   int V = ld_acquire_cta_shared(avail);
   if (V < need) {
@@ -156,9 +159,17 @@ __device__ void publish_loop(const SegmentRun& a, AsyncShared<real, E>& sh, int 
 // trips however many versions arrived.
 template <typename real, int E>
 __device__ void pull_loop(const SegmentRun& a, AsyncShared<real, E>& sh, const int* nprog, const real* nring,
-                          real* lring, int* avail, int lane) {
+                          real* lring, int* avail, int lane, const real* nhist) {
   const int R = a.R;
   int seen = -1;
+  if (nhist) {
+    // A resumed run: the neighbour's edge value at the last q steps before
+    // this launch (versions -q+1 .. 0) is already known.
+    for (int j = lane; j < a.q; j += 32) lring[(j - a.q + 1) & (R - 1)] = nhist[j];
+    __syncwarp();
+    if (lane == 0) st_release_cta_shared(avail, 0);
+    seen = 0;
+  }
   uint64_t t_idle = global_timer_ns();
   unsigned spins = 0;
   while (true) {
@@ -220,10 +231,14 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
       // right neighbour's left edge
       const bool from_left = warp == nwc + 1;
       const int nb = from_left ? sl : sr;
+      // history layout [S][2][q]: side 0 the first point, side 1 the last point
+      const real* nhist = (nb >= 0 && a.hist_in)
+                              ? static_cast<const real*>(a.hist_in) + (static_cast<size_t>(nb) * 2 + (from_left ? 1 : 0)) * a.q
+                              : nullptr;
       if (nb >= 0)
         pull_loop<real, E>(a, sh, a.prog + static_cast<size_t>(nb) * kProgStride,
                            rings + (static_cast<size_t>(nb) * 2 + (from_left ? 1 : 0)) * a.R,
-                           from_left ? sh.lring : sh.rring, from_left ? &sh.lavail : &sh.ravail, lane);
+                           from_left ? sh.lring : sh.rring, from_left ? &sh.lavail : &sh.ravail, lane, nhist);
     }
     return;
   }
@@ -410,6 +425,26 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
   for (int e = 0; e < E; ++e) {
     const int p = Win::pos(warp, lane, e);
     if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) uout[a0 - 1 + p] = v[e];
+  }
+  // The edge values of the last q steps, for a later resumed run: versions
+  // K-q+1 .. K of this launch from the hand-off rings (written by these same
+  // threads), older ones from the history this launch started from.
+  if (a.hist_out && !aborted && (e_first >= 0 || e_last >= 0)) {
+    real* ho = static_cast<real*>(a.hist_out);
+    const real* hi_ = static_cast<const real*>(a.hist_in);
+    for (int j = 0; j < a.q; ++j) {
+      const int ver = K - a.q + 1 + j;
+      if (e_first >= 0) {
+        const real x = ver >= 0 ? sh.own_l[ver & (a.R - 1)]
+                                : (hi_ ? hi_[(static_cast<size_t>(s) * 2 + 0) * a.q + (ver + a.q - 1)] : sh.own_l[0]);
+        ho[(static_cast<size_t>(s) * 2 + 0) * a.q + j] = x;
+      }
+      if (e_last >= 0) {
+        const real x = ver >= 0 ? sh.own_r[ver & (a.R - 1)]
+                                : (hi_ ? hi_[(static_cast<size_t>(s) * 2 + 1) * a.q + (ver + a.q - 1)] : sh.own_r[0]);
+        ho[(static_cast<size_t>(s) * 2 + 1) * a.q + j] = x;
+      }
+    }
   }
   named_barrier_sync(1, nthreads_c);
   if (tid == 0) st_release_cta_shared(&sh.compute_done, aborted ? 2 : 1);

@@ -271,6 +271,7 @@ int launch_batched(const BatchRun& a, int dtype, int E, int threads, int grid, c
     case 4: return f64 ? launch_batched_t<double, 4>(a, threads, grid, st) : launch_batched_t<float, 4>(a, threads, grid, st);
     case 8: return f64 ? launch_batched_t<double, 8>(a, threads, grid, st) : launch_batched_t<float, 8>(a, threads, grid, st);
     case 16: return f64 ? launch_batched_t<double, 16>(a, threads, grid, st) : launch_batched_t<float, 16>(a, threads, grid, st);
+    case 32: return f64 ? HEAT1D_ERR_INVAL : launch_batched_t<float, 32>(a, threads, grid, st);
     default: return HEAT1D_ERR_INVAL;
   }
 }
@@ -281,6 +282,7 @@ int max_resident_batched(int dtype, int E, int threads) {
     case 4: return f64 ? resident_batched_t<double, 4>(threads) : resident_batched_t<float, 4>(threads);
     case 8: return f64 ? resident_batched_t<double, 8>(threads) : resident_batched_t<float, 8>(threads);
     case 16: return f64 ? resident_batched_t<double, 16>(threads) : resident_batched_t<float, 16>(threads);
+    case 32: return f64 ? 0 : resident_batched_t<float, 32>(threads);
     default: return 0;
   }
 }

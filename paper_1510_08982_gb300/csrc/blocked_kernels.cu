@@ -231,6 +231,7 @@ int launch_async_blocked(const SegmentRun& a, int dtype, int E, int threads, cud
     case 4: return f64 ? launch_t<double, 4>(a, threads, st) : launch_t<float, 4>(a, threads, st);
     case 8: return f64 ? launch_t<double, 8>(a, threads, st) : launch_t<float, 8>(a, threads, st);
     case 16: return f64 ? launch_t<double, 16>(a, threads, st) : launch_t<float, 16>(a, threads, st);
+    case 32: return f64 ? HEAT1D_ERR_INVAL : launch_t<float, 32>(a, threads, st);
     default: return HEAT1D_ERR_INVAL;
   }
 }

@@ -269,7 +269,8 @@ __device__ __forceinline__ void warp_steps(real (&v)[E], unsigned fixed, Coef<re
 // counter, a compare or a branch; a shorter run takes the loop.
 template <typename real, int E, int kMode, int H>
 __device__ __forceinline__ void warp_run(real (&v)[E], unsigned fixed, Coef<real> c, int n) {
-  if (kMode == kTileIdle || n != H) {
+  if (kMode == kTileIdle) return;  // a warp wholly outside the tile holds nothing that is read
+  if (n != H) {
     warp_steps<real, E, kMode>(v, fixed, c, n);
     return;
   }
@@ -295,10 +296,10 @@ __device__ __forceinline__ void warp_step_any(int mode, real (&v)[E], unsigned f
 }
 
 // Refreshes every warp's halos from its neighbours (one barrier over the
-// `nthreads` compute threads, named barrier 1).  Returns the OR of `flag`
-// over those threads, so that a failure seen by one thread reaches all of
-// them at the same point.
-template <typename real, int E, int H>
+// `nthreads` compute threads, named barrier 1).  kOr: the barrier also
+// returns the OR of `flag` over those threads, so that a failure seen by one
+// thread reaches all of them at the same point; otherwise a plain barrier.
+template <typename real, int E, int H, bool kOr = true>
 __device__ __forceinline__ bool warp_refresh(real (&v)[E], WindowShared<real, H>& sh, int parity, int warp, int lane,
                                              int nwarps, unsigned nthreads, bool flag) {
   if (lane == 31) {
@@ -309,7 +310,11 @@ __device__ __forceinline__ bool warp_refresh(real (&v)[E], WindowShared<real, H>
 #pragma unroll
     for (int i = 0; i < H; ++i) sh.to_left[parity][warp][i] = v[H + i];
   }
-  const bool any = named_barrier_or(1, nthreads, flag);
+  bool any = false;
+  if (kOr)
+    any = named_barrier_or(1, nthreads, flag);
+  else
+    named_barrier_sync(1, nthreads);
   if (lane == 0 && warp > 0) {
 #pragma unroll
     for (int i = 0; i < H; ++i) v[i] = sh.to_right[parity][warp - 1][i];
@@ -321,31 +326,48 @@ __device__ __forceinline__ bool warp_refresh(real (&v)[E], WindowShared<real, H>
   return any;
 }
 
+// warp_advance for one tile mode: full runs of H steps (unrolled), each
+// followed by a refresh, then the last run of 1..H steps.
+template <typename real, int E, int H, int kMode>
+__device__ __forceinline__ void warp_advance_mode(real (&v)[E], unsigned fixed, Coef<real> c,
+                                                  WindowShared<real, H>& sh, int& parity, int warp, int lane,
+                                                  int nwarps, unsigned nthreads, int steps, bool final_refresh) {
+  int done = 0;
+  for (; done + H < steps; done += H) {
+    warp_run<real, E, kMode, H>(v, fixed, c, H);
+    warp_refresh<real, E, H, false>(v, sh, parity, warp, lane, nwarps, nthreads, false);
+    parity ^= 1;
+  }
+  warp_run<real, E, kMode, H>(v, fixed, c, steps - done);
+  if (final_refresh) {
+    warp_refresh<real, E, H, false>(v, sh, parity, warp, lane, nwarps, nthreads, false);
+    parity ^= 1;
+  }
+}
+
 // Advances the CTA `steps` steps: runs of at most H warp steps, each followed
 // by a refresh, so the windows are fully valid again when it returns.  With
 // final_refresh = false the refresh after the last run is left out: every
 // warp's own positions are valid after at most H steps, and a caller that
 // only stores those (and then discards the tile) saves a barrier; with
-// steps <= H no barrier is met at all.
+// steps <= H no barrier is met at all.  The mode is resolved once per call.
 template <typename real, int E, int H>
 __device__ __forceinline__ void warp_advance(int mode, real (&v)[E], unsigned fixed, Coef<real> c,
                                              WindowShared<real, H>& sh, int& parity, int warp, int lane, int nwarps,
                                              unsigned nthreads, int steps, bool final_refresh = true) {
-  for (int done = 0; done < steps;) {
-    const int n = min(H, steps - done);
-    if (mode == kTileFree) {
-      warp_run<real, E, kTileFree, H>(v, fixed, c, n);
-    } else if (mode == kTileEnds) {
-      warp_run<real, E, kTileEnds, H>(v, fixed, c, n);
-    } else if (mode == kTileMasked) {
-      warp_run<real, E, kTileMasked, H>(v, fixed, c, n);
-    }
-    done += n;
-    if (done < steps || final_refresh) {
-      warp_refresh<real, E, H>(v, sh, parity, warp, lane, nwarps, nthreads, false);
-      parity ^= 1;
-    }
-  }
+  if (steps <= 0) return;
+  if (mode == kTileFree)
+    warp_advance_mode<real, E, H, kTileFree>(v, fixed, c, sh, parity, warp, lane, nwarps, nthreads, steps,
+                                             final_refresh);
+  else if (mode == kTileEnds)
+    warp_advance_mode<real, E, H, kTileEnds>(v, fixed, c, sh, parity, warp, lane, nwarps, nthreads, steps,
+                                             final_refresh);
+  else if (mode == kTileMasked)
+    warp_advance_mode<real, E, H, kTileMasked>(v, fixed, c, sh, parity, warp, lane, nwarps, nthreads, steps,
+                                               final_refresh);
+  else
+    warp_advance_mode<real, E, H, kTileIdle>(v, fixed, c, sh, parity, warp, lane, nwarps, nthreads, steps,
+                                             final_refresh);
 }
 
 __device__ __forceinline__ int ld_volatile_shared(const int* p) { return *reinterpret_cast<const volatile int*>(p); }

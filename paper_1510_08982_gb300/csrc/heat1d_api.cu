@@ -45,6 +45,22 @@ __global__ void set_ends_kernel(real* u, int64_t N, double c1, double cN) {
 }
 
 
+// History of a state that does not continue an asynchronous run: every
+// entry is the segment's current edge value (a run started from it reads no
+// step before it).
+template <typename real>
+__global__ void edges_history_kernel(const real* u, const int64_t* off, int S, int q, real* hist) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    const real first = u[off[s]], last = u[off[s + 1] - 1];
+    for (int j = 0; j < q; ++j) {
+      hist[(static_cast<size_t>(s) * 2 + 0) * q + j] = first;
+      hist[(static_cast<size_t>(s) * 2 + 1) * q + j] = last;
+    }
+  }
+}
+
+constexpr int64_t kStateMagic = 0x3144485453453148LL;  // "H1ESTHD1"
+
 }  // namespace
 
 void heat1d_impl::set_last_error(const std::string& msg) { g_last_error = msg; }
@@ -81,6 +97,14 @@ struct heat1d {
   int64_t snap_every = 0, snap_rows = 0;
   void* strips = nullptr;  // blocked asynchronous run: [S][R][2T] strips, allocated on first use
   size_t strips_bytes = 0;
+  // Checkpoint/resume of the asynchronous run: the current state is global
+  // step async_step of an asynchronous run whose segments' edge values at
+  // its last q steps are in hist[hist_cur] ([S][2][q]); hist_cur < 0: no
+  // such history (the next asynchronous run starts at step 0).
+  int64_t async_step = 0;
+  void* hist[2] = {nullptr, nullptr};
+  size_t hist_bytes = 0;
+  int hist_cur = -1;
 
   unsigned* barrier() { return static_cast<unsigned*>(ctl); }
   int* status() { return static_cast<int*>(ctl) + 32; }
@@ -88,7 +112,19 @@ struct heat1d {
 
 namespace {
 
+// The state no longer continues an asynchronous run (a new u, another kind
+// of run, new options).
+void reset_history(heat1d* h) {
+  h->async_step = 0;
+  h->hist_cur = -1;
+}
+
 void free_scratch(heat1d* h) {
+  cudaFree(h->hist[0]);
+  cudaFree(h->hist[1]);
+  h->hist[0] = h->hist[1] = nullptr;
+  h->hist_bytes = 0;
+  reset_history(h);
   cudaFree(h->d_off);
   cudaFree(h->edges);
   cudaFree(h->rings);
@@ -110,8 +146,8 @@ int configure(heat1d* h, const heat1d_opts& o) {
       o.elems_per_thread < 0 || o.spin_limit_ns < 0)
     return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: negative or out-of-range option");
   if (o.elems_per_thread && o.elems_per_thread != 2 && o.elems_per_thread != 4 && o.elems_per_thread != 8 &&
-      o.elems_per_thread != 16)
-    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: elems_per_thread must be 2, 4, 8 or 16");
+      o.elems_per_thread != 16 && !(o.elems_per_thread == 32 && h->esize == 4))
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: elems_per_thread must be 2, 4, 8 or 16 (or 32 in F32)");
   if (o.block_threads % 32 != 0 || o.block_threads > 1024)
     return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: block_threads must be a multiple of 32, at most 1024");
   int64_t S = o.segments ? o.segments : h->nsm;
@@ -135,11 +171,12 @@ int configure(heat1d* h, const heat1d_opts& o) {
   // On-chip synchronous runs take halos from the neighbouring segment only,
   // so their T is at most the shortest segment (clamped unless on-chip mode
   // was asked for explicitly).
-  // Default depth (measured best on GB300): FP32 128 steps, where a step
-  // costs little and the exchange weighs more; FP64 64 steps on segments of
-  // 4096 points or more and 32 on shorter ones, where the halo's redundant
-  // arithmetic (2T per segment) weighs more.
-  int T = o.halo_steps ? o.halo_steps : (h->esize == 4 ? 128 : (Lmin >= 4096 ? 64 : 32));
+  // Default depth (measured best on GB300): FP32 256 steps on segments of
+  // 4096 points or more (128 on shorter ones), where a step costs little and
+  // the exchange (about 5 us a block on the 2^20-point rod) weighs more; FP64
+  // 64 steps on segments of 4096 points or more and 32 on shorter ones, where
+  // the halo's redundant arithmetic (2T per segment) weighs more.
+  int T = o.halo_steps ? o.halo_steps : (h->esize == 4 ? (Lmin >= 4096 ? 256 : 128) : (Lmin >= 4096 ? 64 : 32));
   if (T > Lmin) {
     if (o.halo_steps && o.sync_mode == 1)
       return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: halo_steps exceeds the shortest segment");
@@ -238,9 +275,11 @@ bool try_shape(const heat1d* h, int64_t slots, int reserved, bool async_kernel, 
   // at least 8 warps: per update it then issues half the shuffles and halo
   // refreshes of E = 8, which on GB300 ran 1.2-1.4x faster.
   const bool prefer16 = h->esize == 4 && slots >= 8 * 32 * 16;
-  const int Es[4] = {2, 4, 8, 16};
-  const int Es16[4] = {16, 2, 4, 8};
-  for (int i = 0; i < 4; ++i) {
+  const int Es[5] = {2, 4, 8, 16, 32};
+  const int Es16[5] = {16, 2, 4, 8, 32};
+  // 32 points per thread: FP32 synchronous-family kernels only
+  const int ncand = (h->esize == 4 && !async_kernel) ? 5 : 4;
+  for (int i = 0; i < ncand; ++i) {
     const int e = prefer16 ? Es16[i] : Es[i];
     if (forced_E && e != forced_E) continue;
     const int64_t limit = (async_kernel ? heat1d_impl::max_async_threads(static_cast<int>(h->esize), e)
@@ -366,12 +405,29 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   if ((rc = stage_traces(h, tbytes, trace_out, out_on_device, trace_in, in_on_device, &out_dev, &in_dev))) return rc;
   a.trace_out = out_dev;
   a.trace_in = in_dev;
+  const size_t hbytes = h->esize * static_cast<size_t>(h->S) * 2 * h->q;
+  if (hbytes > h->hist_bytes) {
+    cudaFree(h->hist[0]);
+    cudaFree(h->hist[1]);
+    h->hist[0] = h->hist[1] = nullptr;
+    h->hist_bytes = 0;
+    reset_history(h);
+    HEAT1D_CUDA(cudaMalloc(&h->hist[0], hbytes));
+    HEAT1D_CUDA(cudaMalloc(&h->hist[1], hbytes));
+    h->hist_bytes = hbytes;
+  }
+  const int hout = h->hist_cur >= 0 ? 1 - h->hist_cur : 0;
+  a.k0 = h->hist_cur >= 0 ? h->async_step : 0;
+  a.hist_in = h->hist_cur >= 0 ? h->hist[h->hist_cur] : nullptr;
+  a.hist_out = h->hist[hout];
   HEAT1D_CUDA(cudaMemsetAsync(h->prog, 0xff, sizeof(int) * h->S * heat1d_impl::kProgStride, h->stream));
   rc = heat1d_impl::launch_async_persistent(a, h->dtype, E, threads, h->stream);
   if (rc == HEAT1D_ERR_NOT_RESIDENT)
     return fail(rc, "asynchronous run: " + std::to_string(h->S) + " CTAs cannot all be resident");
   if (rc) return cuda_fail(cudaGetLastError(), "launch_async_persistent");
   h->cur = 1 - h->cur;
+  h->async_step = a.k0 + K;
+  h->hist_cur = hout;
   if (out_dev && !out_on_device)
     HEAT1D_CUDA(cudaMemcpyAsync(trace_out, out_dev, tbytes, cudaMemcpyDeviceToHost, h->stream));
   return HEAT1D_OK;
@@ -441,6 +497,7 @@ int run_blocked_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_devi
                        int in_on_device) {
   if (K < 0 || K >= INT_MAX) return fail(HEAT1D_ERR_INVAL, "K out of range");
   if (K == 0) return HEAT1D_OK;
+  reset_history(h);
   if (blocked_streamed(h)) return run_blocked_streamed(h, K, trace_out, out_on_device, trace_in, in_on_device);
   const bool periodic = h->opts.boundary == 1;
   if (periodic && h->S < 2) return fail(HEAT1D_ERR_INVAL, "periodic blocked runs need at least 2 segments");
@@ -591,6 +648,7 @@ int64_t heat1d_num_segments(heat1d_t h, int64_t* offsets) {
 
 int heat1d_set_u(heat1d_t h, const void* u, int on_device) {
   if (!h || !u) return fail(HEAT1D_ERR_INVAL, "null argument");
+  reset_history(h);
   HEAT1D_CUDA(cudaMemcpyAsync(h->u[h->cur], u, h->esize * h->N,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
   if (h->opts.boundary == 1) {  // periodic: no Dirichlet ends to force
@@ -618,6 +676,7 @@ int heat1d_run_sync(heat1d_t h, int64_t K) {
   if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
   if (K < 0) return fail(HEAT1D_ERR_INVAL, "K must be >= 0");
   if (K == 0) return HEAT1D_OK;
+  reset_history(h);
   int E = 0, threads = 0;
   int rc = h->opts.sync_mode == 2 ? HEAT1D_ERR_INVAL : pick_shape(h, h->Lmax + 2 * h->T, 0, false, &E, &threads);
   if (rc) {
@@ -687,6 +746,96 @@ int heat1d_replay(heat1d_t h, int64_t K, const uint8_t* trace, int trace_on_devi
   if (!trace && h->S > 1 && K > 0) return fail(HEAT1D_ERR_INVAL, "heat1d_replay: trace is NULL");
   static const uint8_t dummy = 0;
   return run_async_common(h, K, nullptr, 0, trace ? trace : &dummy, trace ? trace_on_device : 0);
+}
+
+int64_t heat1d_state_bytes(heat1d_t h) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  return static_cast<int64_t>(sizeof(heat1d_state_header)) +
+         static_cast<int64_t>(h->esize) * (h->N + static_cast<int64_t>(h->S) * 2 * h->q);
+}
+
+int heat1d_get_state(heat1d_t h, void* state, int on_device) {
+  if (!h || !state) return fail(HEAT1D_ERR_INVAL, "null argument");
+  heat1d_state_header hd{};
+  hd.magic = kStateMagic;
+  hd.step = h->hist_cur >= 0 ? h->async_step : 0;
+  hd.N = h->N;
+  hd.S = h->S;
+  hd.q = h->q;
+  hd.dtype = h->dtype;
+  hd.has_history = h->hist_cur >= 0;
+  const size_t ub = h->esize * h->N, hb = h->esize * static_cast<size_t>(h->S) * 2 * h->q;
+  void* hist = nullptr;
+  if (h->hist_cur >= 0) {
+    hist = h->hist[h->hist_cur];
+  } else {
+    if (hb > h->hist_bytes) {
+      cudaFree(h->hist[0]);
+      cudaFree(h->hist[1]);
+      h->hist[0] = h->hist[1] = nullptr;
+      h->hist_bytes = 0;
+      HEAT1D_CUDA(cudaMalloc(&h->hist[0], hb));
+      HEAT1D_CUDA(cudaMalloc(&h->hist[1], hb));
+      h->hist_bytes = hb;
+    }
+    hist = h->hist[0];
+    const int grid = std::min(1024, (h->S + 127) / 128);
+    if (h->dtype == HEAT1D_F64)
+      edges_history_kernel<double><<<grid, 128, 0, h->stream>>>(static_cast<const double*>(h->u[h->cur]), h->d_off,
+                                                                h->S, h->q, static_cast<double*>(hist));
+    else
+      edges_history_kernel<float><<<grid, 128, 0, h->stream>>>(static_cast<const float*>(h->u[h->cur]), h->d_off,
+                                                               h->S, h->q, static_cast<float*>(hist));
+    HEAT1D_CUDA(cudaGetLastError());
+  }
+  unsigned char* out = static_cast<unsigned char*>(state);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (on_device) {
+    HEAT1D_CUDA(cudaMemcpyAsync(out, &hd, sizeof(hd), cudaMemcpyHostToDevice, h->stream));
+    HEAT1D_CUDA(cudaStreamSynchronize(h->stream));  // hd lives on this stack
+  } else {
+    std::memcpy(out, &hd, sizeof(hd));
+  }
+  HEAT1D_CUDA(cudaMemcpyAsync(out + sizeof(hd), h->u[h->cur], ub, kind, h->stream));
+  HEAT1D_CUDA(cudaMemcpyAsync(out + sizeof(hd) + ub, hist, hb, kind, h->stream));
+  if (!on_device) HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
+  return HEAT1D_OK;
+}
+
+int heat1d_set_state(heat1d_t h, const void* state, int on_device) {
+  if (!h || !state) return fail(HEAT1D_ERR_INVAL, "null argument");
+  heat1d_state_header hd{};
+  const unsigned char* in = static_cast<const unsigned char*>(state);
+  if (on_device) {
+    HEAT1D_CUDA(cudaMemcpyAsync(&hd, in, sizeof(hd), cudaMemcpyDeviceToHost, h->stream));
+    HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
+  } else {
+    std::memcpy(&hd, in, sizeof(hd));
+  }
+  if (hd.magic != kStateMagic) return fail(HEAT1D_ERR_INVAL, "heat1d_set_state: not a heat1d state");
+  if (hd.N != h->N || hd.S != h->S || hd.q != h->q || hd.dtype != h->dtype || hd.step < 0)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_state: the state's N, segments, q or dtype differ from the handle's");
+  const size_t ub = h->esize * h->N, hb = h->esize * static_cast<size_t>(h->S) * 2 * h->q;
+  if (hb > h->hist_bytes) {
+    cudaFree(h->hist[0]);
+    cudaFree(h->hist[1]);
+    h->hist[0] = h->hist[1] = nullptr;
+    h->hist_bytes = 0;
+    HEAT1D_CUDA(cudaMalloc(&h->hist[0], hb));
+    HEAT1D_CUDA(cudaMalloc(&h->hist[1], hb));
+    h->hist_bytes = hb;
+  }
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  HEAT1D_CUDA(cudaMemcpyAsync(h->u[h->cur], in + sizeof(hd), ub, kind, h->stream));
+  HEAT1D_CUDA(cudaMemcpyAsync(h->hist[0], in + sizeof(hd) + ub, hb, kind, h->stream));
+  if (!on_device) HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
+  if (hd.has_history) {
+    h->hist_cur = 0;
+    h->async_step = hd.step;
+  } else {
+    reset_history(h);
+  }
+  return HEAT1D_OK;
 }
 
 int heat1d_sync(heat1d_t h) {
@@ -838,7 +987,8 @@ heat1d_batch_t heat1d_batch_create(const heat1d_rod* rods, int64_t nrods, int dt
   b->T = opts.halo_steps ? opts.halo_steps : (dtype == HEAT1D_F64 ? 16 : 32);
   if (opts.spin_limit_ns > 0) b->spin_limit_ns = opts.spin_limit_ns;
   b->stall_slot = opts.stall_segment >= 0 && opts.stall_segment < INT_MAX ? static_cast<int>(opts.stall_segment) : -1;
-  if ((b->E != 4 && b->E != 8 && b->E != 16) || b->threads % 32 != 0 || b->threads < 32 ||
+  if ((b->E != 4 && b->E != 8 && b->E != 16 && !(b->E == 32 && b->esize == 4)) || b->threads % 32 != 0 ||
+      b->threads < 32 ||
       b->threads > heat1d_impl::max_tile_threads(static_cast<int>(b->esize), b->E) || b->T < 1) {
     fail(HEAT1D_ERR_INVAL, "heat1d_batch_create: elems_per_thread must be 4, 8 or 16 and block_threads a multiple "
                            "of 32 within the CTA limit");
@@ -1022,6 +1172,7 @@ static int adjoint_handle(heat1d_t h, int64_t K, const uint8_t* trace, int trace
   if (rc == HEAT1D_ERR_OOM) return fail(rc, "heat1d_adjoint: out of device memory for checkpoints");
   if (rc) return cuda_fail(cudaGetLastError(), "heat1d_adjoint");
   h->cur = 1 - h->cur;  // the state is now u(K)
+  reset_history(h);
   return HEAT1D_OK;
 }
 

@@ -48,6 +48,14 @@ struct SegmentRun {
   uint8_t* trace_out;      // device or NULL
   const uint8_t* trace_in; // device, replay only
   int stall_segment;       // -1: off
+  // Resuming an asynchronous run (checkpoint/restart): the run's step 0 is
+  // global step k0 of a longer run; hist_in (device [S][2][q], or NULL when
+  // k0 = 0) holds every segment's first and last point at global steps
+  // k0-q+1 .. k0 (oldest first), the versions a step may still read; the run
+  // writes the same for its own last q steps to hist_out (device, or NULL).
+  int64_t k0;
+  const void* hist_in;
+  void* hist_out;
 };
 
 // Arguments of one temporally blocked synchronous run streamed through HBM.
@@ -76,8 +84,10 @@ struct StreamRun {
 // FP32 tile of 16 points: its two register arrays of 16 floats and the loop
 // state did not fit 64 registers (ptxas spilled 112-324 bytes per thread in
 // the synchronous and batched kernels).
+// The FP32 tile of 32 points (two arrays of 32 floats) is limited to 256
+// threads, so that it may use up to 255 registers.
 constexpr int max_tile_threads(int elem_bytes, int E) {
-  return (elem_bytes * E > 64 || (elem_bytes == 4 && E == 16)) ? 512 : 1024;
+  return (elem_bytes == 4 && E == 32) ? 256 : ((elem_bytes * E > 64 || (elem_bytes == 4 && E == 16)) ? 512 : 1024);
 }
 // The asynchronous kernel adds its communication warps to the compute
 // threads (within the 1024-thread CTA limit).

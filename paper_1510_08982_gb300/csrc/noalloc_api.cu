@@ -156,9 +156,9 @@ extern "C" int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N,
   if (S < 1) return fail(HEAT1D_ERR_INVAL, "heat1d_run_sync_noalloc: no segments");
   const int64_t Lmin = N / S, Lmax = N / S + (N % S ? 1 : 0);
   const int esize = dtype == HEAT1D_F64 ? 8 : 4;
-  // The handle API's default halo depth (FP32 128 steps; FP64 64 on segments
-  // of 4096 points or more, else 32), at most the shortest segment; the
-  // array holds exactly that depth.
+  // The handle API's default halo depth capped at what the array holds (FP32
+  // 128 steps; FP64 64 on segments of 4096 points or more, else 32), at most
+  // the shortest segment.  The depth changes the speed, never the result.
   const int Tdef = esize == 4 ? 128 : (Lmin >= 4096 ? 64 : 32);
   const int T = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(Tdef, Lmin)));
   static_assert(kNoallocHaloBytes >= 128 * 4 && kNoallocHaloBytes >= 64 * 8, "halo buffers too small");

@@ -199,6 +199,7 @@ int launch_sync_persistent(const SegmentRun& a, int dtype, int E, int threads, c
     case 4: return f64 ? launch_sync_t<double, 4>(a, threads, st) : launch_sync_t<float, 4>(a, threads, st);
     case 8: return f64 ? launch_sync_t<double, 8>(a, threads, st) : launch_sync_t<float, 8>(a, threads, st);
     case 16: return f64 ? launch_sync_t<double, 16>(a, threads, st) : launch_sync_t<float, 16>(a, threads, st);
+    case 32: return f64 ? HEAT1D_ERR_INVAL : launch_sync_t<float, 32>(a, threads, st);
     default: return HEAT1D_ERR_INVAL;
   }
 }
@@ -210,6 +211,7 @@ int max_resident_sync(int dtype, int E, int threads) {
     case 4: return f64 ? resident_t<double, 4>(threads) : resident_t<float, 4>(threads);
     case 8: return f64 ? resident_t<double, 8>(threads) : resident_t<float, 8>(threads);
     case 16: return f64 ? resident_t<double, 16>(threads) : resident_t<float, 16>(threads);
+    case 32: return f64 ? 0 : resident_t<float, 32>(threads);
     default: return 0;
   }
 }

@@ -31,7 +31,8 @@ EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_las
            "heat1d_run_async_blocked", "heat1d_replay_blocked", "heat1d_blocked_trace_bytes", "heat1d_blocked_segments",
            "heat1d_batch_create", "heat1d_batch_run", "heat1d_batch_sync", "heat1d_batch_describe",
            "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_adjoint", "heat1d_vjp",
-           "heat1d_adjoint_batched", "heat1d_run_sync_noalloc", "heat1d_probe_fma"]
+           "heat1d_adjoint_batched", "heat1d_run_sync_noalloc", "heat1d_probe_fma", "heat1d_state_bytes",
+           "heat1d_get_state", "heat1d_set_state"]
 
 
 class Heat1dError(RuntimeError):
@@ -87,6 +88,9 @@ def load():
         "heat1d_replay_blocked": (i32, [vp, i64, vp, i32]),
         "heat1d_blocked_trace_bytes": (i64, [vp, i64]),
         "heat1d_blocked_segments": (i64, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
+        "heat1d_state_bytes": (i64, [vp]),
+        "heat1d_get_state": (i32, [vp, vp, i32]),
+        "heat1d_set_state": (i32, [vp, vp, i32]),
         "heat1d_run_sync_noalloc": (i32, [vp, vp, i64, dbl, dbl, dbl, i32, i64, i64, vp, vp]),
         "heat1d_probe_fma": (i32, [i32, i32, i64, i64, i32, vp, vp, ctypes.POINTER(i64)]),
         "heat1d_batch_create": (vp, [ctypes.POINTER(RodSpec), i64, i32, ctypes.POINTER(Opts)]),
@@ -314,6 +318,34 @@ class Heat1d:
         self._stream()
         ptr, on_dev = self._trace_ptr(trace, K, self.blocked_trace_bytes(K))
         _check(self.lib.heat1d_replay_blocked(self.h, int(K), ptr, on_dev))
+
+    def state_bytes(self) -> int:
+        return int(self.lib.heat1d_state_bytes(self.h))
+
+    def get_state(self, device=False):
+        """heat1d_get_state: the state (u and the edge history of the last q
+        steps of an asynchronous run) as a uint8 numpy array, or a CUDA
+        tensor with device=True."""
+        torch = _torch()
+        self._stream()
+        n = self.state_bytes()
+        if device:
+            buf = torch.empty(n, dtype=torch.uint8, device="cuda")
+            _check(self.lib.heat1d_get_state(self.h, ctypes.c_void_p(buf.data_ptr()), 1))
+            return buf
+        buf = np.empty(n, dtype=np.uint8)
+        _check(self.lib.heat1d_get_state(self.h, buf.ctypes.data_as(ctypes.c_void_p), 0))
+        return buf
+
+    def set_state(self, state):
+        """heat1d_set_state from a state of get_state (numpy or CUDA tensor)."""
+        torch = _torch()
+        self._stream()
+        if isinstance(state, torch.Tensor) and state.is_cuda:
+            _check(self.lib.heat1d_set_state(self.h, ctypes.c_void_p(state.contiguous().data_ptr()), 1))
+        else:
+            st = np.ascontiguousarray(state if not isinstance(state, torch.Tensor) else state.numpy(), dtype=np.uint8)
+            _check(self.lib.heat1d_set_state(self.h, st.ctypes.data_as(ctypes.c_void_p), 0))
 
     def sync(self):
         """Waits for the stream; raises on a device-side failure."""

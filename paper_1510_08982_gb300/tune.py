@@ -71,7 +71,7 @@ def batched_candidates(dtype: str):
         return [dict(elems_per_thread=e, block_threads=t, halo_steps=T)
                 for e in (4, 8) for t in (128, 256) for T in (8, 16, 32)]
     return [dict(elems_per_thread=e, block_threads=t, halo_steps=T)
-            for e in (8, 16) for t in (128, 256, 512) for T in (32, 64, 128)]
+            for e in (8, 16) for t in (128, 256, 512) for T in (64, 128, 256)]
 
 
 def stream_candidates(dtype: str):
