@@ -65,9 +65,10 @@ typedef struct heat1d_opts {
                             length q).  0: 3. */
   int32_t halo_steps;    /* T, steps advanced between two exchanges in the synchronous run
                             (overlapped halos of width T) and the block length of the blocked
-                            asynchronous run.  0: automatic (on-chip runs: FP64 64 and FP32 256, or
-                            32 and 128 when the shortest segment has fewer than 4096 points; at most
-                            the shortest segment.  Streamed runs 32 in FP64, 128 in FP32).
+                            asynchronous run.  0: automatic (on-chip runs: FP64 64, or 32 when the
+                            shortest segment has fewer than 4096 points; FP32 512 from 6144 points,
+                            256 from 4096, else 128; at most the shortest segment.  Streamed runs 32
+                            in FP64, 128 in FP32).
                             1: exchange and grid barrier after every step, as in Section 2. */
   int32_t block_threads; /* threads per CTA for the compute warps (a multiple of 32; at most 512 in
                             streamed runs, which add a loader and a releaser warp).  0: automatic. */

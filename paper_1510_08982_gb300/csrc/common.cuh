@@ -172,7 +172,10 @@ struct Window {
   static_assert(E >= 2 && E % 2 == 0, "E must be even");
   static constexpr int H = H_;            // halo points per warp side
   static constexpr int D = 32 * E - 2 * H;  // stride between warp windows
-  static_assert(H >= 1 && 2 * H <= E, "halo must fit in lanes 0 and 31");
+  // Either half a lane (the halos and the values sent for them sit in lanes
+  // 0 and 31) or a whole lane (H = E: lanes 0 and 31 are the halos, lanes 1
+  // and 30 send).
+  static_assert(H >= 1 && (2 * H <= E || H == E), "halo must be at most half a lane, or one whole lane");
   __device__ static __forceinline__ int pos(int warp, int lane, int e) { return warp * D + lane * E + e; }
   __device__ static __forceinline__ bool owner(int warp, int lane, int e, int nwarps) {
     if (lane == 0 && e < H) return warp == 0;
@@ -185,8 +188,8 @@ struct Window {
 // before every warp passed the barrier of the refresh in between).
 template <typename real, int H>
 struct WindowShared {
-  real to_right[2][32][H];  // lane 31's positions [E-2H, E-H): the next warp's left halo
-  real to_left[2][32][H];   // lane 0's positions [H, 2H): the previous warp's right halo
+  real to_right[2][32][H];  // window positions [32E-2H, 32E-H): the next warp's left halo
+  real to_left[2][32][H];   // window positions [H, 2H): the previous warp's right halo
 };
 
 // How a warp steps: every point updated; the first and/or last slot of some
@@ -302,13 +305,17 @@ __device__ __forceinline__ void warp_step_any(int mode, real (&v)[E], unsigned f
 template <typename real, int E, int H, bool kOr = true>
 __device__ __forceinline__ bool warp_refresh(real (&v)[E], WindowShared<real, H>& sh, int parity, int warp, int lane,
                                              int nwarps, unsigned nthreads, bool flag) {
-  if (lane == 31) {
+  // The next warp's left halo is this warp's window positions [32E-2H,
+  // 32E-H); the previous warp's right halo is positions [H, 2H).  With
+  // H <= E/2 those are in lanes 31 and 0, with H = E they are lanes 30 and 1.
+  constexpr bool kLane = (H == E);
+  if (lane == (kLane ? 30 : 31)) {
 #pragma unroll
-    for (int i = 0; i < H; ++i) sh.to_right[parity][warp][i] = v[E - 2 * H + i];
+    for (int i = 0; i < H; ++i) sh.to_right[parity][warp][i] = v[kLane ? i : E - 2 * H + i];
   }
-  if (lane == 0) {
+  if (lane == (kLane ? 1 : 0)) {
 #pragma unroll
-    for (int i = 0; i < H; ++i) sh.to_left[parity][warp][i] = v[H + i];
+    for (int i = 0; i < H; ++i) sh.to_left[parity][warp][i] = v[kLane ? i : H + i];
   }
   bool any = false;
   if (kOr)

@@ -171,12 +171,16 @@ int configure(heat1d* h, const heat1d_opts& o) {
   // On-chip synchronous runs take halos from the neighbouring segment only,
   // so their T is at most the shortest segment (clamped unless on-chip mode
   // was asked for explicitly).
-  // Default depth (measured best on GB300): FP32 256 steps on segments of
-  // 4096 points or more (128 on shorter ones), where a step costs little and
-  // the exchange (about 5 us a block on the 2^20-point rod) weighs more; FP64
-  // 64 steps on segments of 4096 points or more and 32 on shorter ones, where
-  // the halo's redundant arithmetic (2T per segment) weighs more.
-  int T = o.halo_steps ? o.halo_steps : (h->esize == 4 ? (Lmin >= 4096 ? 256 : 128) : (Lmin >= 4096 ? 64 : 32));
+  // Default depth (measured best on GB300): FP32 512 steps on segments of
+  // 6144 points or more, 256 from 4096, else 128 -- a step costs little and
+  // an exchange (about 5 us a block on the 2^20-point rod) weighs more than
+  // the halo's redundant points (on that rod: 6.54e12 updates/s at T = 128,
+  // 7.09e12 at 256, 7.33e12 at 512); FP64 64 steps on segments of 4096
+  // points or more and 32 on shorter ones, where the redundant arithmetic
+  // weighs more (1.80e11 at 32, 1.815e11 at 64, 1.76e11 at 128).
+  int T = o.halo_steps ? o.halo_steps
+                       : (h->esize == 4 ? (Lmin >= 6144 ? 512 : (Lmin >= 4096 ? 256 : 128))
+                                        : (Lmin >= 4096 ? 64 : 32));
   if (T > Lmin) {
     if (o.halo_steps && o.sync_mode == 1)
       return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: halo_steps exceeds the shortest segment");
@@ -198,7 +202,7 @@ int configure(heat1d* h, const heat1d_opts& o) {
   if (sE % vn != 0 && o.sync_mode == 2)
     return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: streamed runs need elems_per_thread a multiple of 16 bytes");
   const int64_t W =
-      heat1d_impl::window_width(sthreads / 32, sE, heat1d_impl::sync_window_halo(static_cast<int>(h->esize), sE)) - 2 * Th;
+      heat1d_impl::window_width(sthreads / 32, sE, heat1d_impl::stream_window_halo(static_cast<int>(h->esize), sE)) - 2 * Th;
   // (the streamed kernel adds one producer warp to the compute threads)
   if (o.sync_mode == 2 && (W < vn || sthreads > heat1d_impl::kStreamMaxThreads))
     return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: streamed tile too small for halo_steps, or too many threads");

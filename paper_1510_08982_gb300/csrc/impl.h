@@ -98,12 +98,20 @@ constexpr int max_async_threads(int elem_bytes, int E) {
 // Warp windows (common.cuh): warp w covers 32E positions starting at w*D,
 // D = 32E - 2H, where H (halo points per warp side = steps between two
 // refreshes) trades redundant arithmetic (2H/32E) against barriers (one per
-// H steps).  The synchronous kernels use H = E/2 in FP32 and E/4 in FP64
-// (at least 1): FP64 arithmetic is costly, so less redundancy is worth more
-// barriers.  The asynchronous kernel uses H = E/2: its edge warps must not be
+// H steps).  The synchronous kernels use H = E/2 in FP32 (H = E for E = 16
+// on chip) and E/4 in FP64 (at least 1): FP64 arithmetic is costly, so less
+// redundancy is worth more barriers.  The asynchronous kernel uses H = E/2: its edge warps must not be
 // held back by frequent barriers.  A CTA of nw compute warps covers
 // nw*D + 2H positions.
-constexpr int sync_window_halo(int elem_bytes, int E) { return elem_bytes == 8 ? (E >= 4 ? E / 4 : 1) : E / 2; }
+// On chip, FP32 tiles of 16 points per thread take H = 16: whole lanes 0 and
+// 31 are the halos, refreshed every 16 steps (measured: an H-step run costs
+// about 100 instructions of loop and refresh per warp; half as many refreshes
+// outweigh 3 % more redundant points).  Streamed tiles keep H = E/2: their
+// passes are often no longer than H, so a wider halo only adds redundancy.
+constexpr int sync_window_halo(int elem_bytes, int E) {
+  return elem_bytes == 8 ? (E >= 4 ? E / 4 : 1) : (E == 16 ? 16 : E / 2);
+}
+constexpr int stream_window_halo(int elem_bytes, int E) { return elem_bytes == 8 ? (E >= 4 ? E / 4 : 1) : E / 2; }
 constexpr int async_window_halo(int /*elem_bytes*/, int E) { return E / 2; }
 constexpr int64_t window_width(int64_t nwarps, int E, int H) { return nwarps * (32 * E - 2 * H) + 2 * H; }
 constexpr int64_t window_warps(int64_t positions, int E, int H) {

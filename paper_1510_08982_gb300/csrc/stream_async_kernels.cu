@@ -112,7 +112,7 @@ __global__ void stream_async_setup_kernel(StreamAsyncRun a) {
 template <typename real, int E>
 __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_async_kernel(StreamAsyncRun a) {
   using V = typename Vec16<real>::type;
-  using Win = Window<E, sync_window_halo(sizeof(real), E)>;
+  using Win = Window<E, stream_window_halo(sizeof(real), E)>;
   constexpr int VN = Vec16<real>::n;
   static_assert(E % VN == 0, "E must be a multiple of the 16-byte vector width");
   extern __shared__ __align__(128) unsigned char dyn[];

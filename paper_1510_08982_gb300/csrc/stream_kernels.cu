@@ -69,7 +69,7 @@ __device__ bool wait_tile(const int* done, int want, int* status, int64_t limit_
 template <typename real, int E>
 __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_tma_kernel(StreamRun a) {
   using V = typename Vec16<real>::type;
-  using Win = Window<E, sync_window_halo(sizeof(real), E)>;
+  using Win = Window<E, stream_window_halo(sizeof(real), E)>;
   constexpr int VN = Vec16<real>::n;
   static_assert(E % VN == 0, "E must be a multiple of the 16-byte vector width");
   extern __shared__ __align__(128) unsigned char dyn[];
