@@ -1,29 +1,39 @@
 // async_kernels.cu -- the asynchronous run of Section 3, Eq. (eqn:async), and
-// its exact replay, as one persistent cooperative launch with no barrier
-// between CTAs.
+// its exact replay, as one persistent launch with no barrier between CTAs.
 //
 // One CTA owns one segment (a PE of Fig. 1).  Its compute warps hold the
 // segment plus one halo point per side in registers and step with no
-// asynchrony inside the CTA (Section 3).  Three extra warps per CTA are the
-// "network": one publishes the segment's two edge values of every version to
-// global rings (release store of the segment's version counter), one per
-// neighbour copies that neighbour's published versions into a ring in shared
-// memory (the buffer of Section 3 that keeps the q most recent values
-// received).  Separate warps let the publish fence and the two neighbours'
-// L2 round trips overlap.
+// asynchrony inside the CTA (Section 3).
 //
-// At step k the compute warp holding a halo takes, from that local buffer,
-// the newest neighbour version v <= k; it waits only while v < k-q+1 (bounded
-// delay, k* in {k, ..., k-q+1}).  It records d = k - v for the trace.  In
-// replay mode it waits for, and takes, exactly v = k - min(d, k) from the
-// given trace.  Only the two edge warps (halo reads, edge hand-offs) stop
-// after every step; the other compute warps advance each run of refresh steps
-// at once, and all meet at the warp-halo refresh.
+// Tagged slots.  Every edge value travels with its version: each 32-bit half
+// of the value shares a 64-bit word with the version number, so a reader that
+// finds the version it wants in every word of a slot holds that version's
+// value.  A slot caught in the middle of an update simply does not match yet;
+// no release/acquire pair, no fence and no version counter sit on the path.
+// The thread that computes a segment's first (last) point writes each new
+// version into the ring of R slots that its left (right) neighbour reads:
+//  - a neighbour in the same thread-block cluster: straight into that CTA's
+//    shared-memory ring (distributed shared memory);
+//  - any other neighbour: into the segment's ring in global memory, which a
+//    puller warp of the neighbour mirrors into its own shared-memory ring.
+// The shared-memory ring is the buffer of Section 3 that keeps the most
+// recent values received.
 //
-// Flow control: a segment cannot start step k until both neighbours have
-// published version k-q+1, so no two neighbours drift more than q steps
-// apart, and a ring of R >= 2q versions is never overwritten while a reader
-// may still need the slot.
+// At step k the compute thread holding a halo takes, from its shared ring,
+// the newest neighbour version v <= k; it waits only while no v >= k-q+1 is
+// there (bounded delay, k* in {k, ..., k-q+1}), and records d = k - v for the
+// trace.  In replay mode it waits for, and takes, exactly v = k - min(d, k).
+// Only the two edge warps stop after every step; the other compute warps
+// advance each run of refresh steps at once, and all meet at the warp-halo
+// refresh.
+//
+// Flow control and ring safety: a segment cannot start step k until both
+// neighbours have produced version k-q+1, so neighbours drift at most q-1
+// steps apart and a writer overwrites the slot of version v only once its
+// reader needs versions above v (R >= 2q).  The reader's own loads come
+// first: the value it hands on at version k+1 is computed (its edge point's
+// update) from the halo it read at step k, so no neighbour can see that
+// version before those reads are done.
 #include <algorithm>
 
 #include "common.cuh"
@@ -34,19 +44,95 @@ using namespace heat1d_dev;
 
 namespace {
 
+// A value as 32-bit words, each carried in a tagged slot word.
+template <typename real>
+struct Tag;
+template <>
+struct Tag<double> {
+  static constexpr int W = 2;
+  __device__ static __forceinline__ void split(double x, uint32_t (&b)[2]) {
+    const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
+    b[0] = static_cast<uint32_t>(u);
+    b[1] = static_cast<uint32_t>(u >> 32);
+  }
+  __device__ static __forceinline__ double join(const uint32_t (&b)[2]) {
+    return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(b[1]) << 32) | b[0]));
+  }
+};
+template <>
+struct Tag<float> {
+  static constexpr int W = 1;
+  __device__ static __forceinline__ void split(float x, uint32_t (&b)[1]) { b[0] = __float_as_uint(x); }
+  __device__ static __forceinline__ float join(const uint32_t (&b)[1]) { return __uint_as_float(b[0]); }
+};
+
+// Slot word: version in the high half, 32 value bits in the low half.  The
+// empty word (also the byte pattern the host clears the global rings with)
+// carries version 0x80808080, below any version a run uses (>= -254).
+constexpr unsigned long long kEmptySlot = 0x8080808080808080ull;
+__device__ __forceinline__ unsigned long long slot_word(int ver, uint32_t bits) {
+  return (static_cast<unsigned long long>(static_cast<uint32_t>(ver)) << 32) | bits;
+}
+__device__ __forceinline__ int slot_ver(unsigned long long w) { return static_cast<int>(static_cast<uint32_t>(w >> 32)); }
+
+// Slot words in this CTA's shared memory: written by a puller of this CTA or
+// by a neighbour CTA of the cluster, so both sides use cluster scope.
+__device__ __forceinline__ unsigned long long ld_slot_shared(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.cluster.shared::cta.b64 %0, [%1];"
+               : "=l"(v)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p)))
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_slot_shared(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.cluster.shared::cta.b64 [%0], %1;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))),
+               "l"(v)
+               : "memory");
+}
+// A slot word in a neighbour CTA's shared memory (an address from mapa).
+__device__ __forceinline__ void st_slot_cluster(uint32_t addr, unsigned long long v) {
+  asm volatile("st.relaxed.cluster.shared::cluster.b64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+// Slot words in global memory (read and written at L2).
+__device__ __forceinline__ unsigned long long ld_slot_global(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_slot_global(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Thread-block clusters.
+__device__ __forceinline__ uint32_t cluster_addr(const void* local, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(local))), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA of the cluster (none has exited before it).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
 template <typename real, int E>
 struct AsyncShared {
   WindowShared<real, async_window_halo(sizeof(real), E)> win;
-  real lring[kMaxRing];  // left neighbour's right-edge values, version v at v & (R-1)
-  real rring[kMaxRing];  // right neighbour's left-edge values
-  real own_l[kMaxRing];  // this segment's first point per version, for the comm warp
+  // Tagged slots [R][W]: version v at slot v & (R-1).
+  unsigned long long lin[kMaxRing * Tag<real>::W];  // the left neighbour's last point
+  unsigned long long rin[kMaxRing * Tag<real>::W];  // the right neighbour's first point
+  real own_l[kMaxRing];  // this segment's first point per version (for the edge history)
   real own_r[kMaxRing];  // this segment's last point per version
-  int lavail, ravail;    // newest neighbour version held in lring / rring (-1: none)
-  int own_l_ver, own_r_ver;  // newest own version handed to the comm warp
-  int compute_done;          // 1: finished, 2: aborted
+  unsigned long long dst[2];  // where the first [0] and last [1] points go (see hand_off)
+  int compute_done;      // 1: finished, 2: aborted
 };
-
-
 
 // v[idx] for a run-time idx, by a tree of selects on the bits of idx (no
 // local-memory array, log2(E) levels).
@@ -64,130 +150,96 @@ __device__ __forceinline__ real pick_slot(const real (&v)[E], int idx) {
   return t[0];
 }
 
-// Waits for the neighbour version this step needs and returns its value.
+// Version v of a ring in this CTA's shared memory, if every word of its slot
+// carries v.
+template <typename real>
+__device__ __forceinline__ bool read_slot(const unsigned long long* ring, int R, int v, real& x) {
+  constexpr int W = Tag<real>::W;
+  const unsigned long long* p = ring + static_cast<size_t>(v & (R - 1)) * W;
+  uint32_t b[W];
+  bool ok = true;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const unsigned long long u = ld_slot_shared(p + w);
+    ok = ok && slot_ver(u) == v;
+    b[w] = static_cast<uint32_t>(u);
+  }
+  if (ok) x = Tag<real>::join(b);
+  return ok;
+}
+
+// Waits for the neighbour version this step reads and returns its value.
 // Returns false if the wait ran out or the run failed elsewhere.
 template <typename real>
-__device__ __forceinline__ bool fetch_halo(const SegmentRun& a, const int* avail, const real* ring, int k,
-                                           const uint8_t* trace_in, uint8_t* trace_out, size_t tidx, int d_replay,
-                                           real& value) {
+__device__ __forceinline__ bool fetch_halo(const SegmentRun& a, const unsigned long long* ring, int k, bool replay,
+                                           uint8_t* trace_out, size_t tidx, int d_replay, real& value) {
   // Step k of this launch is global step k0 + k of a resumed run; no read
   // reaches before global step 0 (a delay is clamped to the global step).
   const int kb = a.k0 < a.q ? static_cast<int>(a.k0) : a.q;
-  int need;
-  if (trace_in) {
+  int lo, hi;  // versions this step may take; the newest present wins
+  if (replay) {
     if (d_replay >= a.q) {
       raise_status(a.status, HEAT1D_ERR_TRACE);
       return false;
     }
-    need = k - min(d_replay, k + kb);
+    lo = hi = k - min(d_replay, k + kb);
   } else {
-    need = max(k - a.q + 1, -kb);
+    hi = k;
+    lo = max(k - a.q + 1, -kb);
   }
-  int V = ld_acquire_cta_shared(avail);
-  if (V < need) {
-    const uint64_t t0 = global_timer_ns();
-    unsigned spins = 0;
-    while ((V = ld_acquire_cta_shared(avail)) < need) {
-      if ((++spins & 63u) == 0) {
-        if (status_failed(a.status)) return false;
-        if (static_cast<int64_t>(global_timer_ns() - t0) > a.spin_limit_ns) {
-          raise_status(a.status, HEAT1D_ERR_TIMEOUT);
-          return false;
-        }
+  uint64_t t0 = 0;
+  unsigned spins = 0;
+  int v;
+  while (true) {
+    for (v = hi; v >= lo; --v)
+      if (read_slot<real>(ring, a.R, v, value)) break;
+    if (v >= lo) break;
+    if (spins == 0) t0 = global_timer_ns();
+    if ((++spins & 63u) == 0) {
+      if (status_failed(a.status)) return false;
+      if (static_cast<int64_t>(global_timer_ns() - t0) > a.spin_limit_ns) {
+        raise_status(a.status, HEAT1D_ERR_TIMEOUT);
+        return false;
       }
     }
   }
-  const int vsel = trace_in ? need : min(V, k);
-  value = ring[vsel & (a.R - 1)];
-  if (trace_out) trace_out[tidx] = static_cast<uint8_t>(k - vsel);
+  if (trace_out) trace_out[tidx] = static_cast<uint8_t>(k - v);
   return true;
 }
 
-// The three communication warps (one thread each does the work).
-
-// Publisher: pushes every new version of the segment's two edge values to its
-// global rings, then release-stores the segment's version counter.
-template <typename real, int E>
-__device__ void publish_loop(const SegmentRun& a, AsyncShared<real, E>& sh, int s) {
+// Puller (a whole warp): mirrors a neighbour's ring in global memory into
+// this CTA's shared ring.  Lane l looks after slots l, l+32, ...; a slot is
+// copied when all its words carry one version newer than the one held.
+template <typename real>
+__device__ void pull_loop(const SegmentRun& a, const int* compute_done, const unsigned long long* g,
+                          unsigned long long* loc, int lane) {
+  constexpr int W = Tag<real>::W;
   const int R = a.R;
-  const int K = static_cast<int>(a.K);
-  real* rings = static_cast<real*>(a.rings);
-  real* my_l = rings + (static_cast<size_t>(s) * 2 + 0) * R;
-  real* my_r = rings + (static_cast<size_t>(s) * 2 + 1) * R;
-  int* my_prog = a.prog + static_cast<size_t>(s) * kProgStride;
-  const bool stalled = s == a.stall_segment;
-  const bool replay = a.trace_in != nullptr;
-  int pub = -1;
   uint64_t t_idle = global_timer_ns();
   unsigned spins = 0;
   while (true) {
-    const int w = min(ld_acquire_cta_shared(&sh.own_l_ver), ld_acquire_cta_shared(&sh.own_r_ver));
-    if (!stalled && w > pub) {
-      for (int x = max(pub + 1, w - R + 1); x <= w; ++x) {
-        const int j = x & (R - 1);
-        st_cg(my_l + j, sh.own_l[j]);
-        st_cg(my_r + j, sh.own_r[j]);
-      }
-      st_release_gpu(my_prog, w);
-      pub = w;
-      t_idle = global_timer_ns();
-      continue;
-    }
-    const int done = ld_acquire_cta_shared(&sh.compute_done);
-    if (done == 2 || (done == 1 && (pub >= K || stalled))) break;
-    // Back off between polls: a tight shared-memory spin takes issue and
-    // shared-memory slots from the compute warps.  A replay waits on exact
-    // versions, so its publisher naps less (measured on the 2^20-point rod:
-    // free runs are fastest at 256 ns, replays at 64 ns).
-    __nanosleep(replay ? 64 : 256);
-    if ((++spins & 63u) == 0) {
-      if (status_failed(a.status)) break;
-      if (static_cast<int64_t>(global_timer_ns() - t_idle) > a.spin_limit_ns) {
-        raise_status(a.status, HEAT1D_ERR_TIMEOUT);
-        break;
+    bool moved = false;
+    for (int j = lane; j < R; j += 32) {
+      unsigned long long w[W];
+#pragma unroll
+      for (int x = 0; x < W; ++x) w[x] = ld_slot_global(g + static_cast<size_t>(j) * W + x);
+      const int v = slot_ver(w[0]);
+      bool same = true;
+#pragma unroll
+      for (int x = 1; x < W; ++x) same = same && slot_ver(w[x]) == v;
+      if (same && v > slot_ver(ld_slot_shared(loc + static_cast<size_t>(j) * W))) {
+#pragma unroll
+        for (int x = 0; x < W; ++x) st_slot_shared(loc + static_cast<size_t>(j) * W + x, w[x]);
+        moved = true;
       }
     }
-  }
-}
-
-// Puller (a whole warp): copies each new version of one neighbour's facing
-// edge value from its global ring into the local ring, then release-stores
-// the newest version held (the buffer of Section 3 that keeps the most recent
-// received values).  Lane 0 acquires the neighbour's version counter; after a
-// warp barrier (which orders that acquire before the other lanes' loads) the
-// lanes copy the new versions in parallel, so one pass costs two L2 round
-// trips however many versions arrived.
-template <typename real, int E>
-__device__ void pull_loop(const SegmentRun& a, AsyncShared<real, E>& sh, const int* nprog, const real* nring,
-                          real* lring, int* avail, int lane, const real* nhist) {
-  const int R = a.R;
-  int seen = -1;
-  if (nhist) {
-    // A resumed run: the neighbour's edge value at the last q steps before
-    // this launch (versions -q+1 .. 0) is already known.
-    for (int j = lane; j < a.q; j += 32) lring[(j - a.q + 1) & (R - 1)] = nhist[j];
-    __syncwarp();
-    if (lane == 0) st_release_cta_shared(avail, 0);
-    seen = 0;
-  }
-  uint64_t t_idle = global_timer_ns();
-  unsigned spins = 0;
-  while (true) {
-    int P = 0;
-    if (lane == 0) P = ld_acquire_gpu(nprog);
-    __syncwarp();
-    P = __shfl_sync(kFullMask, P, 0);
-    if (P > seen) {
-      for (int x = max(seen + 1, P - R + 1) + lane; x <= P; x += 32) lring[x & (R - 1)] = ld_cg(nring + (x & (R - 1)));
-      __syncwarp();
-      if (lane == 0) st_release_cta_shared(avail, P);
-      seen = P;
+    if (__any_sync(kFullMask, moved)) {
       t_idle = global_timer_ns();
       continue;
     }
     int stop = 0;
     if (lane == 0) {
-      if (ld_acquire_cta_shared(&sh.compute_done)) {
+      if (ld_acquire_cta_shared(compute_done)) {
         stop = 1;  // no more reads needed
       } else if ((++spins & 63u) == 0) {
         if (status_failed(a.status)) {
@@ -202,258 +254,355 @@ __device__ void pull_loop(const SegmentRun& a, AsyncShared<real, E>& sh, const i
   }
 }
 
+// Where one edge value of this segment goes, as one word: bit 63 set and the
+// neighbour's shared ring address (mapa) in the low half for a neighbour in
+// the cluster; else the address of this segment's ring in global memory; 0
+// for nowhere (no neighbour on that side, or a stalled segment).  Kept in
+// shared memory: the edge threads read it once per step, off their
+// registers.
+constexpr unsigned long long kRemoteDst = 1ull << 63;
+
+template <typename real>
+__device__ __forceinline__ void hand_off(unsigned long long dst, int R, int ver, real x) {
+  constexpr int W = Tag<real>::W;
+  if (!dst) return;
+  uint32_t b[W];
+  Tag<real>::split(x, b);
+  const int j = ver & (R - 1);
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const unsigned long long u = slot_word(ver, b[w]);
+    if (dst & kRemoteDst)
+      st_slot_cluster(static_cast<uint32_t>(dst) + static_cast<uint32_t>((j * W + w) * sizeof(unsigned long long)), u);
+    else
+      st_slot_global(reinterpret_cast<unsigned long long*>(dst) + static_cast<size_t>(j) * W + w, u);
+  }
+}
+
 template <typename real, int E>
 __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_persistent_kernel(SegmentRun a) {
   using Win = Window<E, async_window_halo(sizeof(real), E)>;
   constexpr int kRefresh = Win::H;  // steps between two halo refreshes
+  constexpr int W = Tag<real>::W;
   __shared__ AsyncShared<real, E> sh;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nwc = (blockDim.x >> 5) - kCommWarps;  // compute warps; the last three communicate
+  const int nwc = (blockDim.x >> 5) - kCommWarps;  // compute warps; the last two pull
   const unsigned nthreads_c = static_cast<unsigned>(nwc) * 32u;
-  if (tid == 0) {
-    sh.lavail = -1;
-    sh.ravail = -1;
-    sh.own_l_ver = -1;
-    sh.own_r_ver = -1;
-    sh.compute_done = 0;
+  const int R = a.R;
+  const int sl = s > 0 ? s - 1 : (a.periodic ? a.S - 1 : -1);  // neighbours (ring when periodic)
+  const int sr = s + 1 < a.S ? s + 1 : (a.periodic ? 0 : -1);
+  // Neighbours in this CTA's cluster: a 1-D grid in clusters of C consecutive
+  // CTAs (rank = s mod C); on the periodic ring the two ends only when one
+  // cluster holds every segment.
+  const int C = a.cluster;
+  const unsigned rank = C > 1 ? cluster_rank() : 0u;
+  const bool l_intra = C > 1 && sl >= 0 && (rank > 0 || C == a.S);
+  const bool r_intra = C > 1 && sr >= 0 && (static_cast<int>(rank) + 1 < C || C == a.S);
+  unsigned long long* rings = static_cast<unsigned long long*>(a.rings);  // [S][2][R][W]: side 0 first point, 1 last
+
+  for (int i = tid; i < R * W; i += blockDim.x) {
+    sh.lin[i] = kEmptySlot;
+    sh.rin[i] = kEmptySlot;
+  }
+  if (tid == 0) sh.compute_done = 0;
+  __syncthreads();
+  if (a.hist_in) {
+    // A resumed run: the neighbours' edge values at the last q steps before
+    // this launch (versions -q+1 .. 0).  History layout [S][2][q]: side 0 a
+    // segment's first point, side 1 its last point, oldest first.
+    const real* hist = static_cast<const real*>(a.hist_in);
+    for (int i = tid; i < 2 * a.q; i += blockDim.x) {
+      const bool left = i < a.q;
+      const int j = left ? i : i - a.q;
+      const int nb = left ? sl : sr;
+      if (nb < 0) continue;
+      const int ver = j - a.q + 1;
+      uint32_t b[W];
+      Tag<real>::split(hist[(static_cast<size_t>(nb) * 2 + (left ? 1 : 0)) * a.q + j], b);
+      unsigned long long* ring = left ? sh.lin : sh.rin;
+#pragma unroll
+      for (int w = 0; w < W; ++w) ring[(ver & (R - 1)) * W + w] = slot_word(ver, b[w]);
+    }
   }
   __syncthreads();
+  // No CTA of the cluster may write into a neighbour before that neighbour
+  // has cleared its rings.
+  if (C > 1) cluster_sync_all();
 
   if (warp >= nwc) {
-    real* rings = static_cast<real*>(a.rings);
-    const int sl = s > 0 ? s - 1 : (a.periodic ? a.S - 1 : -1);  // neighbours (ring when periodic)
-    const int sr = s + 1 < a.S ? s + 1 : (a.periodic ? 0 : -1);
-    if (warp == nwc) {
-      if (lane == 0) publish_loop<real, E>(a, sh, s);
-    } else {
-      // warp nwc+1 pulls the left neighbour's right edge, warp nwc+2 the
-      // right neighbour's left edge
-      const bool from_left = warp == nwc + 1;
-      const int nb = from_left ? sl : sr;
-      // history layout [S][2][q]: side 0 the first point, side 1 the last point
-      const real* nhist = (nb >= 0 && a.hist_in)
-                              ? static_cast<const real*>(a.hist_in) + (static_cast<size_t>(nb) * 2 + (from_left ? 1 : 0)) * a.q
-                              : nullptr;
-      if (nb >= 0)
-        pull_loop<real, E>(a, sh, a.prog + static_cast<size_t>(nb) * kProgStride,
-                           rings + (static_cast<size_t>(nb) * 2 + (from_left ? 1 : 0)) * a.R,
-                           from_left ? sh.lring : sh.rring, from_left ? &sh.lavail : &sh.ravail, lane, nhist);
-    }
-    return;
-  }
+    // warp nwc mirrors the left neighbour's last point, warp nwc+1 the right
+    // neighbour's first point (unless that neighbour is in the cluster and
+    // writes here itself)
+    const bool from_left = warp == nwc;
+    const int nb = from_left ? sl : sr;
+    if (nb >= 0 && !(from_left ? l_intra : r_intra))
+      pull_loop<real>(a, &sh.compute_done, rings + (static_cast<size_t>(nb) * 2 + (from_left ? 1 : 0)) * R * W,
+                      from_left ? sh.lin : sh.rin, lane);
+  } else {
+    const int64_t N = a.N;
+    const int64_t a0 = a.seg_off[s];
+    const int L = static_cast<int>(a.seg_off[s + 1] - a0);
+    const int K = static_cast<int>(a.K);
+    const int S = a.S;
+    const real c1 = kparam<real>(a.c1, a.c1_f), cN = kparam<real>(a.cN, a.cN_f);
+    const Coef<real> coef{kparam<real>(a.r, a.r_f), kparam<real>(a.one, a.one_f)};  // one = 1 at run time
+    const real* __restrict__ uin = static_cast<const real*>(a.u_in);
+    real* __restrict__ uout = static_cast<real*>(a.u_out);
+    const bool periodic = a.periodic != 0;
+    const bool has_left = s > 0 || periodic, has_right = s + 1 < S || periodic;
 
-  const int64_t N = a.N;
-  const int64_t a0 = a.seg_off[s];
-  const int L = static_cast<int>(a.seg_off[s + 1] - a0);
-  const int K = static_cast<int>(a.K);
-  const int S = a.S;
-  const real c1 = kparam<real>(a.c1, a.c1_f), cN = kparam<real>(a.cN, a.cN_f);
-  const Coef<real> coef{kparam<real>(a.r, a.r_f), kparam<real>(a.one, a.one_f)};  // one = 1 at run time
-  const real* __restrict__ uin = static_cast<const real*>(a.u_in);
-  real* __restrict__ uout = static_cast<real*>(a.u_out);
-  const bool periodic = a.periodic != 0;
-  const bool has_left = s > 0 || periodic, has_right = s + 1 < S || periodic;
-
-  // Position p holds global point a0 - 1 + p: positions 0 and L+1 are the
-  // halos, written from the neighbours' versions before every step.  The
-  // Dirichlet ends are points end_lo and end_hi; on the periodic ring they are
-  // moved out of reach (every point is updated).
-  const int64_t end_lo = periodic ? -2 : 0, end_hi = periodic ? N + 1 : N - 1;
-  real v[E];
-  unsigned fixed = 0;
-  int e_first = -1, e_last = -1, e_rh = -1;  // slots of this thread holding positions 1, L (owners) and L+1
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int p = Win::pos(warp, lane, e);
-    const int64_t g = a0 - 1 + p;
-    real x = static_cast<real>(0);
-    if (p >= 1 && p <= L) x = uin[g];
-    if (g == end_lo) x = c1;
-    if (g == end_hi) x = cN;
-    v[e] = x;
-    // Only points outside the rod and the Dirichlet ends are held.  The halo
-    // positions 0 and L+1 are written before every step that reads them, and
-    // positions past L+1 reach no point of the segment, so those warps can
-    // step without the per-point selects of the masked mode.
-    if (g <= end_lo || g >= end_hi) fixed |= 1u << e;
-    const bool own = Win::owner(warp, lane, e, nwc);
-    if (p == 1 && own) e_first = e;
-    if (p == L && own) e_last = e;
-    // the copy of position L+1 in the same warp as position L's owner
-    if (p == L + 1 && ((e > 0 && Win::owner(warp, lane, e - 1, nwc)) ||
-                       (e == 0 && lane > 0 && Win::owner(warp, lane - 1, E - 1, nwc))))
-      e_rh = e;
-  }
-  const int mode = tile_mode<E>(fixed);
-  real* snap = static_cast<real*>(a.snap);
-  if (snap) {  // row 0: the state at step 0
+    // Position p holds global point a0 - 1 + p: positions 0 and L+1 are the
+    // halos, written from the neighbours' versions before every step.  The
+    // Dirichlet ends are points end_lo and end_hi; on the periodic ring they
+    // are moved out of reach (every point is updated).
+    const int64_t end_lo = periodic ? -2 : 0, end_hi = periodic ? N + 1 : N - 1;
+    real v[E];
+    unsigned fixed = 0;
+    int e_first = -1, e_last = -1, e_rh = -1;  // slots of this thread holding positions 1, L (owners) and L+1
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
-      if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) snap[a0 - 1 + p] = v[e];
+      const int64_t g = a0 - 1 + p;
+      real x = static_cast<real>(0);
+      if (p >= 1 && p <= L) x = uin[g];
+      if (g == end_lo) x = c1;
+      if (g == end_hi) x = cN;
+      v[e] = x;
+      // Only points outside the rod and the Dirichlet ends are held.  The
+      // halo positions 0 and L+1 are written before every step that reads
+      // them, and positions past L+1 reach no point of the segment, so those
+      // warps can step without the per-point selects of the masked mode.
+      if (g <= end_lo || g >= end_hi) fixed |= 1u << e;
+      const bool own = Win::owner(warp, lane, e, nwc);
+      if (p == 1 && own) e_first = e;
+      if (p == L && own) e_last = e;
+      // the copy of position L+1 in the same warp as position L's owner
+      if (p == L + 1 && ((e > 0 && Win::owner(warp, lane, e - 1, nwc)) ||
+                         (e == 0 && lane > 0 && Win::owner(warp, lane - 1, E - 1, nwc))))
+        e_rh = e;
     }
-  }
-  const bool left_reader = has_left && warp == 0 && lane == 0;  // position 0 is (warp 0, lane 0, slot 0)
-  const bool right_reader = has_right && e_rh >= 0;
-
-  // Version 0 of the edges goes to the comm warp.
-  if (e_first >= 0) {
+    const int mode = tile_mode<E>(fixed);
+    real* snap = static_cast<real*>(a.snap);
+    if (snap) {  // row 0: the state at step 0
 #pragma unroll
-    for (int e = 0; e < E; ++e)
-      if (e == e_first) sh.own_l[0] = v[e];
-    st_release_cta_shared(&sh.own_l_ver, 0);
-  }
-  if (e_last >= 0) {
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-      if (e == e_last) sh.own_r[0] = v[e];
-    st_release_cta_shared(&sh.own_r_ver, 0);
-  }
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) snap[a0 - 1 + p] = v[e];
+      }
+    }
+    const bool left_reader = has_left && warp == 0 && lane == 0;  // position 0 is (warp 0, lane 0, slot 0)
+    const bool right_reader = has_right && e_rh >= 0;
 
-  const uint8_t* trace_in = a.trace_in;
-  uint8_t* trace_out = a.trace_out;
-  // S-1 boundaries (S on the periodic ring, boundary b joining b and b+1 mod S)
-  const size_t tstride = static_cast<size_t>(periodic ? S : S - 1) * 2;
-  const size_t tl = has_left ? static_cast<size_t>((s + S - 1) % S) * 2 + 1 : 0;  // side 1 of boundary s-1
-  const size_t tr = static_cast<size_t>(s) * 2 + 0;                               // side 0 of boundary s
-  int dl_next = 0, dr_next = 0;
-  if (trace_in && K > 0) {
-    if (left_reader) dl_next = __ldg(trace_in + tl);
-    if (right_reader) dr_next = __ldg(trace_in + tr);
-  }
+    // Where this segment's first and last points go (a stalled segment hands
+    // nothing on): the left neighbour reads the first point, the right one
+    // the last.
+    const bool stalled = s == a.stall_segment;
+    if (e_first >= 0) {
+      unsigned long long d = 0;
+      if (!stalled && sl >= 0)
+        d = l_intra ? kRemoteDst | cluster_addr(sh.rin, rank == 0 ? static_cast<unsigned>(C - 1) : rank - 1)
+                    : reinterpret_cast<unsigned long long>(rings + (static_cast<size_t>(s) * 2 + 0) * R * W);
+      sh.dst[0] = d;
+    }
+    if (e_last >= 0) {
+      unsigned long long d = 0;
+      if (!stalled && sr >= 0)
+        d = r_intra ? kRemoteDst | cluster_addr(sh.lin, static_cast<int>(rank) + 1 == C ? 0u : rank + 1)
+                    : reinterpret_cast<unsigned long long>(rings + (static_cast<size_t>(s) * 2 + 1) * R * W);
+      sh.dst[1] = d;
+    }
 
-  // Only the warps that read a halo or hand an edge to the publisher need to
-  // stop after every step.  The others advance each run of kRefresh steps
-  // with the two-array step (no per-step checks, no register rotation); the
-  // arithmetic is the same.  While snapshots are recorded every warp steps
-  // one at a time, so that it can store the state of any step.
-  const bool edge_warp = __any_sync(kFullMask, left_reader || right_reader || e_first >= 0 || e_last >= 0);
-  const bool per_step = edge_warp || snap != nullptr;
-  bool failed = false;   // a wait of this thread gave up: no more waits until the CTA leaves
-  bool aborted = false;
-  int parity = 0;
-  for (int k0 = 0; k0 < K; k0 += kRefresh) {
-    const int n = min(kRefresh, K - k0);
-    if (!per_step) {
-      if (mode == kTileFree)
-        warp_run<real, E, kTileFree, kRefresh>(v, fixed, coef, n);
-      else if (mode == kTileEnds)
-        warp_run<real, E, kTileEnds, kRefresh>(v, fixed, coef, n);
-      else if (mode == kTileMasked)
-        warp_run<real, E, kTileMasked, kRefresh>(v, fixed, coef, n);
-    } else {
-      // One step from `in` to `out`: the halo reads before it, the state
-      // records and edge hand-offs after it.  Steps alternate between v and
-      // w, so the loop carries no register rotation.
-      auto edge_step = [&](real (&in)[E], real (&out)[E], int k) {
-        if (left_reader && !failed) {
-          const int d = dl_next;
-          if (trace_in && k + 1 < K) dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
-          real val;
-          if (fetch_halo<real>(a, &sh.lavail, sh.lring, k, trace_in, trace_out, static_cast<size_t>(k) * tstride + tl,
-                               d, val))
-            in[0] = val;
-          else
-            failed = true;
-        }
-        if (right_reader && !failed) {
-          const int d = dr_next;
-          if (trace_in && k + 1 < K) dr_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tr);
-          real val;
-          if (fetch_halo<real>(a, &sh.ravail, sh.rring, k, trace_in, trace_out, static_cast<size_t>(k) * tstride + tr,
-                               d, val)) {
+    // Version 0 of the edges (the state the run starts from).
+    if (e_first >= 0) {
+      real x = v[0];
 #pragma unroll
-            for (int e = 0; e < E; ++e)
-              if (e == e_rh) in[e] = val;
+      for (int e = 0; e < E; ++e)
+        if (e == e_first) x = v[e];
+      sh.own_l[0] = x;
+      hand_off<real>(sh.dst[0], R, 0, x);
+    }
+    if (e_last >= 0) {
+      real x = v[0];
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e == e_last) x = v[e];
+      sh.own_r[0] = x;
+      hand_off<real>(sh.dst[1], R, 0, x);
+    }
+
+    const uint8_t* trace_in = a.trace_in;
+    uint8_t* trace_out = a.trace_out;
+    const bool replay = trace_in != nullptr;
+    // S-1 boundaries (S on the periodic ring, boundary b joining b and b+1 mod S)
+    const int tstride = (periodic ? S : S - 1) * 2;
+    const int tl = has_left ? ((s + S - 1) % S) * 2 + 1 : 0;  // side 1 of boundary s-1
+    const int tr = s * 2 + 0;                                 // side 0 of boundary s
+    int dl_next = 0, dr_next = 0;
+    if (replay && K > 0) {
+      if (left_reader) dl_next = __ldg(trace_in + tl);
+      if (right_reader) dr_next = __ldg(trace_in + tr);
+    }
+
+    // Only the warps that read a halo or hand an edge on need to stop after
+    // every step.  The others advance each run of kRefresh steps with the
+    // two-array step (no per-step checks, no register rotation); the
+    // arithmetic is the same.  While snapshots are recorded every warp steps
+    // one at a time, so that it can store the state of any step.
+    const bool edge_warp = __any_sync(kFullMask, left_reader || right_reader || e_first >= 0 || e_last >= 0);
+    const bool per_step = edge_warp || snap != nullptr;
+    bool failed = false;  // a wait of this thread gave up: no more waits until the CTA leaves
+    bool aborted = false;
+    int parity = 0;
+    for (int k0 = 0; k0 < K; k0 += kRefresh) {
+      const int n = min(kRefresh, K - k0);
+      if (!per_step) {
+        if (mode == kTileFree)
+          warp_run<real, E, kTileFree, kRefresh>(v, fixed, coef, n);
+        else if (mode == kTileEnds)
+          warp_run<real, E, kTileEnds, kRefresh>(v, fixed, coef, n);
+        else if (mode == kTileMasked)
+          warp_run<real, E, kTileMasked, kRefresh>(v, fixed, coef, n);
+      } else {
+        // One step from `in` to `out`: the halo reads before it, the state
+        // records and edge hand-offs after it.  Steps alternate between v and
+        // w, so the loop carries no register rotation.
+        auto edge_step = [&](real (&in)[E], real (&out)[E], int k) {
+          if (left_reader && !failed) {
+            const int d = dl_next;
+            if (replay && k + 1 < K) dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
+            real val;
+            if (fetch_halo<real>(a, sh.lin, k, replay, trace_out, static_cast<size_t>(k) * tstride + tl, d, val))
+              in[0] = val;
+            else
+              failed = true;
+          }
+          if (right_reader && !failed) {
+            const int d = dr_next;
+            if (replay && k + 1 < K) dr_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tr);
+            real val;
+            if (fetch_halo<real>(a, sh.rin, k, replay, trace_out, static_cast<size_t>(k) * tstride + tr, d, val)) {
+#pragma unroll
+              for (int e = 0; e < E; ++e)
+                if (e == e_rh) in[e] = val;
+            } else {
+              failed = true;
+            }
+          }
+          if (mode == kTileFree) {
+            warp_step_to<real, E, kTileFree>(in, out, fixed, coef);
+          } else if (mode == kTileEnds) {
+            warp_step_to<real, E, kTileEnds>(in, out, fixed, coef);
+          } else if (mode == kTileMasked) {
+            warp_step_to<real, E, kTileMasked>(in, out, fixed, coef);
           } else {
-            failed = true;
-          }
-        }
-        if (mode == kTileFree) {
-          warp_step_to<real, E, kTileFree>(in, out, fixed, coef);
-        } else if (mode == kTileEnds) {
-          warp_step_to<real, E, kTileEnds>(in, out, fixed, coef);
-        } else if (mode == kTileMasked) {
-          warp_step_to<real, E, kTileMasked>(in, out, fixed, coef);
-        } else {
 #pragma unroll
-          for (int e = 0; e < E; ++e) out[e] = in[e];
-        }
-        const int ver = k + 1, j = ver & (a.R - 1);
-        if (snap && ver % a.snap_every == 0) {  // owners record the state at step ver
-          real* row = snap + static_cast<size_t>(ver / a.snap_every) * N;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const int p = Win::pos(warp, lane, e);
-            if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) row[a0 - 1 + p] = out[e];
+            for (int e = 0; e < E; ++e) out[e] = in[e];
           }
+          const int ver = k + 1;
+          if (e_first >= 0) {  // position 1: always slot 1 of lane 0 in warp 0
+            hand_off<real>(sh.dst[0], R, ver, out[1]);
+            sh.own_l[ver & (R - 1)] = out[1];
+          }
+          if (e_last >= 0) {
+            const real x = pick_slot<real, E>(out, e_last);
+            hand_off<real>(sh.dst[1], R, ver, x);
+            sh.own_r[ver & (R - 1)] = x;
+          }
+          if (a.snap && ver % a.snap_every == 0) {  // owners record the state at step ver
+            real* row = static_cast<real*>(a.snap) + static_cast<size_t>(ver / a.snap_every) * N;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int p = Win::pos(warp, lane, e);
+              if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) row[a0 - 1 + p] = out[e];
+            }
+          }
+        };
+        real w[E];
+        int k = k0;
+        for (; k + 1 < k0 + n; k += 2) {
+          edge_step(v, w, k);
+          edge_step(w, v, k + 1);
         }
-        if (e_first >= 0) {  // position 1: always slot 1 of lane 0 in warp 0
-          sh.own_l[j] = out[1];
-          st_release_cta_shared(&sh.own_l_ver, ver);
+        if (k < k0 + n) {
+          edge_step(v, w, k);
+#pragma unroll
+          for (int e = 0; e < E; ++e) v[e] = w[e];
+        }
+      }
+      // Refresh the warp halos after every run of kRefresh steps (and after
+      // the last step); the refresh barrier also tells every warp whether a
+      // wait gave up.
+      const bool any_failed = warp_refresh<real, E, Win::H>(v, sh.win, parity, warp, lane, nwc, nthreads_c, failed);
+      parity ^= 1;
+      if (any_failed) {
+        aborted = true;
+        break;
+      }
+    }
+
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = Win::pos(warp, lane, e);
+      if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) uout[a0 - 1 + p] = v[e];
+    }
+    // The edge values of the last q steps, for a later resumed run: versions
+    // K-q+1 .. K of this launch from the own rings (written by these same
+    // threads), older ones from the history this launch started from.
+    if (a.hist_out && !aborted && (e_first >= 0 || e_last >= 0)) {
+      real* ho = static_cast<real*>(a.hist_out);
+      const real* hi_ = static_cast<const real*>(a.hist_in);
+      for (int j = 0; j < a.q; ++j) {
+        const int ver = K - a.q + 1 + j;
+        if (e_first >= 0) {
+          const real x = ver >= 0 ? sh.own_l[ver & (R - 1)]
+                                  : (hi_ ? hi_[(static_cast<size_t>(s) * 2 + 0) * a.q + (ver + a.q - 1)] : sh.own_l[0]);
+          ho[(static_cast<size_t>(s) * 2 + 0) * a.q + j] = x;
         }
         if (e_last >= 0) {
-          sh.own_r[j] = pick_slot<real, E>(out, e_last);
-          st_release_cta_shared(&sh.own_r_ver, ver);
+          const real x = ver >= 0 ? sh.own_r[ver & (R - 1)]
+                                  : (hi_ ? hi_[(static_cast<size_t>(s) * 2 + 1) * a.q + (ver + a.q - 1)] : sh.own_r[0]);
+          ho[(static_cast<size_t>(s) * 2 + 1) * a.q + j] = x;
         }
-      };
-      real w[E];
-      int k = k0;
-      for (; k + 1 < k0 + n; k += 2) {
-        edge_step(v, w, k);
-        edge_step(w, v, k + 1);
-      }
-      if (k < k0 + n) {
-        edge_step(v, w, k);
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = w[e];
       }
     }
-    // Refresh the warp halos after every run of kRefresh steps (and after the
-    // last step); the refresh barrier also tells every warp whether a wait
-    // gave up.
-    const bool any_failed = warp_refresh<real, E, Win::H>(v, sh.win, parity, warp, lane, nwc, nthreads_c, failed);
-    parity ^= 1;
-    if (any_failed) {
-      aborted = true;
-      break;
-    }
+    named_barrier_sync(1, nthreads_c);
+    if (tid == 0) st_release_cta_shared(&sh.compute_done, aborted ? 2 : 1);
   }
+  // Every thread of the cluster reaches this point (all waits are bounded),
+  // so no CTA leaves while a neighbour may still write into its rings.
+  if (C > 1) cluster_sync_all();
+}
 
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int p = Win::pos(warp, lane, e);
-    if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) uout[a0 - 1 + p] = v[e];
-  }
-  // The edge values of the last q steps, for a later resumed run: versions
-  // K-q+1 .. K of this launch from the hand-off rings (written by these same
-  // threads), older ones from the history this launch started from.
-  if (a.hist_out && !aborted && (e_first >= 0 || e_last >= 0)) {
-    real* ho = static_cast<real*>(a.hist_out);
-    const real* hi_ = static_cast<const real*>(a.hist_in);
-    for (int j = 0; j < a.q; ++j) {
-      const int ver = K - a.q + 1 + j;
-      if (e_first >= 0) {
-        const real x = ver >= 0 ? sh.own_l[ver & (a.R - 1)]
-                                : (hi_ ? hi_[(static_cast<size_t>(s) * 2 + 0) * a.q + (ver + a.q - 1)] : sh.own_l[0]);
-        ho[(static_cast<size_t>(s) * 2 + 0) * a.q + j] = x;
-      }
-      if (e_last >= 0) {
-        const real x = ver >= 0 ? sh.own_r[ver & (a.R - 1)]
-                                : (hi_ ? hi_[(static_cast<size_t>(s) * 2 + 1) * a.q + (ver + a.q - 1)] : sh.own_r[0]);
-        ho[(static_cast<size_t>(s) * 2 + 1) * a.q + j] = x;
-      }
-    }
-  }
-  named_barrier_sync(1, nthreads_c);
-  if (tid == 0) st_release_cta_shared(&sh.compute_done, aborted ? 2 : 1);
+template <typename real, int E>
+cudaLaunchConfig_t cluster_config(int S, int threads, int C, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(S);
+  cfg.blockDim = dim3(threads + 32 * kCommWarps);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
 }
 
 template <typename real, int E>
 int launch_async_t(const SegmentRun& a, int threads, cudaStream_t st) {
   SegmentRun args = a;
   set_run_params(args);
+  if (a.cluster > 1) {
+    // A cluster launch (not cooperative): the residency of every cluster was
+    // checked by async_cluster_size, and every wait in the kernel is bounded,
+    // so a CTA that could not be scheduled makes the run time out, not hang.
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = cluster_config<real, E>(a.S, threads, a.cluster, st, attr);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, async_persistent_kernel<real, E>, args);
+    return e == cudaSuccess ? HEAT1D_OK : HEAT1D_ERR_CUDA;
+  }
   void* params[] = {&args};
   cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(async_persistent_kernel<real, E>), dim3(a.S),
                                               dim3(threads + 32 * kCommWarps), params, 0, st);
@@ -475,7 +624,41 @@ int resident_t(int threads) {
   return per_sm * nsm;
 }
 
+// How many clusters of C CTAs can be resident at once (0 on any error).
+template <typename real, int E>
+int active_clusters_t(int S, int threads, int C) {
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cluster_config<real, E>(S, threads, C, nullptr, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, async_persistent_kernel<real, E>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int active_clusters(int dtype, int E, int threads, int S, int C) {
+  const bool f64 = dtype == HEAT1D_F64;
+  switch (E) {
+    case 2: return f64 ? active_clusters_t<double, 2>(S, threads, C) : active_clusters_t<float, 2>(S, threads, C);
+    case 4: return f64 ? active_clusters_t<double, 4>(S, threads, C) : active_clusters_t<float, 4>(S, threads, C);
+    case 8: return f64 ? active_clusters_t<double, 8>(S, threads, C) : active_clusters_t<float, 8>(S, threads, C);
+    case 16: return f64 ? active_clusters_t<double, 16>(S, threads, C) : active_clusters_t<float, 16>(S, threads, C);
+    default: return 0;
+  }
+}
+
 }  // namespace
+
+int async_cluster_size(int dtype, int E, int threads, int S, int wanted) {
+  if (wanted == 1 || S < 2) return wanted <= 1 ? 1 : 0;
+  const int cands[3] = {8, 4, 2};
+  for (int c : cands) {
+    if ((wanted && c != wanted) || S % c != 0) continue;
+    if (static_cast<int64_t>(active_clusters(dtype, E, threads, S, c)) * c >= S) return c;
+  }
+  return wanted ? 0 : 1;
+}
 
 int launch_async_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st) {
   const bool f64 = dtype == HEAT1D_F64;

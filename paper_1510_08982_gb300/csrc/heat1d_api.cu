@@ -191,6 +191,10 @@ int configure(heat1d* h, const heat1d_opts& o) {
   if (o.boundary < 0 || o.boundary > 1) return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: boundary must be 0 or 1");
   if (o.boundary == 1 && o.sync_mode == 2)
     return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: periodic runs are on-chip only (sync_mode 0 or 1)");
+  if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4 && o.cluster != 8)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: cluster must be 0, 1, 2, 4 or 8");
+  if (o.cluster > 1 && S % o.cluster != 0)
+    return fail(HEAT1D_ERR_INVAL, "heat1d_set_opts: cluster must divide the number of segments");
 
   // Streamed shape: 16-byte vectors, so E and the halo are multiples of
   // 16 / sizeof(real) points and every tile starts on a 16-byte boundary.
@@ -227,7 +231,8 @@ int configure(heat1d* h, const heat1d_opts& o) {
   HEAT1D_CUDA(cudaMalloc(&h->d_off, sizeof(int64_t) * (S + 1)));
   HEAT1D_CUDA(cudaMemcpy(h->d_off, off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice));
   HEAT1D_CUDA(cudaMalloc(&h->edges, h->esize * 2 * S * 2 * T));
-  HEAT1D_CUDA(cudaMalloc(&h->rings, h->esize * S * 2 * R));
+  // tagged slots: one 64-bit word per 32 bits of a value
+  HEAT1D_CUDA(cudaMalloc(&h->rings, 2 * h->esize * S * 2 * R));
   HEAT1D_CUDA(cudaMalloc(&h->prog, sizeof(int) * S * heat1d_impl::kProgStride));
   if (ntiles > 0) HEAT1D_CUDA(cudaMalloc(&h->done, sizeof(int) * ntiles));
   return HEAT1D_OK;
@@ -424,7 +429,12 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   a.k0 = h->hist_cur >= 0 ? h->async_step : 0;
   a.hist_in = h->hist_cur >= 0 ? h->hist[h->hist_cur] : nullptr;
   a.hist_out = h->hist[hout];
-  HEAT1D_CUDA(cudaMemsetAsync(h->prog, 0xff, sizeof(int) * h->S * heat1d_impl::kProgStride, h->stream));
+  a.cluster = heat1d_impl::async_cluster_size(h->dtype, E, threads, h->S, h->opts.cluster);
+  if (a.cluster < 1)
+    return fail(HEAT1D_ERR_NOT_RESIDENT, "asynchronous run: clusters of " + std::to_string(h->opts.cluster) +
+                                             " CTAs cannot all be resident");
+  // empty slots: every word carries version 0x80808080, which no run uses
+  HEAT1D_CUDA(cudaMemsetAsync(h->rings, 0x80, 2 * h->esize * h->S * 2 * h->R, h->stream));
   rc = heat1d_impl::launch_async_persistent(a, h->dtype, E, threads, h->stream);
   if (rc == HEAT1D_ERR_NOT_RESIDENT)
     return fail(rc, "asynchronous run: " + std::to_string(h->S) + " CTAs cannot all be resident");
@@ -738,6 +748,16 @@ int64_t heat1d_blocked_segments(heat1d_t h, int64_t* offsets, int32_t* block_ste
     for (int64_t j = 0; j <= h->ntiles; ++j) offsets[j] = std::min<int64_t>(j * h->W, h->N);
   if (block_steps) *block_steps = h->Ts;
   return h->ntiles;
+}
+
+int heat1d_async_cluster(heat1d_t h) {
+  if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
+  int E = 0, threads = 0;
+  const int rc = pick_shape(h, h->Lmax + 2, 32 * heat1d_impl::kCommWarps, true, &E, &threads);
+  if (rc) return rc;
+  const int c = heat1d_impl::async_cluster_size(h->dtype, E, threads, static_cast<int>(h->S), h->opts.cluster);
+  if (c < 1) return fail(HEAT1D_ERR_NOT_RESIDENT, "clusters of the requested size cannot all be resident");
+  return c;
 }
 
 int64_t heat1d_trace_bytes(heat1d_t h, int64_t K) {

@@ -10,9 +10,9 @@ namespace heat1d_impl {
 
 // Largest ring of the asynchronous run (versions kept per directed edge).
 constexpr int kMaxRing = 512;
-// Communication warps per CTA of the asynchronous kernel (publisher, left
-// puller, right puller).
-constexpr int kCommWarps = 3;
+// Communication warps per CTA of the asynchronous kernel (left puller, right
+// puller).
+constexpr int kCommWarps = 2;
 // Padding, in ints, between the per-segment version counters (one 128-byte
 // line each, so that CTAs never share a line they write).
 constexpr int kProgStride = 32;
@@ -43,8 +43,10 @@ struct SegmentRun {
   // asynchronous run / replay
   int q;                   // delay window
   int R;                   // ring length (power of two, >= 2q)
-  int* prog;               // [S * kProgStride] published versions, -1 at launch
-  void* rings;             // [S][2][R] values: [s][0] left edge, [s][1] right edge
+  int* prog;               // blocked run: [S * kProgStride] strip versions, -1 at launch
+  void* rings;             // per-step run: [S][2][R][sizeof(real)/4] tagged slot words (uint64, version in
+                           // the high half, 32 value bits in the low half), cleared to bytes 0x80;
+                           // [s][0] the first point, [s][1] the last point.  Blocked run: the strips.
   uint8_t* trace_out;      // device or NULL
   const uint8_t* trace_in; // device, replay only
   int stall_segment;       // -1: off
@@ -56,6 +58,10 @@ struct SegmentRun {
   int64_t k0;
   const void* hist_in;
   void* hist_out;
+  // CTAs per thread-block cluster (1: none).  Neighbouring segments in one
+  // cluster hand their edge values to each other through distributed shared
+  // memory; the others through the global rings.
+  int cluster;
 };
 
 // Arguments of one temporally blocked synchronous run streamed through HBM.
@@ -103,14 +109,11 @@ constexpr int max_async_threads(int elem_bytes, int E) {
 // redundancy is worth more barriers.  The asynchronous kernel uses H = E/2: its edge warps must not be
 // held back by frequent barriers.  A CTA of nw compute warps covers
 // nw*D + 2H positions.
-// On chip, FP32 tiles of 16 points per thread take H = 16: whole lanes 0 and
-// 31 are the halos, refreshed every 16 steps (measured: an H-step run costs
-// about 100 instructions of loop and refresh per warp; half as many refreshes
-// outweigh 3 % more redundant points).  Streamed tiles keep H = E/2: their
-// passes are often no longer than H, so a wider halo only adds redundancy.
-constexpr int sync_window_halo(int elem_bytes, int E) {
-  return elem_bytes == 8 ? (E >= 4 ? E / 4 : 1) : (E == 16 ? 16 : E / 2);
-}
+// FP32 tiles take H = E/2.  Whole-lane halos (H = E = 16: lanes 0 and 31 the
+// halos, refreshed every 16 steps; Window allows the form) were measured on
+// GB300 and lost: 4.75e12 against 7.33e12 updates/s on the 2^20-point rod at
+// T = 512, 0.33 against 0.41 of the FP32 ALU roofline on the uneven batch.
+constexpr int sync_window_halo(int elem_bytes, int E) { return elem_bytes == 8 ? (E >= 4 ? E / 4 : 1) : E / 2; }
 constexpr int stream_window_halo(int elem_bytes, int E) { return elem_bytes == 8 ? (E >= 4 ? E / 4 : 1) : E / 2; }
 constexpr int async_window_halo(int /*elem_bytes*/, int E) { return E / 2; }
 constexpr int64_t window_width(int64_t nwarps, int E, int H) { return nwarps * (32 * E - 2 * H) + 2 * H; }
@@ -135,6 +138,10 @@ inline void set_run_params(Run& a) {
 // threads per CTA (a multiple of 32).  Return a heat1d_status code.
 int launch_sync_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
 int launch_async_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
+// Cluster size for the asynchronous per-step run of S segments: `wanted` 0
+// picks the largest of 8, 4, 2 that divides S with every cluster resident
+// (else 1); 1, 2, 4 or 8 is checked.  Returns 0 when `wanted` cannot be met.
+int async_cluster_size(int dtype, int E, int threads, int S, int wanted);
 // Asynchronous run with temporal blocking: a.T steps per block, a.rings holds
 // [S][R][2T] strips, a.prog the per-segment strip versions (-1 at launch).
 int launch_async_blocked(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);

@@ -29,6 +29,7 @@ EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_las
            "heat1d_set_snapshots", "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
            "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync",
            "heat1d_run_async_blocked", "heat1d_replay_blocked", "heat1d_blocked_trace_bytes", "heat1d_blocked_segments",
+           "heat1d_async_cluster",
            "heat1d_batch_create", "heat1d_batch_run", "heat1d_batch_sync", "heat1d_batch_describe",
            "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_adjoint", "heat1d_vjp",
            "heat1d_adjoint_batched", "heat1d_run_sync_noalloc", "heat1d_probe_fma", "heat1d_state_bytes",
@@ -45,7 +46,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("segments", ctypes.c_int64), ("q", ctypes.c_int32), ("halo_steps", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("elems_per_thread", ctypes.c_int32),
                 ("spin_limit_ns", ctypes.c_int64), ("stall_segment", ctypes.c_int32),
-                ("sync_mode", ctypes.c_int32), ("boundary", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("sync_mode", ctypes.c_int32), ("boundary", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class RodSpec(ctypes.Structure):
@@ -88,6 +90,7 @@ def load():
         "heat1d_replay_blocked": (i32, [vp, i64, vp, i32]),
         "heat1d_blocked_trace_bytes": (i64, [vp, i64]),
         "heat1d_blocked_segments": (i64, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
+        "heat1d_async_cluster": (i32, [vp]),
         "heat1d_state_bytes": (i64, [vp]),
         "heat1d_get_state": (i32, [vp, vp, i32]),
         "heat1d_set_state": (i32, [vp, vp, i32]),
@@ -146,8 +149,9 @@ class Heat1d:
     """One rod of N points: state, options and scratch on the current device.
 
     ``opts`` keywords: segments, q, halo_steps, block_threads,
-    elems_per_thread, spin_limit_ns, stall_segment, sync_mode, boundary (see
-    heat1d_opts; boundary=1 is the periodic ring of Section 5.3)."""
+    elems_per_thread, spin_limit_ns, stall_segment, sync_mode, boundary,
+    cluster (see heat1d_opts; boundary=1 is the periodic ring of Section 5.3,
+    cluster the CTAs per thread-block cluster of per-step asynchronous runs)."""
 
     def __init__(self, N, r, c1, cN, dtype="float64", **opts):
         torch = _torch()
@@ -294,6 +298,14 @@ class Heat1d:
         T = ctypes.c_int32(0)
         self.lib.heat1d_blocked_segments(self.h, off.ctypes.data_as(ctypes.c_void_p), ctypes.byref(T))
         return off, int(T.value)
+
+    def async_cluster(self) -> int:
+        """CTAs per thread-block cluster of the per-step asynchronous run (1:
+        every edge exchange through global memory)."""
+        c = int(self.lib.heat1d_async_cluster(self.h))
+        if c < 0:
+            raise Heat1dError(c, last_error())
+        return c
 
     def new_blocked_trace(self, K, device=True):
         """A trace buffer for a blocked run of K steps: (ceil(K/T), S-1, 2)
