@@ -90,16 +90,17 @@ typedef struct heat1d_opts {
                             c1 and cN are then unused.  Periodic runs are on-chip synchronous runs
                             and asynchronous runs with S >= 2 (the ring has S boundaries, so a
                             periodic trace is uint8[K][S][2]). */
-  int32_t cluster;       /* asynchronous per-step runs (heat1d_run_async, heat1d_replay): CTAs per
-                            thread-block cluster.  Consecutive segments in one cluster hand their
-                            edge values to each other through distributed shared memory (a store
-                            into the neighbour CTA's ring and a cluster-scope release of its
-                            version word); segments in different clusters exchange through the
-                            global rings.  The results and the delay model are the same.
-                            0: automatic (the largest of 8, 4 and 2 that divides S and keeps all
-                            S CTAs resident, else 1).  1: no clusters.  2, 4 or 8: that size
-                            (HEAT1D_ERR_INVAL if it does not divide S, HEAT1D_ERR_NOT_RESIDENT if
-                            the clusters cannot all be resident). */
+  int32_t cluster;       /* on-chip asynchronous runs (per-step and blocked): CTAs per thread-block
+                            cluster.  Consecutive segments in one cluster hand their edge values
+                            (per-step run) or edge strips (blocked run) to each other through
+                            distributed shared memory, written straight into the neighbour CTA's
+                            shared memory; segments in different clusters exchange through the
+                            rings in global memory.  The results and the delay model are the
+                            same.  0: automatic (the largest of 8, 4 and 2 that divides S and
+                            keeps all S CTAs resident, else 1; blocked runs also need the
+                            neighbours' strip rings, 2*R*T values, within 96 KB).  1: no
+                            clusters.  2, 4 or 8: that size (HEAT1D_ERR_INVAL if it does not
+                            divide S, HEAT1D_ERR_NOT_RESIDENT if it cannot be met). */
   int32_t reserved[4];
 } heat1d_opts;
 
@@ -275,11 +276,13 @@ int64_t heat1d_blocked_trace_bytes(heat1d_t h, int64_t K);
 int64_t heat1d_blocked_segments(heat1d_t h, int64_t* offsets, int32_t* block_steps);
 
 /* The thread-block cluster size (CTAs per cluster, 1 = none) that the
- * handle's per-step asynchronous runs (heat1d_run_async, heat1d_replay) use
- * with its current options (heat1d_opts.cluster).  Negative status on error:
+ * handle's per-step asynchronous runs (blocked = 0: heat1d_run_async,
+ * heat1d_replay) or blocked asynchronous runs (blocked = 1:
+ * heat1d_run_async_blocked, heat1d_replay_blocked; 1 when streamed) use with
+ * its current options (heat1d_opts.cluster).  Negative status on error:
  * HEAT1D_ERR_INVAL for segments too long for the on-chip kernel,
  * HEAT1D_ERR_NOT_RESIDENT when the requested size cannot be met. */
-int heat1d_async_cluster(heat1d_t h);
+int heat1d_async_cluster(heat1d_t h, int blocked);
 
 /* Waits for the handle's stream and returns the device-side status of the
  * runs enqueued since the previous heat1d_sync(): HEAT1D_OK,

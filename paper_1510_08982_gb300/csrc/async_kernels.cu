@@ -36,6 +36,7 @@
 // version before those reads are done.
 #include <algorithm>
 
+#include "cluster.cuh"
 #include "common.cuh"
 #include "impl.h"
 
@@ -102,24 +103,6 @@ __device__ __forceinline__ unsigned long long ld_slot_global(const unsigned long
 }
 __device__ __forceinline__ void st_slot_global(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Thread-block clusters.
-__device__ __forceinline__ uint32_t cluster_addr(const void* local, unsigned rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
-               : "=r"(r)
-               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(local))), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// Every thread of every CTA of the cluster (none has exited before it).
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
 template <typename real, int E>
@@ -575,22 +558,6 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
 }
 
 template <typename real, int E>
-cudaLaunchConfig_t cluster_config(int S, int threads, int C, cudaStream_t st, cudaLaunchAttribute* attr) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(S);
-  cfg.blockDim = dim3(threads + 32 * kCommWarps);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cfg;
-}
-
-template <typename real, int E>
 int launch_async_t(const SegmentRun& a, int threads, cudaStream_t st) {
   SegmentRun args = a;
   set_run_params(args);
@@ -599,7 +566,7 @@ int launch_async_t(const SegmentRun& a, int threads, cudaStream_t st) {
     // checked by async_cluster_size, and every wait in the kernel is bounded,
     // so a CTA that could not be scheduled makes the run time out, not hang.
     cudaLaunchAttribute attr[1];
-    const cudaLaunchConfig_t cfg = cluster_config<real, E>(a.S, threads, a.cluster, st, attr);
+    const cudaLaunchConfig_t cfg = cluster_launch_config(a.S, threads + 32 * kCommWarps, 0, a.cluster, st, attr);
     const cudaError_t e = cudaLaunchKernelEx(&cfg, async_persistent_kernel<real, E>, args);
     return e == cudaSuccess ? HEAT1D_OK : HEAT1D_ERR_CUDA;
   }
@@ -624,40 +591,22 @@ int resident_t(int threads) {
   return per_sm * nsm;
 }
 
-// How many clusters of C CTAs can be resident at once (0 on any error).
-template <typename real, int E>
-int active_clusters_t(int S, int threads, int C) {
-  cudaLaunchAttribute attr[1];
-  const cudaLaunchConfig_t cfg = cluster_config<real, E>(S, threads, C, nullptr, attr);
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, async_persistent_kernel<real, E>, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
-}
-
-int active_clusters(int dtype, int E, int threads, int S, int C) {
-  const bool f64 = dtype == HEAT1D_F64;
-  switch (E) {
-    case 2: return f64 ? active_clusters_t<double, 2>(S, threads, C) : active_clusters_t<float, 2>(S, threads, C);
-    case 4: return f64 ? active_clusters_t<double, 4>(S, threads, C) : active_clusters_t<float, 4>(S, threads, C);
-    case 8: return f64 ? active_clusters_t<double, 8>(S, threads, C) : active_clusters_t<float, 8>(S, threads, C);
-    case 16: return f64 ? active_clusters_t<double, 16>(S, threads, C) : active_clusters_t<float, 16>(S, threads, C);
-    default: return 0;
-  }
-}
-
 }  // namespace
 
 int async_cluster_size(int dtype, int E, int threads, int S, int wanted) {
-  if (wanted == 1 || S < 2) return wanted <= 1 ? 1 : 0;
-  const int cands[3] = {8, 4, 2};
-  for (int c : cands) {
-    if ((wanted && c != wanted) || S % c != 0) continue;
-    if (static_cast<int64_t>(active_clusters(dtype, E, threads, S, c)) * c >= S) return c;
+  const bool f64 = dtype == HEAT1D_F64;
+  const int t = threads + 32 * kCommWarps;
+  switch (E) {
+    case 2: return f64 ? pick_cluster_size(async_persistent_kernel<double, 2>, S, t, 0, wanted)
+                       : pick_cluster_size(async_persistent_kernel<float, 2>, S, t, 0, wanted);
+    case 4: return f64 ? pick_cluster_size(async_persistent_kernel<double, 4>, S, t, 0, wanted)
+                       : pick_cluster_size(async_persistent_kernel<float, 4>, S, t, 0, wanted);
+    case 8: return f64 ? pick_cluster_size(async_persistent_kernel<double, 8>, S, t, 0, wanted)
+                       : pick_cluster_size(async_persistent_kernel<float, 8>, S, t, 0, wanted);
+    case 16: return f64 ? pick_cluster_size(async_persistent_kernel<double, 16>, S, t, 0, wanted)
+                        : pick_cluster_size(async_persistent_kernel<float, 16>, S, t, 0, wanted);
+    default: return 0;
   }
-  return wanted ? 0 : 1;
 }
 
 int launch_async_persistent(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st) {

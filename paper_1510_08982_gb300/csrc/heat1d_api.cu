@@ -541,6 +541,11 @@ int run_blocked_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_devi
   if ((rc = stage_traces(h, tbytes, trace_out, out_on_device, trace_in, in_on_device, &out_dev, &in_dev))) return rc;
   a.trace_out = out_dev;
   a.trace_in = in_dev;
+  a.cluster = heat1d_impl::blocked_cluster_size(h->dtype, E, threads, static_cast<int>(h->S), h->R, h->T,
+                                                h->opts.cluster);
+  if (a.cluster < 1)
+    return fail(HEAT1D_ERR_NOT_RESIDENT, "blocked asynchronous run: clusters of " +
+                                             std::to_string(h->opts.cluster) + " CTAs cannot all be resident");
   HEAT1D_CUDA(cudaMemsetAsync(h->prog, 0xff, sizeof(int) * h->S * heat1d_impl::kProgStride, h->stream));
   rc = heat1d_impl::launch_async_blocked(a, h->dtype, E, threads, h->stream);
   if (rc == HEAT1D_ERR_NOT_RESIDENT)
@@ -750,12 +755,16 @@ int64_t heat1d_blocked_segments(heat1d_t h, int64_t* offsets, int32_t* block_ste
   return h->ntiles;
 }
 
-int heat1d_async_cluster(heat1d_t h) {
+int heat1d_async_cluster(heat1d_t h, int blocked) {
   if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
   int E = 0, threads = 0;
-  const int rc = pick_shape(h, h->Lmax + 2, 32 * heat1d_impl::kCommWarps, true, &E, &threads);
+  if (blocked && blocked_streamed(h)) return 1;  // tiles streamed through HBM: no clusters
+  const int rc = blocked ? pick_shape(h, h->Lmax + 2 * h->T, 0, false, &E, &threads)
+                         : pick_shape(h, h->Lmax + 2, 32 * heat1d_impl::kCommWarps, true, &E, &threads);
   if (rc) return rc;
-  const int c = heat1d_impl::async_cluster_size(h->dtype, E, threads, static_cast<int>(h->S), h->opts.cluster);
+  const int S = static_cast<int>(h->S);
+  const int c = blocked ? heat1d_impl::blocked_cluster_size(h->dtype, E, threads, S, h->R, h->T, h->opts.cluster)
+                        : heat1d_impl::async_cluster_size(h->dtype, E, threads, S, h->opts.cluster);
   if (c < 1) return fail(HEAT1D_ERR_NOT_RESIDENT, "clusters of the requested size cannot all be resident");
   return c;
 }

@@ -145,6 +145,11 @@ int async_cluster_size(int dtype, int E, int threads, int S, int wanted);
 // Asynchronous run with temporal blocking: a.T steps per block, a.rings holds
 // [S][R][2T] strips, a.prog the per-segment strip versions (-1 at launch).
 int launch_async_blocked(const SegmentRun& a, int dtype, int E, int threads, cudaStream_t st);
+// Cluster size for the blocked run (as async_cluster_size; a cluster launch
+// keeps the neighbours' strip rings, 2*R*T values, in shared memory, at most
+// kMaxClusterStripBytes).
+constexpr size_t kMaxClusterStripBytes = 96 * 1024;
+int blocked_cluster_size(int dtype, int E, int threads, int S, int R, int T, int wanted);
 
 // Sets the message returned by heat1d_last_error() on this host thread.
 void set_last_error(const std::string& msg);

@@ -90,7 +90,7 @@ def load():
         "heat1d_replay_blocked": (i32, [vp, i64, vp, i32]),
         "heat1d_blocked_trace_bytes": (i64, [vp, i64]),
         "heat1d_blocked_segments": (i64, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
-        "heat1d_async_cluster": (i32, [vp]),
+        "heat1d_async_cluster": (i32, [vp, i32]),
         "heat1d_state_bytes": (i64, [vp]),
         "heat1d_get_state": (i32, [vp, vp, i32]),
         "heat1d_set_state": (i32, [vp, vp, i32]),
@@ -299,10 +299,11 @@ class Heat1d:
         self.lib.heat1d_blocked_segments(self.h, off.ctypes.data_as(ctypes.c_void_p), ctypes.byref(T))
         return off, int(T.value)
 
-    def async_cluster(self) -> int:
-        """CTAs per thread-block cluster of the per-step asynchronous run (1:
-        every edge exchange through global memory)."""
-        c = int(self.lib.heat1d_async_cluster(self.h))
+    def async_cluster(self, blocked=False) -> int:
+        """CTAs per thread-block cluster of the per-step (or, blocked=True,
+        the blocked) asynchronous run (1: every exchange through global
+        memory)."""
+        c = int(self.lib.heat1d_async_cluster(self.h, 1 if blocked else 0))
         if c < 0:
             raise Heat1dError(c, last_error())
         return c

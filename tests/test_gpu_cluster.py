@@ -9,7 +9,9 @@ state with clusters and without.  Cluster sizes 1, 2, 4 and 8 are forced on
 rods where all segments share one cluster, where clusters meet (mixed
 exchange paths), on the periodic ring (the wrap inside one cluster, or
 between clusters), in FP32 and FP64, for resumed runs and for a stalled
-segment inside a cluster.
+segment inside a cluster.  The blocked run (strips of T points once per
+block, the same clusters) is checked the same way against the oracle's
+blocked model.
 """
 from __future__ import annotations
 
@@ -145,6 +147,68 @@ def test_cluster_stalled_segment_times_out(H):
         h.run_sync(rod.K)
         h.sync()
         assert np.array_equal(h.get_u(device=False), oracle.sync(rod.u0, rod.r, rod.c1, rod.cN, rod.K))
+
+
+# --------------------------------------------------------------------------- blocked run
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+@pytest.mark.parametrize("N,S,C,q,T,K", [
+    (1024, 8, 8, 3, 32, 3000),   # the small rod's shape, one cluster
+    (1024, 8, 1, 3, 32, 3000),
+    (5000, 16, 4, 3, 16, 1000),  # clusters meet: strips through both paths
+    (4099, 8, 2, 2, 33, 777),    # a block length that divides neither K nor the segments
+    (2000, 4, 4, 5, 100, 1234),
+])
+def test_cluster_blocked_free_run_replayed_by_oracle(H, dtype, N, S, C, q, T, K):
+    rod = rod_of(N, K, 3 * N + S + C)
+    with H.Heat1d(N, rod.r, rod.c1, rod.cN, dtype=dtype, segments=S, q=q, halo_steps=T, cluster=C) as h:
+        assert h.async_cluster(blocked=True) == C
+        tr = h.new_blocked_trace(K)
+        h.set_u(rod.u0)
+        h.run_async_blocked(K, tr)
+        h.sync()
+        got = h.get_u(device=False)
+        trh = tr.cpu().numpy()
+        assert trh.max(initial=0) < q
+        ref = oracle.async_blocked(rod.u0, rod.r, rod.c1, rod.cN, S, q, T, K, trh, dtype=np_dt(dtype))
+        assert np.array_equal(got, ref)
+        h.set_u(rod.u0)
+        h.replay_blocked(K, tr)
+        h.sync()
+        assert np.array_equal(h.get_u(device=False), got)
+    with H.Heat1d(N, rod.r, rod.c1, rod.cN, dtype=dtype, segments=S, q=q, halo_steps=T, cluster=1) as h1:
+        h1.set_u(rod.u0)
+        h1.replay_blocked(K, np.ascontiguousarray(trh))
+        h1.sync()
+        assert np.array_equal(h1.get_u(device=False), got)
+
+
+@pytest.mark.parametrize("S,C", [(8, 8), (8, 2)])
+def test_cluster_blocked_periodic_seeded_replay(H, S, C):
+    N, q, T, K = 1200, 3, 20, 900
+    rng = np.random.default_rng(S + C)
+    u0 = rng.uniform(-1, 1, size=N)
+    nb = (K + T - 1) // T
+    tr = inputs.periodic_delay_trace(nb, S, q, seed=7)
+    with H.Heat1d(N, 0.5, 0.0, 0.0, segments=S, q=q, halo_steps=T, boundary=1, cluster=C) as h:
+        assert h.async_cluster(blocked=True) == C
+        h.set_u(u0)
+        h.replay_blocked(K, tr)
+        h.sync()
+        got = h.get_u(device=False)
+    assert np.array_equal(got, oracle.async_blocked_periodic(u0, 0.5, S, q, T, K, tr))
+
+
+def test_cluster_blocked_stalled_segment_times_out(H):
+    rod = inputs.small_rod(K=2000)
+    with H.Heat1d(rod.N, rod.r, rod.c1, rod.cN, segments=8, q=3, halo_steps=16, cluster=8, stall_segment=5,
+                  spin_limit_ns=200_000_000) as h:
+        h.set_u(rod.u0)
+        h.run_async_blocked(rod.K)
+        with pytest.raises(H.Heat1dError) as ei:
+            h.sync()
+        assert ei.value.code == H.ERR_TIMEOUT
 
 
 def test_cluster_option_checks(H):
