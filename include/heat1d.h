@@ -55,7 +55,10 @@ enum heat1d_status {
   HEAT1D_ERR_TIMEOUT = -3,      /* a device-side wait exceeded spin_limit_ns */
   HEAT1D_ERR_NOT_RESIDENT = -4, /* the segments cannot all be resident at once */
   HEAT1D_ERR_TRACE = -5,        /* a replay trace entry is >= q */
-  HEAT1D_ERR_OOM = -6           /* device memory could not be allocated */
+  HEAT1D_ERR_OOM = -6,          /* device memory could not be allocated */
+  HEAT1D_ERR_BOUNDS = -7        /* bounds-checked build only: a kernel computed an index outside
+                                   its buffer; the access was skipped and the run's results are
+                                   unspecified */
 };
 
 /* Run options.  Zero in a field means "choose automatically". */
@@ -283,6 +286,25 @@ int64_t heat1d_blocked_segments(heat1d_t h, int64_t* offsets, int32_t* block_ste
  * HEAT1D_ERR_INVAL for segments too long for the on-chip kernel,
  * HEAT1D_ERR_NOT_RESIDENT when the requested size cannot be met. */
 int heat1d_async_cluster(heat1d_t h, int blocked);
+
+/* Bounds-checked build.  The library can be compiled with HEAT1D_CHECKED
+ * defined (libheat1d_checked.so): in the on-chip synchronous, per-step
+ * asynchronous and blocked kernels, the streamed asynchronous kernel and the
+ * batched kernel, every global-memory index computed for the state,
+ * snapshots, traces, edge buffers, rings, strips and edge histories (and the
+ * range of every bulk copy) is then compared with its buffer's extent before
+ * the access; an index outside it skips the access and records
+ * HEAT1D_ERR_BOUNDS in the device status word (reported by heat1d_sync /
+ * heat1d_batch_sync), without trapping.  Results are otherwise identical.
+ * heat1d_checked() returns 1 in that build, 0 in the normal one. */
+int heat1d_checked(void);
+
+/* Checked build only: runs one kernel on the current device that computes
+ * an index one past the end of a 4-element device buffer for a load and a
+ * store; the checks skip both.  Returns HEAT1D_ERR_BOUNDS when they fired
+ * (the expected result), HEAT1D_OK if they did not, HEAT1D_ERR_CUDA on a CUDA
+ * error.  The normal build returns HEAT1D_ERR_INVAL and launches nothing. */
+int heat1d_checked_selftest(void);
 
 /* Waits for the handle's stream and returns the device-side status of the
  * runs enqueued since the previous heat1d_sync(): HEAT1D_OK,

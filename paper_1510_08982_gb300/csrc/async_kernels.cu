@@ -36,6 +36,7 @@
 // version before those reads are done.
 #include <algorithm>
 
+#include "checked.cuh"
 #include "cluster.cuh"
 #include "common.cuh"
 #include "impl.h"
@@ -186,7 +187,8 @@ __device__ __forceinline__ bool fetch_halo(const SegmentRun& a, const unsigned l
       }
     }
   }
-  if (trace_out) trace_out[tidx] = static_cast<uint8_t>(k - v);
+  if (trace_out && index_ok(a.status, static_cast<int64_t>(tidx), a.trace_len))
+    trace_out[tidx] = static_cast<uint8_t>(k - v);
   return true;
 }
 
@@ -301,8 +303,10 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
       const int nb = left ? sl : sr;
       if (nb < 0) continue;
       const int ver = j - a.q + 1;
+      const int64_t hi_idx = (static_cast<int64_t>(nb) * 2 + (left ? 1 : 0)) * a.q + j;
+      if (!index_ok(a.status, hi_idx, a.hist_len)) continue;
       uint32_t b[W];
-      Tag<real>::split(hist[(static_cast<size_t>(nb) * 2 + (left ? 1 : 0)) * a.q + j], b);
+      Tag<real>::split(hist[hi_idx], b);
       unsigned long long* ring = left ? sh.lin : sh.rin;
 #pragma unroll
       for (int w = 0; w < W; ++w) ring[(ver & (R - 1)) * W + w] = slot_word(ver, b[w]);
@@ -319,9 +323,9 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
     // writes here itself)
     const bool from_left = warp == nwc;
     const int nb = from_left ? sl : sr;
-    if (nb >= 0 && !(from_left ? l_intra : r_intra))
-      pull_loop<real>(a, &sh.compute_done, rings + (static_cast<size_t>(nb) * 2 + (from_left ? 1 : 0)) * R * W,
-                      from_left ? sh.lin : sh.rin, lane);
+    const int64_t ring0 = (static_cast<int64_t>(nb) * 2 + (from_left ? 1 : 0)) * R * W;
+    if (nb >= 0 && !(from_left ? l_intra : r_intra) && index_ok(a.status, ring0 + R * W - 1, a.ring_len))
+      pull_loop<real>(a, &sh.compute_done, rings + ring0, from_left ? sh.lin : sh.rin, lane);
   } else {
     const int64_t N = a.N;
     const int64_t a0 = a.seg_off[s];
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
       const int p = Win::pos(warp, lane, e);
       const int64_t g = a0 - 1 + p;
       real x = static_cast<real>(0);
-      if (p >= 1 && p <= L) x = uin[g];
+      if (p >= 1 && p <= L && index_ok(a.status, g, N)) x = uin[g];
       if (g == end_lo) x = c1;
       if (g == end_hi) x = cN;
       v[e] = x;
@@ -371,7 +375,8 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) snap[a0 - 1 + p] = v[e];
+        if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc) && index_ok(a.status, a0 - 1 + p, a.snap_len))
+          snap[a0 - 1 + p] = v[e];
       }
     }
     const bool left_reader = has_left && warp == 0 && lane == 0;  // position 0 is (warp 0, lane 0, slot 0)
@@ -383,14 +388,15 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
     const bool stalled = s == a.stall_segment;
     if (e_first >= 0) {
       unsigned long long d = 0;
-      if (!stalled && sl >= 0)
+      // (a ring in global memory must lie wholly inside the rings buffer)
+      if (!stalled && sl >= 0 && (l_intra || index_ok(a.status, (static_cast<int64_t>(s) * 2 + 1) * R * W - 1, a.ring_len)))
         d = l_intra ? kRemoteDst | cluster_addr(sh.rin, rank == 0 ? static_cast<unsigned>(C - 1) : rank - 1)
                     : reinterpret_cast<unsigned long long>(rings + (static_cast<size_t>(s) * 2 + 0) * R * W);
       sh.dst[0] = d;
     }
     if (e_last >= 0) {
       unsigned long long d = 0;
-      if (!stalled && sr >= 0)
+      if (!stalled && sr >= 0 && (r_intra || index_ok(a.status, (static_cast<int64_t>(s) * 2 + 2) * R * W - 1, a.ring_len)))
         d = r_intra ? kRemoteDst | cluster_addr(sh.lin, static_cast<int>(rank) + 1 == C ? 0u : rank + 1)
                     : reinterpret_cast<unsigned long long>(rings + (static_cast<size_t>(s) * 2 + 1) * R * W);
       sh.dst[1] = d;
@@ -423,8 +429,8 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
     const int tr = s * 2 + 0;                                 // side 0 of boundary s
     int dl_next = 0, dr_next = 0;
     if (replay && K > 0) {
-      if (left_reader) dl_next = __ldg(trace_in + tl);
-      if (right_reader) dr_next = __ldg(trace_in + tr);
+      if (left_reader && index_ok(a.status, tl, a.trace_len)) dl_next = __ldg(trace_in + tl);
+      if (right_reader && index_ok(a.status, tr, a.trace_len)) dr_next = __ldg(trace_in + tr);
     }
 
     // Only the warps that read a halo or hand an edge on need to stop after
@@ -453,7 +459,8 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
         auto edge_step = [&](real (&in)[E], real (&out)[E], int k) {
           if (left_reader && !failed) {
             const int d = dl_next;
-            if (replay && k + 1 < K) dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
+            if (replay && k + 1 < K && index_ok(a.status, static_cast<int64_t>(k + 1) * tstride + tl, a.trace_len))
+              dl_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tl);
             real val;
             if (fetch_halo<real>(a, sh.lin, k, replay, trace_out, static_cast<size_t>(k) * tstride + tl, d, val))
               in[0] = val;
@@ -462,7 +469,8 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
           }
           if (right_reader && !failed) {
             const int d = dr_next;
-            if (replay && k + 1 < K) dr_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tr);
+            if (replay && k + 1 < K && index_ok(a.status, static_cast<int64_t>(k + 1) * tstride + tr, a.trace_len))
+              dr_next = __ldg(trace_in + static_cast<size_t>(k + 1) * tstride + tr);
             real val;
             if (fetch_halo<real>(a, sh.rin, k, replay, trace_out, static_cast<size_t>(k) * tstride + tr, d, val)) {
 #pragma unroll
@@ -493,11 +501,13 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
             sh.own_r[ver & (R - 1)] = x;
           }
           if (a.snap && ver % a.snap_every == 0) {  // owners record the state at step ver
-            real* row = static_cast<real*>(a.snap) + static_cast<size_t>(ver / a.snap_every) * N;
+            const int64_t row0 = static_cast<int64_t>(ver / a.snap_every) * N;
+            real* row = static_cast<real*>(a.snap) + row0;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
               const int p = Win::pos(warp, lane, e);
-              if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) row[a0 - 1 + p] = out[e];
+              if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc) && index_ok(a.status, row0 + a0 - 1 + p, a.snap_len))
+                row[a0 - 1 + p] = out[e];
             }
           }
         };
@@ -527,7 +537,8 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
-      if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc)) uout[a0 - 1 + p] = v[e];
+      if (p >= 1 && p <= L && Win::owner(warp, lane, e, nwc) && index_ok(a.status, a0 - 1 + p, N))
+        uout[a0 - 1 + p] = v[e];
     }
     // The edge values of the last q steps, for a later resumed run: versions
     // K-q+1 .. K of this launch from the own rings (written by these same
@@ -537,15 +548,17 @@ __global__ void __launch_bounds__(max_async_threads(sizeof(real), E), 1) async_p
       const real* hi_ = static_cast<const real*>(a.hist_in);
       for (int j = 0; j < a.q; ++j) {
         const int ver = K - a.q + 1 + j;
-        if (e_first >= 0) {
-          const real x = ver >= 0 ? sh.own_l[ver & (R - 1)]
-                                  : (hi_ ? hi_[(static_cast<size_t>(s) * 2 + 0) * a.q + (ver + a.q - 1)] : sh.own_l[0]);
-          ho[(static_cast<size_t>(s) * 2 + 0) * a.q + j] = x;
-        }
-        if (e_last >= 0) {
-          const real x = ver >= 0 ? sh.own_r[ver & (R - 1)]
-                                  : (hi_ ? hi_[(static_cast<size_t>(s) * 2 + 1) * a.q + (ver + a.q - 1)] : sh.own_r[0]);
-          ho[(static_cast<size_t>(s) * 2 + 1) * a.q + j] = x;
+        for (int side = 0; side < 2; ++side) {
+          if ((side ? e_last : e_first) < 0) continue;
+          const real* own = side ? sh.own_r : sh.own_l;
+          const int64_t hin = (static_cast<int64_t>(s) * 2 + side) * a.q + (ver + a.q - 1);
+          const int64_t hout = (static_cast<int64_t>(s) * 2 + side) * a.q + j;
+          real x = own[0];
+          if (ver >= 0)
+            x = own[ver & (R - 1)];
+          else if (hi_ && index_ok(a.status, hin, a.hist_len))
+            x = hi_[hin];
+          if (index_ok(a.status, hout, a.hist_len)) ho[hout] = x;
         }
       }
     }

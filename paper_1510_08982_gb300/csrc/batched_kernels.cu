@@ -20,6 +20,7 @@
 // waits are bounded.  Results are bit-identical to stepping each rod alone.
 #include <algorithm>
 
+#include "checked.cuh"
 #include "common.cuh"
 #include "impl.h"
 
@@ -49,7 +50,8 @@ __device__ bool wait_flag_at_least(const int* flag, int want, int* status, int64
 
 // A small rod advanced by one warp: positions lane*E + e.
 template <typename real, int E>
-__device__ void run_warp_rod(const BatchRod& rd, real* u, int lane, double one, float one_f) {
+__device__ void run_warp_rod(const BatchRod& rd, real* u, int lane, double one, float one_f, int* status,
+                             int64_t u_len) {
   real* x = u + rd.offset;
   const int N = static_cast<int>(rd.N);
   const real c1 = kparam<real>(rd.c1, rd.c1_f), cN = kparam<real>(rd.cN, rd.cN_f);
@@ -59,7 +61,7 @@ __device__ void run_warp_rod(const BatchRod& rd, real* u, int lane, double one, 
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = lane * E + e;
-    real y = p < N ? x[p] : static_cast<real>(0);
+    real y = p < N && index_ok(status, rd.offset + p, u_len) ? x[p] : static_cast<real>(0);
     if (p == 0) y = c1;
     if (p == N - 1) y = cN;
     v[e] = y;
@@ -75,7 +77,7 @@ __device__ void run_warp_rod(const BatchRod& rd, real* u, int lane, double one, 
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = lane * E + e;
-    if (p < N) x[p] = v[e];
+    if (p < N && index_ok(status, rd.offset + p, u_len)) x[p] = v[e];
   }
 }
 
@@ -100,7 +102,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
     const BatchItem it = a.items[idx];
 
     if (it.kind == kBatchWarps) {
-      if (warp < it.count) run_warp_rod<real, E>(a.rods[a.warp_rods[it.rod + warp]], u, lane, one, one_f);
+      if (warp < it.count)
+        run_warp_rod<real, E>(a.rods[a.warp_rods[it.rod + warp]], u, lane, one, one_f, a.status, a.u_len);
     } else if (it.kind == kBatchRod) {
       // The whole rod in this CTA; its ends are fixed, so nothing degrades.
       const BatchRod rd = a.rods[it.rod];
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        real y = p < N ? x[p] : static_cast<real>(0);
+        real y = p < N && index_ok(a.status, rd.offset + p, a.u_len) ? x[p] : static_cast<real>(0);
         if (p == 0) y = c1;
         if (p == N - 1) y = cN;
         v[e] = y;
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p < N && Win::owner(warp, lane, e, nwarps)) x[p] = v[e];
+        if (p < N && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, rd.offset + p, a.u_len)) x[p] = v[e];
       }
     } else {
       // One part: position p holds rod point a0 - lo + p, owned points
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         const int p = Win::pos(warp, lane, e);
         const int64_t g = a0 - lo + p;
         real y = static_cast<real>(0);
-        if (p < tile_end && g >= 0 && g < N) y = x[g];
+        if (p < tile_end && g >= 0 && g < N && index_ok(a.status, rd.offset + g, a.u_len)) y = x[g];
         if (g == 0) y = c1;
         if (g == N - 1) y = cN;
         v[e] = y;
@@ -172,13 +175,15 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         const int tb = static_cast<int>(std::min<int64_t>(T, rd.K - k0));
         warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
         if (k0 + tb >= rd.K) break;
-        real* mine = edges + it.slot * estride + (epoch & 1) * 2 * a.Tmax;
+        const int64_t mine0 = it.slot * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax;
+        real* mine = edges + mine0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int p = Win::pos(warp, lane, e);
           if (!Win::owner(warp, lane, e, nwarps)) continue;
-          if (p >= lo && p < lo + T) st_cg(mine + (p - lo), v[e]);
-          if (p >= hi - T && p < hi) st_cg(mine + a.Tmax + (p - (hi - T)), v[e]);
+          if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.edges_len)) st_cg(mine + (p - lo), v[e]);
+          if (p >= hi - T && p < hi && index_ok(a.status, mine0 + a.Tmax + (p - (hi - T)), a.edges_len))
+            st_cg(mine + a.Tmax + (p - (hi - T)), v[e]);
         }
         __syncthreads();
         if (tid == 0) {
@@ -196,19 +201,22 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
           break;
         }
         if (it.part > 0) {
-          const real* left = edges + (it.slot - 1) * estride + (epoch & 1) * 2 * a.Tmax;
+          const int64_t left0 = (it.slot - 1) * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax + a.Tmax;
+          const real* left = edges + left0;
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int p = Win::pos(warp, lane, e);
-            if (p >= lo - T && p < lo) v[e] = ld_cg(left + a.Tmax + (p - (lo - T)));
+            if (p >= lo - T && p < lo && index_ok(a.status, left0 + (p - (lo - T)), a.edges_len))
+              v[e] = ld_cg(left + (p - (lo - T)));
           }
         }
         if (it.part + 1 < it.nparts) {
-          const real* right = edges + (it.slot + 1) * estride + (epoch & 1) * 2 * a.Tmax;
+          const int64_t right0 = (it.slot + 1) * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax;
+          const real* right = edges + right0;
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int p = Win::pos(warp, lane, e);
-            if (p >= hi && p < hi + T) v[e] = ld_cg(right + (p - hi));
+            if (p >= hi && p < hi + T && index_ok(a.status, right0 + (p - hi), a.edges_len)) v[e] = ld_cg(right + (p - hi));
           }
         }
         ++epoch;
@@ -226,7 +234,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) x[a0 - lo + p] = v[e];
+        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, rd.offset + a0 - lo + p, a.u_len))
+          x[a0 - lo + p] = v[e];
       }
     }
     __syncthreads();

@@ -27,6 +27,7 @@
 // memory.  Neighbours in different clusters keep the rings in global memory.
 #include <algorithm>
 
+#include "checked.cuh"
 #include "cluster.cuh"
 #include "common.cuh"
 #include "impl.h"
@@ -44,7 +45,7 @@ namespace {
 __device__ int strip_version(const SegmentRun& a, const int* nb_prog, bool local, int j, size_t tidx) {
   int need;
   if (a.trace_in) {
-    const int d = a.trace_in[tidx];
+    const int d = index_ok(a.status, static_cast<int64_t>(tidx), a.trace_len) ? a.trace_in[tidx] : 0;
     if (d >= a.q) {
       raise_status(a.status, HEAT1D_ERR_TRACE);
       return -1;
@@ -68,7 +69,8 @@ __device__ int strip_version(const SegmentRun& a, const int* nb_prog, bool local
     }
   }
   const int v = a.trace_in ? need : min(V, j);
-  if (a.trace_out) a.trace_out[tidx] = static_cast<uint8_t>(j - v);
+  if (a.trace_out && index_ok(a.status, static_cast<int64_t>(tidx), a.trace_len))
+    a.trace_out[tidx] = static_cast<uint8_t>(j - v);
   return v;
 }
 
@@ -86,20 +88,21 @@ struct StripOut {
 template <typename real, int E, typename Win>
 __device__ __forceinline__ void publish_strips(const real (&v)[E], real* strips, int* my_prog, const StripOut& o,
                                                int s, int R, int T, int lo, int hi, int ver, bool stalled, int warp,
-                                               int lane, int nwarps, int tid) {
+                                               int lane, int nwarps, int tid, int* status, int64_t strips_len) {
   if (!stalled) {
-    real* mine = strips + (static_cast<size_t>(s) * R + (ver & (R - 1))) * 2 * T;
+    const int64_t mine0 = (static_cast<int64_t>(s) * R + (ver & (R - 1))) * 2 * T;
+    real* mine = strips + mine0;
     const uint32_t slot = static_cast<uint32_t>((ver & (R - 1)) * T * sizeof(real));
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
       if (!Win::owner(warp, lane, e, nwarps)) continue;
       if (p >= lo && p < lo + T) {
-        if (o.global) st_cg(mine + (p - lo), v[e]);
+        if (o.global && index_ok(status, mine0 + (p - lo), strips_len)) st_cg(mine + (p - lo), v[e]);
         if (o.l_ring) st_cluster(o.l_ring + slot + static_cast<uint32_t>((p - lo) * sizeof(real)), v[e]);
       }
       if (p >= hi - T && p < hi) {
-        if (o.global) st_cg(mine + T + (p - (hi - T)), v[e]);
+        if (o.global && index_ok(status, mine0 + T + (p - (hi - T)), strips_len)) st_cg(mine + T + (p - (hi - T)), v[e]);
         if (o.r_ring) st_cluster(o.r_ring + slot + static_cast<uint32_t>((p - (hi - T)) * sizeof(real)), v[e]);
       }
     }
@@ -189,9 +192,10 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
     const int64_t g = a0 - lo + p;
     real x = static_cast<real>(0);
     if (periodic) {  // halos wrap around the ring
-      if (p < tile_end) x = uin[((g % N) + N) % N];
+      const int64_t gw = ((g % N) + N) % N;
+      if (p < tile_end && index_ok(a.status, gw, N)) x = uin[gw];
     } else {
-      if (p < tile_end && g >= 0 && g < N) x = uin[g];
+      if (p < tile_end && g >= 0 && g < N && index_ok(a.status, g, N)) x = uin[g];
       if (g == 0) x = c1;
       if (g == N - 1) x = cN;
       if (p < tile_end && (g == 0 || g == N - 1)) fixed |= 1u << e;
@@ -204,10 +208,12 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
-      if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) static_cast<real*>(a.snap)[a0 + (p - lo)] = v[e];
+      if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, a0 + (p - lo), a.snap_len))
+        static_cast<real*>(a.snap)[a0 + (p - lo)] = v[e];
     }
   }
-  publish_strips<real, E, Win>(v, strips, my_prog, out, s, R, T, lo, hi, 0, stalled, warp, lane, nwarps, tid);
+  publish_strips<real, E, Win>(v, strips, my_prog, out, s, R, T, lo, hi, 0, stalled, warp, lane, nwarps, tid, a.status,
+                               a.ring_len);
   int parity = 0;
   bool ok = true;
   int j = 0;
@@ -242,44 +248,52 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
     }
     if (j > 0) {  // block 0 runs on the initial halos (version 0)
       if (sl >= 0) {
-        const real* left = strips + (static_cast<size_t>(sl) * R + (vl & (R - 1))) * 2 * T + T;
+        const int64_t left0 = (static_cast<int64_t>(sl) * R + (vl & (R - 1))) * 2 * T + T;
+        const real* left = strips + left0;
         const real* lloc = lstrip + static_cast<size_t>(vl & (R - 1)) * T;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int p = Win::pos(warp, lane, e);
-          if (p >= lo - T && p < lo) v[e] = l_intra ? lloc[p - (lo - T)] : ld_cg(left + (p - (lo - T)));
+          if (p >= lo - T && p < lo && (l_intra || index_ok(a.status, left0 + (p - (lo - T)), a.ring_len)))
+            v[e] = l_intra ? lloc[p - (lo - T)] : ld_cg(left + (p - (lo - T)));
         }
       }
       if (sr >= 0) {
-        const real* right = strips + (static_cast<size_t>(sr) * R + (vr & (R - 1))) * 2 * T;
+        const int64_t right0 = (static_cast<int64_t>(sr) * R + (vr & (R - 1))) * 2 * T;
+        const real* right = strips + right0;
         const real* rloc = rstrip + static_cast<size_t>(vr & (R - 1)) * T;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int p = Win::pos(warp, lane, e);
-          if (p >= hi && p < hi + T) v[e] = r_intra ? rloc[p - hi] : ld_cg(right + (p - hi));
+          if (p >= hi && p < hi + T && (r_intra || index_ok(a.status, right0 + (p - hi), a.ring_len)))
+            v[e] = r_intra ? rloc[p - hi] : ld_cg(right + (p - hi));
         }
       }
     }
     const int tb = static_cast<int>(std::min<int64_t>(T, a.K - k0));
     warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
     if (a.snap && (k0 + tb) % a.snap_every == 0) {  // owners record the state at step k0+tb
-      real* row = static_cast<real*>(a.snap) + static_cast<size_t>((k0 + tb) / a.snap_every) * N;
+      const int64_t row0 = ((k0 + tb) / a.snap_every) * N;
+      real* row = static_cast<real*>(a.snap) + row0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) row[a0 + (p - lo)] = v[e];
+        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, row0 + a0 + (p - lo), a.snap_len))
+          row[a0 + (p - lo)] = v[e];
       }
     }
     if (k0 + tb >= a.K) break;
     // The barrier inside also keeps sh_v stable until every thread has read it.
-    publish_strips<real, E, Win>(v, strips, my_prog, out, s, R, T, lo, hi, j + 1, stalled, warp, lane, nwarps, tid);
+    publish_strips<real, E, Win>(v, strips, my_prog, out, s, R, T, lo, hi, j + 1, stalled, warp, lane, nwarps, tid,
+                                 a.status, a.ring_len);
   }
 
   if (ok) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
-      if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) uout[a0 + (p - lo)] = v[e];
+      if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, a0 + (p - lo), N))
+        uout[a0 + (p - lo)] = v[e];
     }
   }
   // Every thread of the cluster reaches this point (all waits are bounded),

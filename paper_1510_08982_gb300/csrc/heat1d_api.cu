@@ -12,6 +12,7 @@
 
 #include <cuda_runtime.h>
 
+#include "checked.cuh"
 #include "heat1d.h"
 #include "impl.h"
 
@@ -56,6 +57,19 @@ __global__ void edges_history_kernel(const real* u, const int64_t* off, int S, i
       hist[(static_cast<size_t>(s) * 2 + 0) * q + j] = first;
       hist[(static_cast<size_t>(s) * 2 + 1) * q + j] = last;
     }
+  }
+}
+
+// Checked build only: one load and one store at index n (one past the end
+// of buf); the checks skip both and record HEAT1D_ERR_BOUNDS.  The index is
+// computed on the device so that no compiler can drop the checks.
+__global__ void checked_selftest_kernel(double* buf, int n, int* status) {
+  if constexpr (heat1d_dev::kChecked) {
+    if (threadIdx.x != 0) return;
+    const int i = n + static_cast<int>(blockIdx.x);  // = n
+    double x = 0.0;
+    if (heat1d_dev::index_ok(status, i, n)) x = buf[i];
+    if (heat1d_dev::index_ok(status, i, n)) buf[i] = x + 1.0;
   }
 }
 
@@ -351,7 +365,11 @@ SegmentRun base_run(heat1d* h, int64_t K) {
   if (h->snap && h->snap_every > 0 && K / h->snap_every + 1 <= h->snap_rows) {
     a.snap = h->snap;
     a.snap_every = h->snap_every;
+    a.snap_len = h->snap_rows * h->N;
   }
+  a.edges_len = 2 * h->S * 2 * static_cast<int64_t>(h->T);
+  a.ring_len = h->S * 2 * static_cast<int64_t>(h->R) * static_cast<int64_t>(h->esize / 4);  // tagged slot words
+  a.hist_len = h->S * 2 * static_cast<int64_t>(h->q);
   return a;
 }
 
@@ -414,6 +432,7 @@ int run_async_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_device
   if ((rc = stage_traces(h, tbytes, trace_out, out_on_device, trace_in, in_on_device, &out_dev, &in_dev))) return rc;
   a.trace_out = out_dev;
   a.trace_in = in_dev;
+  a.trace_len = static_cast<int64_t>(tbytes);
   const size_t hbytes = h->esize * static_cast<size_t>(h->S) * 2 * h->q;
   if (hbytes > h->hist_bytes) {
     cudaFree(h->hist[0]);
@@ -487,9 +506,11 @@ int run_blocked_streamed(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_de
   a.q = h->q;
   a.R = h->R;
   a.strips = h->strips;
+  a.strips_len = static_cast<int64_t>(h->ntiles) * h->R * 2 * h->Th;
   a.ver = h->done;
   a.trace_out = out_dev;
   a.trace_in = in_dev;
+  a.trace_len = static_cast<int64_t>(tbytes);
   a.status = h->status();
   a.spin_limit_ns = h->opts.spin_limit_ns;
   a.stall_tile = h->opts.stall_segment;
@@ -536,11 +557,13 @@ int run_blocked_common(heat1d* h, int64_t K, uint8_t* trace_out, int out_on_devi
   const size_t tbytes = static_cast<size_t>(nb) * (periodic ? h->S : h->S - 1) * 2;
   SegmentRun a = base_run(h, K);
   a.rings = h->strips;
+  a.ring_len = h->S * static_cast<int64_t>(h->R) * 2 * h->T;
   uint8_t* out_dev = nullptr;
   const uint8_t* in_dev = nullptr;
   if ((rc = stage_traces(h, tbytes, trace_out, out_on_device, trace_in, in_on_device, &out_dev, &in_dev))) return rc;
   a.trace_out = out_dev;
   a.trace_in = in_dev;
+  a.trace_len = static_cast<int64_t>(tbytes);
   a.cluster = heat1d_impl::blocked_cluster_size(h->dtype, E, threads, static_cast<int>(h->S), h->R, h->T,
                                                 h->opts.cluster);
   if (a.cluster < 1)
@@ -871,6 +894,31 @@ int heat1d_set_state(heat1d_t h, const void* state, int on_device) {
   return HEAT1D_OK;
 }
 
+int heat1d_checked(void) { return heat1d_dev::kChecked ? 1 : 0; }
+
+int heat1d_checked_selftest(void) {
+  if (!heat1d_dev::kChecked) return fail(HEAT1D_ERR_INVAL, "heat1d_checked_selftest: not a bounds-checked build");
+  double* buf = nullptr;
+  int* status = nullptr;
+  HEAT1D_CUDA(cudaMalloc(&buf, 4 * sizeof(double)));
+  if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) {
+    cudaFree(buf);
+    return cuda_fail(cudaGetLastError(), "cudaMalloc(status)");
+  }
+  int st = 0;
+  cudaError_t e = cudaMemset(status, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    checked_selftest_kernel<<<1, 32>>>(buf, 4, status);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  cudaFree(status);
+  if (e != cudaSuccess) return cuda_fail(e, "heat1d_checked_selftest");
+  return st;
+}
+
 int heat1d_sync(heat1d_t h) {
   if (!h) return fail(HEAT1D_ERR_INVAL, "null handle");
   HEAT1D_CUDA(cudaStreamSynchronize(h->stream));
@@ -880,6 +928,7 @@ int heat1d_sync(heat1d_t h) {
     HEAT1D_CUDA(cudaMemset(h->status(), 0, sizeof(int)));
     if (st == HEAT1D_ERR_TIMEOUT) return fail(st, "a device-side wait exceeded spin_limit_ns");
     if (st == HEAT1D_ERR_TRACE) return fail(st, "a replay trace entry is >= q");
+    if (st == HEAT1D_ERR_BOUNDS) return fail(st, "a kernel index was out of bounds (checked build)");
     return fail(st, "device status " + std::to_string(st));
   }
   return HEAT1D_OK;
@@ -903,6 +952,7 @@ struct heat1d_batch {
   void* d_ctl = nullptr;  // [0]: queue counter, [32]: status word
   int* d_flags = nullptr;
   void* d_edges = nullptr;
+  int64_t u_len = 0;  // values of the packed state the rods cover (max offset + N)
   cudaStream_t last_stream = nullptr;
 };
 
@@ -1014,6 +1064,7 @@ heat1d_batch_t heat1d_batch_create(const heat1d_rod* rods, int64_t nrods, int dt
   if (o) opts = *o;
   heat1d_batch* b = new heat1d_batch();
   b->dtype = dtype;
+  for (int64_t i = 0; i < nrods; ++i) b->u_len = std::max<int64_t>(b->u_len, rods[i].offset + rods[i].N);
   b->esize = dtype == HEAT1D_F64 ? 8 : 4;
   b->E = opts.elems_per_thread ? opts.elems_per_thread : (dtype == HEAT1D_F64 ? 8 : 16);
   b->threads = opts.block_threads ? opts.block_threads : 256;
@@ -1094,6 +1145,8 @@ int heat1d_batch_run(heat1d_batch_t b, void* u_packed, void* stream) {
   a.counter = static_cast<unsigned*>(b->d_ctl);
   a.flags = b->d_flags;
   a.edges = b->d_edges;
+  a.u_len = b->u_len;
+  a.edges_len = 4 * static_cast<int64_t>(b->T) * std::max<int64_t>(b->nparts, 1);
   a.Tmax = b->T;
   a.one = 1.0;
   a.one_f = 1.0f;
@@ -1115,8 +1168,9 @@ int heat1d_batch_sync(heat1d_batch_t b) {
   HEAT1D_CUDA(cudaMemcpy(&st, static_cast<int*>(b->d_ctl) + 32, sizeof(int), cudaMemcpyDeviceToHost));
   if (st != 0) {
     HEAT1D_CUDA(cudaMemset(static_cast<int*>(b->d_ctl) + 32, 0, sizeof(int)));
-    return fail(st, st == HEAT1D_ERR_TIMEOUT ? "a device-side wait exceeded spin_limit_ns"
-                                             : "device status " + std::to_string(st));
+    return fail(st, st == HEAT1D_ERR_TIMEOUT  ? "a device-side wait exceeded spin_limit_ns"
+                    : st == HEAT1D_ERR_BOUNDS ? "a kernel index was out of bounds (checked build)"
+                                              : "device status " + std::to_string(st));
   }
   return HEAT1D_OK;
 }

@@ -62,6 +62,9 @@ struct SegmentRun {
   // cluster hand their edge values to each other through distributed shared
   // memory; the others through the global rings.
   int cluster;
+  // Buffer extents, in elements, for the bounds-checked build (checked.cuh):
+  // snapshots, trace (bytes), rings or strips, edges, edge histories.
+  int64_t snap_len, trace_len, ring_len, edges_len, hist_len;
 };
 
 // Arguments of one temporally blocked synchronous run streamed through HBM.
@@ -187,6 +190,7 @@ struct StreamAsyncRun {
   int* status;
   int64_t spin_limit_ns;
   int64_t stall_tile;      // -1: off; else that tile never publishes (failure test)
+  int64_t strips_len, trace_len;  // extents in elements / bytes (bounds-checked build)
 };
 // Publishes version 0 of every tile's strips (the initial state) and sets the
 // version counters to 0; then the persistent launch (cooperative, `grid` CTAs
@@ -235,6 +239,7 @@ struct BatchRun {
   int* status;
   int64_t spin_limit_ns;
   int stall_slot;         // -1: off; else the part in that flag slot never publishes an epoch (failure test)
+  int64_t u_len, edges_len;  // extents of u and edges in elements (bounds-checked build)
 };
 
 // Batched launch: `grid` CTAs (all resident) of `threads` threads, E points

@@ -203,6 +203,7 @@ extern "C" int heat1d_run_sync_noalloc(const void* u_in, void* u_out, int64_t N,
     a.spin_limit_ns = 2000000000LL;
     a.T = T;
     a.edges = scratch + kEdgeOffset;
+    a.edges_len = 2 * S * 2 * static_cast<int64_t>(T);
     a.barrier = reinterpret_cast<unsigned*>(scratch);
     a.stall_segment = -1;
     rc = heat1d_impl::launch_sync_persistent(a, dtype, E, threads, st);

@@ -29,6 +29,7 @@
 #include <algorithm>
 
 #include "bulk.cuh"
+#include "checked.cuh"
 #include "common.cuh"
 #include "impl.h"
 
@@ -43,7 +44,7 @@ namespace {
 __device__ int tile_strip_version(const StreamAsyncRun& a, const int* nb_ver, int b, size_t tidx) {
   int need;
   if (a.trace_in) {
-    const int d = a.trace_in[tidx];
+    const int d = index_ok(a.status, static_cast<int64_t>(tidx), a.trace_len) ? a.trace_in[tidx] : 0;
     if (d >= a.q) {
       raise_status(a.status, HEAT1D_ERR_TRACE);
       return -1;
@@ -68,7 +69,8 @@ __device__ int tile_strip_version(const StreamAsyncRun& a, const int* nb_ver, in
     }
   }
   const int v = a.trace_in ? need : min(V, b);
-  if (a.trace_out) a.trace_out[tidx] = static_cast<uint8_t>(b - v);
+  if (a.trace_out && index_ok(a.status, static_cast<int64_t>(tidx), a.trace_len))
+    a.trace_out[tidx] = static_cast<uint8_t>(b - v);
   return v;
 }
 
@@ -99,11 +101,14 @@ __global__ void stream_async_setup_kernel(StreamAsyncRun a) {
   for (int64_t j = blockIdx.x; j < a.ntiles; j += gridDim.x) {
     const int64_t lo = j * a.W;
     const int64_t L = std::min<int64_t>(a.W, a.N - lo);
-    real* s0 = strips + static_cast<size_t>(j) * a.R * 2 * Th;  // version 0 sits in slot 0
+    const int64_t s00 = j * a.R * 2 * Th;
+    real* s0 = strips + s00;  // version 0 sits in slot 0
     for (int i = threadIdx.x; i < Th; i += blockDim.x) {
       const int64_t gf = lo + i, gl = lo + L - Th + i;
-      s0[i] = gf < a.N ? u[gf] : static_cast<real>(0);
-      s0[Th + i] = gl >= 0 ? u[gl] : static_cast<real>(0);
+      if (index_ok(a.status, s00 + i, a.strips_len))
+        s0[i] = gf < a.N && index_ok(a.status, gf, a.N) ? u[gf] : static_cast<real>(0);
+      if (index_ok(a.status, s00 + Th + i, a.strips_len))
+        s0[Th + i] = gl >= 0 && index_ok(a.status, gl, a.N) ? u[gl] : static_cast<real>(0);
     }
     if (threadIdx.x == 0) a.ver[j] = 0;
   }
@@ -181,13 +186,16 @@ __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_async_kernel
         const unsigned hb = static_cast<unsigned>(Th) * sizeof(real), ob = static_cast<unsigned>(W) * sizeof(real);
         const unsigned bytes = ob + (vl >= 0 ? hb : 0u) + hb;
         mbar_arrive_expect_tx(&full[st], bytes);
-        bulk_copy_to_shared(stg + Th, u + j * W, ob, &full[st]);
-        if (vl >= 0)  // the left neighbour's last Th points
-          bulk_copy_to_shared(stg, strips + ((static_cast<size_t>(j - 1) * R + (vl & (R - 1))) * 2 + 1) * Th, hb,
-                              &full[st]);
-        // the right neighbour's first Th points
-        bulk_copy_to_shared(stg + Th + W, strips + (static_cast<size_t>(j + 1) * R + (vr & (R - 1))) * 2 * Th, hb,
-                            &full[st]);
+        // (checked build: a copy whose range leaves its buffer is skipped; its
+        // stage then never fills and the compute warps' bounded wait ends the run)
+        const int64_t ls0 = ((static_cast<int64_t>(j - 1) * R + (vl & (R - 1))) * 2 + 1) * Th;
+        const int64_t rs0 = (static_cast<int64_t>(j + 1) * R + (vr & (R - 1))) * 2 * Th;
+        if (index_ok(a.status, j * W, N) && index_ok(a.status, j * W + W - 1, N))
+          bulk_copy_to_shared(stg + Th, u + j * W, ob, &full[st]);
+        if (vl >= 0 && index_ok(a.status, ls0, a.strips_len) && index_ok(a.status, ls0 + Th - 1, a.strips_len))
+          bulk_copy_to_shared(stg, strips + ls0, hb, &full[st]);  // the left neighbour's last Th points
+        if (index_ok(a.status, rs0, a.strips_len) && index_ok(a.status, rs0 + Th - 1, a.strips_len))
+          bulk_copy_to_shared(stg + Th + W, strips + rs0, hb, &full[st]);  // the right neighbour's first Th points
       }
       issued = i + 1;
       j += gridDim.x;
@@ -260,8 +268,10 @@ __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_async_kernel
       }
     } else {
       const int vl = stage_vl[st], vr = stage_vr[st];
-      const real* sl = vl >= 0 ? strips + ((static_cast<size_t>(j - 1) * R + (vl & (R - 1))) * 2 + 1) * Th : nullptr;
-      const real* sr = vr >= 0 ? strips + (static_cast<size_t>(j + 1) * R + (vr & (R - 1))) * 2 * Th : nullptr;
+      const int64_t sl0 = ((static_cast<int64_t>(j - 1) * R + (vl & (R - 1))) * 2 + 1) * Th;
+      const int64_t sr0 = (static_cast<int64_t>(j + 1) * R + (vr & (R - 1))) * 2 * Th;
+      const real* sl = vl >= 0 ? strips + sl0 : nullptr;
+      const real* sr = vr >= 0 ? strips + sr0 : nullptr;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = p0 + e;
@@ -269,11 +279,11 @@ __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_async_kernel
         real x = static_cast<real>(0);
         if (!failed) {
           if (p < Th) {
-            if (sl) x = ld_cg(sl + p);
+            if (sl && index_ok(a.status, sl0 + p, a.strips_len)) x = ld_cg(sl + p);
           } else if (p < Th + L) {
-            x = ld_cg(u + g);
+            if (index_ok(a.status, g, N)) x = ld_cg(u + g);
           } else if (p < Th + W + Th && p >= Th + W) {
-            if (sr) x = ld_cg(sr + (p - Th - W));
+            if (sr && index_ok(a.status, sr0 + (p - Th - W), a.strips_len)) x = ld_cg(sr + (p - Th - W));
           }
         }
         v[e] = x;
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_async_kernel
     }
     // Own points back in place, and strip version b+1: the first Th and the
     // last Th own points.
-    if (owns_all && p0 >= Th && p0 + E <= Th + L) {
+    if (owns_all && p0 >= Th && p0 + E <= Th + L && index_ok(a.status, gt, N) && index_ok(a.status, gt + E - 1, N)) {
 #pragma unroll
       for (int qq = 0; qq < E / VN; ++qq) {
         V x;
@@ -319,17 +329,19 @@ __global__ void __launch_bounds__(kStreamMaxThreads + 64, 1) stream_async_kernel
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = p0 + e;
-        if (p >= Th && p < Th + L && Win::owner(warp, lane, e, nwc)) __stcg(u + gt + e, v[e]);
+        if (p >= Th && p < Th + L && Win::owner(warp, lane, e, nwc) && index_ok(a.status, gt + e, N))
+          __stcg(u + gt + e, v[e]);
       }
     }
     if (b + 1 < nblocks) {
-      real* sv = strips + (static_cast<size_t>(j) * R + ((b + 1) & (R - 1))) * 2 * Th;
+      const int64_t sv0 = (static_cast<int64_t>(j) * R + ((b + 1) & (R - 1))) * 2 * Th;
+      real* sv = strips + sv0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = p0 + e;
         if (!Win::owner(warp, lane, e, nwc)) continue;
-        if (p >= Th && p < 2 * Th) st_cg(sv + (p - Th), v[e]);
-        if (p >= L && p < L + Th) st_cg(sv + Th + (p - L), v[e]);
+        if (p >= Th && p < 2 * Th && index_ok(a.status, sv0 + (p - Th), a.strips_len)) st_cg(sv + (p - Th), v[e]);
+        if (p >= L && p < L + Th && index_ok(a.status, sv0 + Th + (p - L), a.strips_len)) st_cg(sv + Th + (p - L), v[e]);
       }
     }
     __syncwarp();

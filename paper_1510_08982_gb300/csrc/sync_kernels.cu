@@ -13,6 +13,7 @@
 // bit for bit, to a barrier after every step (T = 1).
 #include <algorithm>
 
+#include "checked.cuh"
 #include "common.cuh"
 #include "impl.h"
 
@@ -86,9 +87,10 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
     const int64_t g = a0 - lo + p;
     real x = static_cast<real>(0);
     if (a.periodic) {  // halos wrap around the ring
-      if (p < tile_end) x = uin[((g % N) + N) % N];
+      const int64_t gw = ((g % N) + N) % N;
+      if (p < tile_end && index_ok(a.status, gw, N)) x = uin[gw];
     } else {
-      if (p < tile_end && g >= 0 && g < N) x = uin[g];
+      if (p < tile_end && g >= 0 && g < N && index_ok(a.status, g, N)) x = uin[g];
       if (g == 0) x = c1;
       if (g == N - 1) x = cN;
       if (p < tile_end && (g == 0 || g == N - 1)) fixed |= 1u << e;
@@ -103,7 +105,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
-      if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) static_cast<real*>(a.snap)[a0 + (p - lo)] = v[e];
+      if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, a0 + (p - lo), a.snap_len))
+        static_cast<real*>(a.snap)[a0 + (p - lo)] = v[e];
     }
   }
   int parity = 0;
@@ -112,23 +115,27 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
     const int tb = static_cast<int>(std::min<int64_t>(T, a.K - k0));
     warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
     if (a.snap && (k0 + tb) % a.snap_every == 0) {  // owners record the state at step k0+tb
-      real* row = static_cast<real*>(a.snap) + static_cast<size_t>((k0 + tb) / a.snap_every) * N;
+      const int64_t row0 = ((k0 + tb) / a.snap_every) * N;
+      real* row = static_cast<real*>(a.snap) + row0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) row[a0 + (p - lo)] = v[e];
+        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, row0 + a0 + (p - lo), a.snap_len))
+          row[a0 + (p - lo)] = v[e];
       }
     }
     if (k0 + tb >= a.K) break;
 
     // Publish the first T and the last T points of the segment.
-    real* mine = edges + (static_cast<size_t>(epoch & 1u) * a.S + s) * 2 * T;
+    const int64_t mine0 = (static_cast<int64_t>(epoch & 1u) * a.S + s) * 2 * T;
+    real* mine = edges + mine0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = Win::pos(warp, lane, e);
       if (!Win::owner(warp, lane, e, nwarps)) continue;
-      if (p >= lo && p < lo + T) st_cg(mine + (p - lo), v[e]);
-      if (p >= hi - T && p < hi) st_cg(mine + T + (p - (hi - T)), v[e]);
+      if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.edges_len)) st_cg(mine + (p - lo), v[e]);
+      if (p >= hi - T && p < hi && index_ok(a.status, mine0 + T + (p - (hi - T)), a.edges_len))
+        st_cg(mine + T + (p - (hi - T)), v[e]);
     }
     __syncthreads();
     if (tid == 0) {
@@ -140,19 +147,22 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
     // Reload the halos (every copy): the left neighbour's last T points, the
     // right neighbour's first T points.
     if (sl >= 0) {
-      const real* left = edges + (static_cast<size_t>(epoch & 1u) * a.S + sl) * 2 * T;
+      const int64_t left0 = (static_cast<int64_t>(epoch & 1u) * a.S + sl) * 2 * T + T;
+      const real* left = edges + left0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= lo - T && p < lo) v[e] = ld_cg(left + T + (p - (lo - T)));
+        if (p >= lo - T && p < lo && index_ok(a.status, left0 + (p - (lo - T)), a.edges_len))
+          v[e] = ld_cg(left + (p - (lo - T)));
       }
     }
     if (sr >= 0) {
-      const real* right = edges + (static_cast<size_t>(epoch & 1u) * a.S + sr) * 2 * T;
+      const int64_t right0 = (static_cast<int64_t>(epoch & 1u) * a.S + sr) * 2 * T;
+      const real* right = edges + right0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= hi && p < hi + T) v[e] = ld_cg(right + (p - hi));
+        if (p >= hi && p < hi + T && index_ok(a.status, right0 + (p - hi), a.edges_len)) v[e] = ld_cg(right + (p - hi));
       }
     }
     ++epoch;
@@ -161,7 +171,8 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int p = Win::pos(warp, lane, e);
-    if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps)) uout[a0 + (p - lo)] = v[e];
+    if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, a0 + (p - lo), N))
+      uout[a0 + (p - lo)] = v[e];
   }
 }
 

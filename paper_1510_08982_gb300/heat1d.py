@@ -16,20 +16,22 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libheat1d.so")
+# HEAT1D_CHECKED=1 in the environment loads the bounds-checked build
+# (libheat1d_checked.so, built by build.build(checked=True)) instead.
+LIB_PATH = os.path.join(_PKG, "libheat1d_checked.so" if os.environ.get("HEAT1D_CHECKED") == "1" else "libheat1d.so")
 
 F32, F64 = 0, 1
-OK, ERR_INVAL, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_RESIDENT, ERR_TRACE, ERR_OOM = 0, -1, -2, -3, -4, -5, -6
+OK, ERR_INVAL, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_RESIDENT, ERR_TRACE, ERR_OOM, ERR_BOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 STATUS_NAMES = {OK: "HEAT1D_OK", ERR_INVAL: "HEAT1D_ERR_INVAL", ERR_CUDA: "HEAT1D_ERR_CUDA",
                 ERR_TIMEOUT: "HEAT1D_ERR_TIMEOUT", ERR_NOT_RESIDENT: "HEAT1D_ERR_NOT_RESIDENT",
-                ERR_TRACE: "HEAT1D_ERR_TRACE", ERR_OOM: "HEAT1D_ERR_OOM"}
+                ERR_TRACE: "HEAT1D_ERR_TRACE", ERR_OOM: "HEAT1D_ERR_OOM", ERR_BOUNDS: "HEAT1D_ERR_BOUNDS"}
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_last_error", "heat1d_set_stream",
            "heat1d_set_snapshots", "heat1d_set_opts", "heat1d_get_opts", "heat1d_num_segments", "heat1d_set_u", "heat1d_get_u",
            "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync",
            "heat1d_run_async_blocked", "heat1d_replay_blocked", "heat1d_blocked_trace_bytes", "heat1d_blocked_segments",
-           "heat1d_async_cluster",
+           "heat1d_async_cluster", "heat1d_checked", "heat1d_checked_selftest",
            "heat1d_batch_create", "heat1d_batch_run", "heat1d_batch_sync", "heat1d_batch_describe",
            "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_adjoint", "heat1d_vjp",
            "heat1d_adjoint_batched", "heat1d_run_sync_noalloc", "heat1d_probe_fma", "heat1d_state_bytes",
@@ -40,6 +42,17 @@ class Heat1dError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s: %s" % (STATUS_NAMES.get(code, str(code)), msg))
         self.code = code
+
+
+def checked() -> bool:
+    """Whether the loaded library is the bounds-checked build."""
+    return bool(load().heat1d_checked())
+
+
+def checked_selftest() -> int:
+    """Checked build: the status of a kernel whose checked load and store
+    at one past the end of a buffer were skipped (ERR_BOUNDS expected)."""
+    return int(load().heat1d_checked_selftest())
 
 
 class Opts(ctypes.Structure):
@@ -91,6 +104,8 @@ def load():
         "heat1d_blocked_trace_bytes": (i64, [vp, i64]),
         "heat1d_blocked_segments": (i64, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
         "heat1d_async_cluster": (i32, [vp, i32]),
+        "heat1d_checked": (i32, []),
+        "heat1d_checked_selftest": (i32, []),
         "heat1d_state_bytes": (i64, [vp]),
         "heat1d_get_state": (i32, [vp, vp, i32]),
         "heat1d_set_state": (i32, [vp, vp, i32]),

@@ -109,3 +109,19 @@ def test_buffer_and_batch_arguments_are_checked_without_a_gpu(lib):
     assert "dtype" in heat1d.last_error()
     assert lib.heat1d_adjoint_batched(0, 100, 10, None, None, None, heat1d.F64, None, None, 0, 0, 3, None, 0,
                                       None, None, None, None, None) == heat1d.ERR_INVAL
+
+
+def test_normal_build_is_not_bounds_checked(lib):
+    """The normal library reports that it is not the checked build, and its
+    self-test refuses before launching anything (no GPU needed)."""
+    if os.environ.get("HEAT1D_CHECKED") == "1":
+        pytest.skip("the checked build is loaded in this process")
+    assert lib.heat1d_checked() == 0
+    assert lib.heat1d_checked_selftest() == heat1d.ERR_INVAL
+
+
+def test_checked_build_compiles():
+    """The bounds-checked variant builds for sm_103a beside the normal one
+    (its checks run on the GPU: tests/test_gpu_checked.py)."""
+    path = build_mod.build(checked=True)
+    assert path.endswith("libheat1d_checked.so") and os.path.exists(path)
