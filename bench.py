@@ -58,7 +58,7 @@ FP64_INSTR_PER_UPDATE = 3
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the asynchronous kernel on the
 # 2^20-point rod, from the committed ncu summary of that kernel.
-ASYNC_KERNEL_DRAM_BYTES = 8_503_552 + 1_792
+ASYNC_KERNEL_DRAM_BYTES = 8_492_544 + 2_560
 # DRAM bytes (read + write) per pass of the streamed kernel on the 2^26-point
 # FP32 rod, from the committed ncu summary (T = 1: 4 passes, T = 128: 2
 # passes); a launch makes ceil(K/T) passes of the same traffic.
@@ -502,6 +502,28 @@ def measure_streamed(dt, T, r, K, N, steps, warmup, leg=None, rank=0):
     clk = clocks.stop()
     h.sync()
     total = _max_over_ranks(torch, world, total, dev)
+    samples = [1, N // 3, N // 2 + 12345, N - 2]
+    if leg is not None:  # the synchronous result, sampled before the asynchronous runs reuse the handle
+        got_t = h.get_u(device=True)
+        got = got_t[torch.tensor(samples, device=dev)].cpu().numpy()
+        mp_ok = bool(float(got_t.min()) >= 0.0 and float(got_t.max()) <= 1.0)
+        del got_t
+    # The asynchronous run with temporal blocking on the same tiles (Eq.
+    # (eqn:async) per block of T steps, strips up to q-1 blocks old), timed
+    # after the synchronous one on the same handle, free-running with its
+    # trace recorded.
+    btr = h.new_blocked_trace(K)
+    for _ in range(max(1, min(warmup, 1))):
+        h.set_u(u0)
+        h.run_async_blocked(K, btr)
+    h.sync()
+    atotal = 0.0
+    for _ in range(steps):
+        h.set_u(u0)
+        atotal += event_seconds(torch, stream, lambda: h.run_async_blocked(K, btr))
+    h.sync()
+    atotal = _max_over_ranks(torch, world, atotal, dev)
+    a_hist = np.bincount(btr.cpu().numpy().reshape(-1), minlength=Q).tolist()
     secs = total / steps
     ups = world * (N - 2) * K / secs
     peaks, src = measured_peaks()
@@ -530,13 +552,25 @@ def measure_streamed(dt, T, r, K, N, steps, warmup, leg=None, rank=0):
                                    "HBM pass" % (N, dt.upper(), r, K, T), "N": N, "K": K, "T": T, "r": r,
                        "l2": "inputs larger than L2 (%d MB state)" % (N * esz >> 20)},
             "roofline": roof, "clocks": clk, "gpu_launches": 2 * steps}
+    a_secs = atotal / steps
+    a_ups = world * (N - 2) * K / a_secs
+    a_roof = {"kernel": "stream_async_kernel"}
+    if roof["bound"] == "hbm":
+        a_gbs = alg_bytes / a_secs / 1e9
+        a_roof.update({"bound": "hbm", "achieved": a_gbs, "peak": hbm, "unit": "GB/s", "frac": a_gbs / hbm})
+    else:
+        a_roof.update({"bound": "alu", "achieved": a_ups / 1e9, "peak": alu_ups / 1e9, "unit": "Gupdates/s",
+                       "frac": a_ups / alu_ups})
+    line["async_blocked"] = {
+        "updates_per_s": a_ups, "ms_per_run": a_secs * 1e3, "vs_sync": a_ups / ups, "roofline": a_roof,
+        "q": Q, "delay_histogram_blocks": a_hist,
+        "note": "asynchronous run with temporal blocking streamed through HBM (tiles as segments, strips "
+                "up to q-1 blocks old, trace recorded), same handle and T, timed after the synchronous run; "
+                "parity: tests/test_gpu_stream_async.py replays such runs in the oracle bit for bit"}
+    line["gpu_launches"] += 2 * steps
     if leg is not None:
-        # sampled outputs of the last timed run, each recomputed by the oracle
-        # on its dependency cone
-        got_t = h.get_u(device=True)
-        samples = [1, N // 3, N // 2 + 12345, N - 2]
-        got = got_t[torch.tensor(samples, device=dev)].cpu().numpy()
-        mp_ok = bool(float(got_t.min()) >= 0.0 and float(got_t.max()) <= 1.0)
+        # sampled outputs of the last timed synchronous run, each recomputed
+        # by the oracle on its dependency cone
         u0f = u0_host.astype(np.float64)
         errs = {}
         line["error"] = {"maximum_principle_holds": mp_ok, "oracle_cones": errs,
