@@ -342,6 +342,37 @@ heat1d_batch_t heat1d_batch_create(const heat1d_rod* rods, int64_t nrods, int dt
  * synchronisation, so the call can be captured in a CUDA graph. */
 int heat1d_batch_run(heat1d_batch_t b, void* u_packed, void* stream);
 
+/* Asynchronous batched run (the config-4 stretch of Section 3's model): the
+ * parts of every rod that is split over several CTAs are the segments of the
+ * blocked asynchronous model (Eq. (eqn:async) per block of T = halo_steps
+ * steps): after each block a part publishes its first and last T points as a
+ * strip version and starts the next block with its neighbouring parts'
+ * newest strips not newer than that block, waiting only while one is more
+ * than q-1 blocks old (q from heat1d_opts.q at heat1d_batch_create, default
+ * 3).  Rods that fit one CTA or one warp have no inner boundary and advance
+ * as in heat1d_batch_run.  trace_out (device, heat1d_batch_trace_bytes(b)
+ * bytes, or NULL) receives the delays: part by part (see
+ * heat1d_batch_rod_parts), uint8[ceil(K/T)][2] per part, [j][0] the delay of
+ * its read of the left neighbour in block j, [j][1] of the right one (0 in
+ * block 0 and at a rod end).  The launch is capturable in a CUDA graph. */
+int heat1d_batch_run_async(heat1d_batch_t b, void* u_packed, void* stream, uint8_t* trace_out);
+
+/* Replay of an asynchronous batched run with the delays given (device, the
+ * layout above); an entry >= q makes heat1d_batch_sync return
+ * HEAT1D_ERR_TRACE. */
+int heat1d_batch_replay(heat1d_batch_t b, void* u_packed, void* stream, const uint8_t* trace);
+
+/* Bytes of the trace of an asynchronous batched run. */
+int64_t heat1d_batch_trace_bytes(heat1d_batch_t b);
+
+/* The parts of rod `rod` (its index in the array given to
+ * heat1d_batch_create): returns their number P (1 for a rod that is not
+ * split); offsets (may be NULL; P+1 entries) receives the parts' first points
+ * relative to the rod's start and the rod length last; *trace_offset (may be
+ * NULL) the byte offset of its first part's trace (-1 if not split; part p's
+ * trace follows at trace_offset + 2*p*ceil(K/T)). */
+int64_t heat1d_batch_rod_parts(heat1d_batch_t b, int64_t rod, int64_t* offsets, int64_t* trace_offset);
+
 /* Waits for the last run's stream; returns its device status. */
 int heat1d_batch_sync(heat1d_batch_t b);
 

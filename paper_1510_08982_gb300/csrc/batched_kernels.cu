@@ -48,6 +48,44 @@ __device__ bool wait_flag_at_least(const int* flag, int want, int* status, int64
   return true;
 }
 
+// Asynchronous batched run: the strip version of a neighbouring part that
+// block j of this part reads -- the newest one not newer than j, waiting only
+// while it is more than q-1 blocks old (free run), or exactly j - d from the
+// trace (replay) -- with a bounded wait on the neighbour's version counter.
+// Records the delay at `tidx` (a byte of the trace).  One thread.  Returns the
+// version, or -1 after raising a failure.
+__device__ int part_strip_version(const BatchRun& a, const int* nb_ver, int j, int64_t tidx) {
+  int need;
+  if (a.async_mode == 2) {
+    const int d = index_ok(a.status, tidx, a.trace_len) ? a.trace_in[tidx] : 0;
+    if (d >= a.q) {
+      raise_status(a.status, HEAT1D_ERR_TRACE);
+      return -1;
+    }
+    need = j - min(d, j);
+  } else {
+    need = max(j - a.q + 1, 0);
+  }
+  int V = ld_acquire_gpu(nb_ver);
+  if (V < need) {
+    const uint64_t t0 = global_timer_ns();
+    unsigned spins = 0;
+    while ((V = ld_acquire_gpu(nb_ver)) < need) {
+      if ((++spins & 31u) == 0) {
+        if (status_failed(a.status)) return -1;
+        if (static_cast<int64_t>(global_timer_ns() - t0) > a.spin_limit_ns) {
+          raise_status(a.status, HEAT1D_ERR_TIMEOUT);
+          return -1;
+        }
+      }
+      __nanosleep(32);
+    }
+  }
+  const int v = a.async_mode == 2 ? need : min(V, j);
+  if (a.trace_out && index_ok(a.status, tidx, a.trace_len)) a.trace_out[tidx] = static_cast<uint8_t>(j - v);
+  return v;
+}
+
 // A small rod advanced by one warp: positions lane*E + e.
 template <typename real, int E>
 __device__ void run_warp_rod(const BatchRod& rd, real* u, int lane, double one, float one_f, int* status,
@@ -81,12 +119,15 @@ __device__ void run_warp_rod(const BatchRod& rd, real* u, int lane, double one, 
   }
 }
 
-template <typename real, int E>
+// kAsync: the launch of an asynchronous batched run (a separate instance, so
+// that the synchronous launch carries none of the asynchronous code).
+template <typename real, int E, bool kAsync>
 __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_kernel(BatchRun a) {
   using Win = Window<E, sync_window_halo(sizeof(real), E)>;
   __shared__ WindowShared<real, Win::H> sh;
   __shared__ int sh_item;
   __shared__ int sh_ok;
+  __shared__ int sh_v[2];  // asynchronous parts: strip versions read by this block (-1: failed)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   real* u = static_cast<real*>(a.u);
   real* edges = static_cast<real*>(a.edges);
@@ -132,6 +173,127 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
         if (p < N && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, rd.offset + p, a.u_len)) x[p] = v[e];
+      }
+    } else if (kAsync) {
+      // One part of a rod run asynchronously: the tile as in the synchronous
+      // part below; after each block of T steps the part publishes its first
+      // and last T points as strip version j+1 (a ring of R versions per
+      // part, release-stored version counter) and starts block j+1 with its
+      // neighbours' newest strips not newer than j+1 (at most q-1 blocks old;
+      // the recorded ones in a replay), as the blocked asynchronous kernel
+      // does for the segments of one rod.
+      const BatchRod rd = a.rods[it.rod];
+      real* x = u + rd.offset;
+      const int64_t N = rd.N;
+      const int T = it.T, L = it.L, R = a.R;
+      const int64_t a0 = it.a0;
+      const bool first = it.part == 0, last = it.part + 1 == it.nparts;
+      const int P = nwarps * Win::D + 2 * Win::H;
+      const int lo = first ? 0 : (last ? P - L : T);
+      const int hi = lo + L;
+      const int tile_end = last ? hi : hi + T;
+      const real c1 = kparam<real>(rd.c1, rd.c1_f), cN = kparam<real>(rd.cN, rd.cN_f);
+      const Coef<real> coef{kparam<real>(rd.r, rd.r_f), kparam<real>(one, one_f)};
+      real* strips = static_cast<real*>(a.strips);
+      const int64_t sstride = static_cast<int64_t>(R) * 2 * a.Tmax;  // values per part
+      int* myflag = a.flags + it.slot;
+      const int64_t nb = (rd.K + T - 1) / T;
+      const int64_t toff = a.toff[it.slot];
+      real v[E];
+      unsigned fixed = 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        const int64_t g = a0 - lo + p;
+        real y = static_cast<real>(0);
+        if (p < tile_end && g >= 0 && g < N && index_ok(a.status, rd.offset + g, a.u_len)) y = x[g];
+        if (g == 0) y = c1;
+        if (g == N - 1) y = cN;
+        v[e] = y;
+        if (p < tile_end && (g == 0 || g == N - 1)) fixed |= 1u << e;
+      }
+      const int mode = Win::pos(warp, 0, 0) >= tile_end ? static_cast<int>(kTileIdle) : tile_mode<E>(fixed);
+      // Strip version `ver` of this part; the CTA barrier inside orders every
+      // thread's stores before the release of the version counter.
+      auto publish = [&](int ver) {
+        const int64_t mine0 = it.slot * sstride + static_cast<int64_t>(ver & (R - 1)) * 2 * a.Tmax;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int p = Win::pos(warp, lane, e);
+          if (!Win::owner(warp, lane, e, nwarps)) continue;
+          if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.strips_len))
+            st_cg(strips + mine0 + (p - lo), v[e]);
+          if (p >= hi - T && p < hi && index_ok(a.status, mine0 + a.Tmax + (p - (hi - T)), a.strips_len))
+            st_cg(strips + mine0 + a.Tmax + (p - (hi - T)), v[e]);
+        }
+        __syncthreads();
+        if (tid == 0 && it.slot != a.stall_slot) st_release_gpu(a.pver + it.slot, ver);
+      };
+      if (tid == 0) st_release_gpu(myflag, 1);  // loaded: neighbours may now overwrite their own points
+      publish(0);  // version 0: the initial state
+      bool ok = true;
+      int j = 0;
+      for (int64_t k0 = 0; k0 < rd.K; k0 += T, ++j) {
+        if (j > 0) {  // block 0 runs on the initial halos (version 0)
+          if (tid == 0 || tid == 32 || (blockDim.x <= 32 && tid == 0)) {
+            const bool left = tid == 0;
+            int ver = j;
+            if (left && it.part > 0) ver = part_strip_version(a, a.pver + it.slot - 1, j, toff + 2 * j + 0);
+            if (!left && it.part + 1 < it.nparts) ver = part_strip_version(a, a.pver + it.slot + 1, j, toff + 2 * j + 1);
+            sh_v[left ? 0 : 1] = ver;
+            if (blockDim.x <= 32) {  // one-warp CTA: thread 0 takes both sides
+              int vr = j;
+              if (it.part + 1 < it.nparts) vr = part_strip_version(a, a.pver + it.slot + 1, j, toff + 2 * j + 1);
+              sh_v[1] = vr;
+            }
+          }
+          __syncthreads();
+          const int vl = sh_v[0], vr = sh_v[1];
+          if (vl < 0 || vr < 0) {  // CTA-uniform: every thread reads the same words
+            ok = false;
+            break;
+          }
+          if (it.part > 0) {
+            const int64_t left0 = (it.slot - 1) * sstride + static_cast<int64_t>(vl & (R - 1)) * 2 * a.Tmax + a.Tmax;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int p = Win::pos(warp, lane, e);
+              if (p >= lo - T && p < lo && index_ok(a.status, left0 + (p - (lo - T)), a.strips_len))
+                v[e] = ld_cg(strips + left0 + (p - (lo - T)));
+            }
+          }
+          if (it.part + 1 < it.nparts) {
+            const int64_t right0 = (it.slot + 1) * sstride + static_cast<int64_t>(vr & (R - 1)) * 2 * a.Tmax;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int p = Win::pos(warp, lane, e);
+              if (p >= hi && p < hi + T && index_ok(a.status, right0 + (p - hi), a.strips_len))
+                v[e] = ld_cg(strips + right0 + (p - hi));
+            }
+          }
+        }
+        const int tb = static_cast<int>(std::min<int64_t>(T, rd.K - k0));
+        warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
+        if (k0 + tb >= rd.K) break;
+        // (the barrier inside also keeps sh_v stable until every thread has read it)
+        publish(j + 1);
+      }
+      (void)nb;
+      if (!ok) return;  // CTA-uniform; the status word holds the failure
+      // The neighbours must have loaded their halos before our points change.
+      if (tid == 0) {
+        bool w = true;
+        if (it.part > 0) w = wait_flag_at_least(myflag - 1, 1, a.status, a.spin_limit_ns);
+        if (w && it.part + 1 < it.nparts) w = wait_flag_at_least(myflag + 1, 1, a.status, a.spin_limit_ns);
+        sh_ok = w;
+      }
+      __syncthreads();
+      if (!sh_ok) return;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, rd.offset + a0 - lo + p, a.u_len))
+          x[a0 - lo + p] = v[e];
       }
     } else {
       // One part: position p holds rod point a0 - lo + p, owned points
@@ -254,7 +416,8 @@ int launch_batched_t(const BatchRun& a, int threads, int grid, cudaStream_t st) 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, batched_kernel<real, E>, a);
+  cudaError_t e = a.async_mode ? cudaLaunchKernelEx(&cfg, batched_kernel<real, E, true>, a)
+                               : cudaLaunchKernelEx(&cfg, batched_kernel<real, E, false>, a);
   if (e == cudaErrorCooperativeLaunchTooLarge) {
     cudaGetLastError();
     return HEAT1D_ERR_NOT_RESIDENT;
@@ -265,8 +428,13 @@ int launch_batched_t(const BatchRun& a, int threads, int grid, cudaStream_t st) 
 template <typename real, int E>
 int resident_batched_t(int threads) {
   int per_sm = 0, dev = 0, nsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<real, E>, threads, 0) != cudaSuccess)
+  // the residency of the smaller of the two instances (both must fit the grid)
+  int per_sm_async = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<real, E, false>, threads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_async, batched_kernel<real, E, true>, threads, 0) !=
+          cudaSuccess)
     return 0;
+  per_sm = std::min(per_sm, per_sm_async);
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   return per_sm * nsm;

@@ -954,6 +954,14 @@ struct heat1d_batch {
   void* d_edges = nullptr;
   int64_t u_len = 0;  // values of the packed state the rods cover (max offset + N)
   cudaStream_t last_stream = nullptr;
+  // asynchronous batched runs (allocated on first use)
+  int q = 3, R = 8;
+  std::vector<int64_t> part_rod, part_a0, part_L, part_toff;  // per part slot (host)
+  std::vector<int64_t> rod_first_slot;                        // per rod: first part slot, -1 if not split
+  int64_t trace_bytes = 0;
+  int* d_pver = nullptr;
+  void* d_strips = nullptr;
+  int64_t* d_toff = nullptr;
 };
 
 namespace {
@@ -965,6 +973,9 @@ void batch_free(heat1d_batch* b) {
   cudaFree(b->d_ctl);
   cudaFree(b->d_flags);
   cudaFree(b->d_edges);
+  cudaFree(b->d_pver);
+  cudaFree(b->d_strips);
+  cudaFree(b->d_toff);
 }
 
 // Plans the work items: rods that fit one warp window go into warp batches
@@ -984,6 +995,7 @@ int batch_plan(heat1d_batch* b, const heat1d_rod* rods, int64_t nrods, std::vect
   std::vector<Unit> units;
   std::vector<int> small;
   out_rods.resize(nrods);
+  b->rod_first_slot.assign(nrods, -1);
   for (int64_t j = 0; j < nrods; ++j) {
     const heat1d_rod& r = rods[j];
     if (r.N < 3 || r.K < 0 || r.offset < 0 || !(r.r > 0.0 && r.r <= 0.5))
@@ -1029,6 +1041,8 @@ int batch_plan(heat1d_batch* b, const heat1d_rod* rods, int64_t nrods, std::vect
     const int64_t base = r.N / P, extra = r.N % P;
     if (base < b->T) return fail(HEAT1D_ERR_INVAL, "batched rods: parts shorter than the halo depth");
     int64_t pos = 0;
+    b->rod_first_slot[un.first] = slot;
+    const int64_t nblocks = (r.K + b->T - 1) / b->T;
     for (int64_t p = 0; p < P; ++p) {
       const int64_t L = base + (p < extra ? 1 : 0);
       it.part = static_cast<int>(p);
@@ -1037,6 +1051,12 @@ int batch_plan(heat1d_batch* b, const heat1d_rod* rods, int64_t nrods, std::vect
       it.L = static_cast<int>(L);
       it.slot = slot++;
       it.a0 = pos;
+      // an asynchronous run records [ceil(K/T)][2] delays per part
+      b->part_rod.push_back(un.first);
+      b->part_a0.push_back(pos);
+      b->part_L.push_back(L);
+      b->part_toff.push_back(b->trace_bytes);
+      b->trace_bytes += 2 * nblocks;
       pos += L;
       items.push_back(it);
       b->counts[heat1d_impl::kBatchPart] += 1;
@@ -1070,6 +1090,14 @@ heat1d_batch_t heat1d_batch_create(const heat1d_rod* rods, int64_t nrods, int dt
   b->threads = opts.block_threads ? opts.block_threads : 256;
   b->T = opts.halo_steps ? opts.halo_steps : (dtype == HEAT1D_F64 ? 16 : 32);
   if (opts.spin_limit_ns > 0) b->spin_limit_ns = opts.spin_limit_ns;
+  if (opts.q < 0 || opts.q > 255) {
+    fail(HEAT1D_ERR_INVAL, "heat1d_batch_create: q must be 1..255 (0: 3)");
+    delete b;
+    return nullptr;
+  }
+  b->q = opts.q ? opts.q : 3;
+  b->R = 1;
+  while (b->R < 2 * b->q) b->R <<= 1;
   b->stall_slot = opts.stall_segment >= 0 && opts.stall_segment < INT_MAX ? static_cast<int>(opts.stall_segment) : -1;
   if ((b->E != 4 && b->E != 8 && b->E != 16 && !(b->E == 32 && b->esize == 4)) || b->threads % 32 != 0 ||
       b->threads < 32 ||
@@ -1131,12 +1159,44 @@ heat1d_batch_t heat1d_batch_create(const heat1d_rod* rods, int64_t nrods, int dt
   return b;
 }
 
-int heat1d_batch_run(heat1d_batch_t b, void* u_packed, void* stream) {
-  if (!b || !u_packed) return fail(HEAT1D_ERR_INVAL, "heat1d_batch_run: null argument");
+namespace {
+
+int batch_run_common(heat1d_batch* b, void* u_packed, void* stream, int async_mode, uint8_t* trace_out,
+                     const uint8_t* trace_in) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   b->last_stream = st;
   if (b->nitems == 0) return HEAT1D_OK;
   heat1d_impl::BatchRun a{};
+  if (async_mode && b->nparts > 0) {
+    if (!b->d_pver) {  // first asynchronous run: version counters, strip rings, trace offsets
+      cudaError_t e = cudaMalloc(&b->d_pver, sizeof(int) * b->nparts);
+      if (e == cudaSuccess)
+        e = cudaMalloc(&b->d_strips, b->esize * static_cast<size_t>(b->nparts) * b->R * 2 * b->T);
+      if (e == cudaSuccess) e = cudaMalloc(&b->d_toff, sizeof(int64_t) * b->nparts);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_toff, b->part_toff.data(), sizeof(int64_t) * b->nparts, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        cudaFree(b->d_pver);
+        cudaFree(b->d_strips);
+        cudaFree(b->d_toff);
+        b->d_pver = nullptr;
+        b->d_strips = nullptr;
+        b->d_toff = nullptr;
+        return cuda_fail(e, "heat1d_batch: asynchronous buffers");
+      }
+    }
+    a.async_mode = async_mode;
+    a.q = b->q;
+    a.R = b->R;
+    a.pver = b->d_pver;
+    a.strips = b->d_strips;
+    a.toff = b->d_toff;
+    a.trace_out = trace_out;
+    a.trace_in = trace_in;
+    a.strips_len = static_cast<int64_t>(b->nparts) * b->R * 2 * b->T;
+    a.trace_len = b->trace_bytes;
+    HEAT1D_CUDA(cudaMemsetAsync(b->d_pver, 0xff, sizeof(int) * b->nparts, st));
+  }
   a.rods = b->d_rods;
   a.warp_rods = b->d_warp_rods;
   a.items = b->d_items;
@@ -1159,6 +1219,46 @@ int heat1d_batch_run(heat1d_batch_t b, void* u_packed, void* stream) {
   if (rc == HEAT1D_ERR_NOT_RESIDENT) return fail(rc, "heat1d_batch_run: grid cannot be resident");
   if (rc) return cuda_fail(cudaGetLastError(), "launch_batched");
   return HEAT1D_OK;
+}
+
+}  // namespace
+
+int heat1d_batch_run(heat1d_batch_t b, void* u_packed, void* stream) {
+  if (!b || !u_packed) return fail(HEAT1D_ERR_INVAL, "heat1d_batch_run: null argument");
+  return batch_run_common(b, u_packed, stream, 0, nullptr, nullptr);
+}
+
+int heat1d_batch_run_async(heat1d_batch_t b, void* u_packed, void* stream, uint8_t* trace_out) {
+  if (!b || !u_packed) return fail(HEAT1D_ERR_INVAL, "heat1d_batch_run_async: null argument");
+  return batch_run_common(b, u_packed, stream, 1, trace_out, nullptr);
+}
+
+int heat1d_batch_replay(heat1d_batch_t b, void* u_packed, void* stream, const uint8_t* trace) {
+  if (!b || !u_packed) return fail(HEAT1D_ERR_INVAL, "heat1d_batch_replay: null argument");
+  if (!trace && b->nparts > 0) return fail(HEAT1D_ERR_INVAL, "heat1d_batch_replay: trace is NULL");
+  return batch_run_common(b, u_packed, stream, 2, nullptr, trace);
+}
+
+int64_t heat1d_batch_trace_bytes(heat1d_batch_t b) {
+  if (!b) return fail(HEAT1D_ERR_INVAL, "null batch");
+  return b->trace_bytes;
+}
+
+int64_t heat1d_batch_rod_parts(heat1d_batch_t b, int64_t rod, int64_t* offsets, int64_t* trace_offset) {
+  if (!b || rod < 0 || rod >= b->nrods) return fail(HEAT1D_ERR_INVAL, "heat1d_batch_rod_parts: bad argument");
+  const int64_t first = b->rod_first_slot[rod];
+  if (first < 0) {
+    if (trace_offset) *trace_offset = -1;
+    return 1;
+  }
+  int64_t P = 0;
+  while (first + P < b->nparts && b->part_rod[first + P] == rod) ++P;
+  if (offsets) {
+    for (int64_t p = 0; p < P; ++p) offsets[p] = b->part_a0[first + p];
+    offsets[P] = b->part_a0[first + P - 1] + b->part_L[first + P - 1];
+  }
+  if (trace_offset) *trace_offset = b->part_toff[first];
+  return P;
 }
 
 int heat1d_batch_sync(heat1d_batch_t b) {

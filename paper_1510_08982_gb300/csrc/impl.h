@@ -240,6 +240,18 @@ struct BatchRun {
   int64_t spin_limit_ns;
   int stall_slot;         // -1: off; else the part in that flag slot never publishes an epoch (failure test)
   int64_t u_len, edges_len;  // extents of u and edges in elements (bounds-checked build)
+  // Asynchronous batched run: the parts of each split rod are the segments of
+  // the blocked model (Eq. (eqn:async) per block of T steps, strips up to q-1
+  // blocks old); rods that fit one CTA or one warp have no inner boundary and
+  // run as above.
+  int async_mode;          // 0: synchronous; 1: free run (trace recorded); 2: replay of trace_in
+  int q, R;                // delay window in blocks; strip versions kept per part (power of two >= 2q)
+  int* pver;               // [nparts] newest strip version published, -1 at launch
+  void* strips;            // [nparts][R][2][Tmax] values: first and last T points of a part per version
+  const int64_t* toff;     // [nparts] byte offset of each part's trace: [ceil(K/T)][2], [j][0] the left read
+  uint8_t* trace_out;      // free run: delays, or null
+  const uint8_t* trace_in; // replay
+  int64_t strips_len, trace_len;
 };
 
 // Batched launch: `grid` CTAs (all resident) of `threads` threads, E points

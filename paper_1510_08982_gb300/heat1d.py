@@ -32,6 +32,7 @@ EXPORTS = ["heat1d_default_opts", "heat1d_create", "heat1d_destroy", "heat1d_las
            "heat1d_run_sync", "heat1d_run_async", "heat1d_trace_bytes", "heat1d_replay", "heat1d_sync",
            "heat1d_run_async_blocked", "heat1d_replay_blocked", "heat1d_blocked_trace_bytes", "heat1d_blocked_segments",
            "heat1d_async_cluster", "heat1d_checked", "heat1d_checked_selftest",
+           "heat1d_batch_run_async", "heat1d_batch_replay", "heat1d_batch_trace_bytes", "heat1d_batch_rod_parts",
            "heat1d_batch_create", "heat1d_batch_run", "heat1d_batch_sync", "heat1d_batch_describe",
            "heat1d_batch_destroy", "heat1d_run_batched", "heat1d_adjoint", "heat1d_vjp",
            "heat1d_adjoint_batched", "heat1d_run_sync_noalloc", "heat1d_probe_fma", "heat1d_state_bytes",
@@ -105,6 +106,10 @@ def load():
         "heat1d_blocked_segments": (i64, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
         "heat1d_async_cluster": (i32, [vp, i32]),
         "heat1d_checked": (i32, []),
+        "heat1d_batch_run_async": (i32, [vp, vp, vp, vp]),
+        "heat1d_batch_replay": (i32, [vp, vp, vp, vp]),
+        "heat1d_batch_trace_bytes": (i64, [vp]),
+        "heat1d_batch_rod_parts": (i64, [vp, i64, vp, ctypes.POINTER(ctypes.c_int64)]),
         "heat1d_checked_selftest": (i32, []),
         "heat1d_state_bytes": (i64, [vp]),
         "heat1d_get_state": (i32, [vp, vp, i32]),
@@ -531,6 +536,57 @@ class Batch:
             raise ValueError("u has the wrong dtype for this batch")
         st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
         _check(self.lib.heat1d_batch_run(self.b, ctypes.c_void_p(u.data_ptr()), st))
+
+    def run_async(self, u, trace=None):
+        """Asynchronous run: the parts of split rods exchange strips with
+        bounded block delays (heat1d_batch_run_async); trace: a CUDA uint8
+        tensor of trace_bytes() entries (or None)."""
+        torch = _torch()
+        self._check_u(u)
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        tp = None if trace is None else ctypes.c_void_p(self._trace_ptr(trace))
+        _check(self.lib.heat1d_batch_run_async(self.b, ctypes.c_void_p(u.data_ptr()), st, tp))
+
+    def replay(self, u, trace):
+        """Replay of an asynchronous run with the delays of `trace` (CUDA
+        uint8 tensor of trace_bytes() entries)."""
+        torch = _torch()
+        self._check_u(u)
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        _check(self.lib.heat1d_batch_replay(self.b, ctypes.c_void_p(u.data_ptr()), st,
+                                            ctypes.c_void_p(self._trace_ptr(trace))))
+
+    def trace_bytes(self) -> int:
+        return int(self.lib.heat1d_batch_trace_bytes(self.b))
+
+    def new_trace(self):
+        torch = _torch()
+        return torch.zeros(max(self.trace_bytes(), 1), dtype=torch.uint8, device="cuda")
+
+    def rod_parts(self, rod):
+        """(offsets, trace_offset) of a rod's parts: offsets has P+1 entries
+        (rod-relative part starts, then N); trace_offset is -1 for a rod that
+        is not split."""
+        n = int(self.lib.heat1d_batch_rod_parts(self.b, int(rod), None, None))
+        if n < 0:
+            raise Heat1dError(n, last_error())
+        off = np.zeros(n + 1, dtype=np.int64)
+        toff = ctypes.c_int64(0)
+        self.lib.heat1d_batch_rod_parts(self.b, int(rod), off.ctypes.data_as(ctypes.c_void_p), ctypes.byref(toff))
+        return off, int(toff.value)
+
+    def _check_u(self, u):
+        if not u.is_cuda or not u.is_contiguous():
+            raise ValueError("u must be a contiguous CUDA tensor")
+        if _dtype_code(u.dtype) != self.code:
+            raise ValueError("u has the wrong dtype for this batch")
+
+    def _trace_ptr(self, trace):
+        torch = _torch()
+        if not (isinstance(trace, torch.Tensor) and trace.is_cuda and trace.dtype == torch.uint8 and trace.is_contiguous()
+                and trace.numel() >= self.trace_bytes()):
+            raise ValueError("trace must be a contiguous CUDA uint8 tensor of trace_bytes() entries")
+        return trace.data_ptr()
 
     def sync(self):
         _check(self.lib.heat1d_batch_sync(self.b))
