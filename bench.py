@@ -807,17 +807,39 @@ def measure_uneven(dt, steps, warmup, e2e=True, leg=None):
         e2e_out = {"value": world * updates / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": total_n * esz,
                    "d2h_bytes_per_step": total_n * esz,
                    "path": "pinned host -> device, heat1d_batch_run, device -> host"}
+    # The asynchronous batched run on the same batch (the parts of split
+    # rods exchange strips with up to q-1 blocks of delay), free-running with
+    # its trace recorded, timed after the synchronous one.
+    atr = b.new_trace()
+    u.copy_(u0)
+    b.run_async(u, atr)
+    b.sync()
+    atotal = 0.0
+    for _ in range(max(1, steps)):
+        u.copy_(u0)
+        atotal += event_seconds(torch, stream, lambda: b.run_async(u, atr))
+    b.sync()
+    atotal = _max_over_ranks(torch, world, atotal, dev)
+    a_ups = world * updates / (atotal / max(1, steps))
+    a_got = u.cpu().numpy() if leg is not None else None
+    a_trace = atr.cpu().numpy()
     roof = alu_roofline("batched_kernel", ups, dt, alu)
     roof["traffic"] = None
     line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": warmup, "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dt, "data": "synthetic",
+            "async": {"updates_per_s": a_ups, "vs_sync": a_ups / ups,
+                      "frac": a_ups / alu[dt]["nominal_updates_per_s"], "q": Q, "T": opts.get("halo_steps"),
+                      "delay_histogram_blocks": np.bincount(a_trace.reshape(-1), minlength=Q).tolist(),
+                      "note": "asynchronous batched run (heat1d_batch_run_async): the parts of split rods are the "
+                              "segments of the blocked model; rods on one CTA or warp run as in the synchronous "
+                              "launch; timed after the synchronous replays, not part of value"},
             "config": {"workload": "uneven rods: 4096 rods, N log-U[256,65536], K log-U[1e3,1e5], r U[0.05,0.5], "
                                    "8 sine modes; one batched persistent launch replayed from a CUDA graph; tile "
                                    "and halo depth from the autotuner",
                        "rods": len(rods), "points": total_n, "updates": updates, "plan": info, "opts": opts,
                        "l2": "flushed between timed steps (256 MB write)"},
-            "roofline": roof, "clocks": clk, "e2e": e2e_out, "gpu_launches": steps}
+            "roofline": roof, "clocks": clk, "e2e": e2e_out, "gpu_launches": steps + 1 + max(1, steps)}
     if leg is not None:
         cheap = [j for j, r in enumerate(rods) if r.N * r.K <= 2e7]
         pick = [int(j) for j in np.random.default_rng(1).choice(cheap, size=24, replace=False)]
@@ -831,6 +853,26 @@ def measure_uneven(dt, steps, warmup, e2e=True, leg=None):
             r = rods[j]
             leg.submit(errs, "rod %d (N=%d, K=%d)" % (j, r.N, r.K), "sync", (r.u0, r.r, r.c1, r.cN, r.K),
                        {"dtype": np_dt}, compare=compare_exact(got[off[j]:off[j] + r.N]))
+        # the asynchronous run: four cheap split rods replayed by the oracle's
+        # split model from the recorded delays
+        T = int(opts.get("halo_steps") or b.describe()["halo_steps"])
+        split = [j for j in cheap if b.rod_parts(j)[0].size > 2][:4]
+        aerrs = {}
+        line["async"]["error"] = {"oracle": aerrs, "note": "split rods recomputed by the oracle's blocked model "
+                                                           "(async_blocked_split) from the recorded part delays"}
+        for j in split:
+            r = rods[j]
+            offs, toff = b.rod_parts(j)
+            P, nb = offs.size - 1, (r.K + T - 1) // T
+            parts = a_trace[toff:toff + 2 * P * nb].reshape(P, nb, 2)
+            rtr = np.zeros((nb, P - 1, 2), dtype=np.uint8)
+            for bnd in range(P - 1):
+                rtr[:, bnd, 0] = parts[bnd, :, 1]
+                rtr[:, bnd, 1] = parts[bnd + 1, :, 0]
+            u0r = r.u0.astype(np_dt).astype(np.float64)
+            leg.submit(aerrs, "rod %d (N=%d, K=%d, %d parts)" % (j, r.N, r.K, P), "async_blocked_split",
+                       (u0r, r.r, r.c1, r.cN, offs, Q, T, r.K, rtr), {"dtype": np_dt},
+                       compare=compare_exact(a_got[off[j]:off[j] + r.N]))
     b.close()
     return line
 
