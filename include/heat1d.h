@@ -165,9 +165,11 @@ int heat1d_get_u(heat1d_t h, void* u, int on_device);
 int heat1d_run_sync(heat1d_t h, int64_t K);
 
 /* Asynchronous run, Section 3 Eq. (eqn:async): advances the state by K steps
- * with no barrier.  Each segment publishes its two edge values after every
- * step with a release store of its version counter and reads its neighbours'
- * newest version v <= k (waiting only while v < k-q+1).  trace_out (may be
+ * with no barrier.  Each segment hands its two edge values on after every
+ * step, each value tagged with its version (into the neighbour's shared
+ * memory inside a thread-block cluster, else through a ring in global
+ * memory), and reads its neighbours' newest version v <= k (waiting only
+ * while none >= k-q+1 has arrived).  trace_out (may be
  * NULL) receives the delays actually used, heat1d_trace_bytes(h, K) bytes in
  * the layout above; trace_on_device says where it lives.  Host traces are
  * complete when heat1d_sync() returns. */
