@@ -217,14 +217,16 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
       // thread's stores before the release of the version counter.
       auto publish = [&](int ver) {
         const int64_t mine0 = it.slot * sstride + static_cast<int64_t>(ver & (R - 1)) * 2 * a.Tmax;
+        if (Win::touches(warp, lo, lo + T) || Win::touches(warp, hi - T, hi)) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int p = Win::pos(warp, lane, e);
-          if (!Win::owner(warp, lane, e, nwarps)) continue;
-          if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.strips_len))
-            st_cg(strips + mine0 + (p - lo), v[e]);
-          if (p >= hi - T && p < hi && index_ok(a.status, mine0 + a.Tmax + (p - (hi - T)), a.strips_len))
-            st_cg(strips + mine0 + a.Tmax + (p - (hi - T)), v[e]);
+          for (int e = 0; e < E; ++e) {
+            const int p = Win::pos(warp, lane, e);
+            if (!Win::owner(warp, lane, e, nwarps)) continue;
+            if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.strips_len))
+              st_cg(strips + mine0 + (p - lo), v[e]);
+            if (p >= hi - T && p < hi && index_ok(a.status, mine0 + a.Tmax + (p - (hi - T)), a.strips_len))
+              st_cg(strips + mine0 + a.Tmax + (p - (hi - T)), v[e]);
+          }
         }
         __syncthreads();
         if (tid == 0 && it.slot != a.stall_slot) st_release_gpu(a.pver + it.slot, ver);
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
             ok = false;
             break;
           }
-          if (it.part > 0) {
+          if (it.part > 0 && Win::touches(warp, lo - T, lo)) {
             const int64_t left0 = (it.slot - 1) * sstride + static_cast<int64_t>(vl & (R - 1)) * 2 * a.Tmax + a.Tmax;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
                 v[e] = ld_cg(strips + left0 + (p - (lo - T)));
             }
           }
-          if (it.part + 1 < it.nparts) {
+          if (it.part + 1 < it.nparts && Win::touches(warp, hi, hi + T)) {
             const int64_t right0 = (it.slot + 1) * sstride + static_cast<int64_t>(vr & (R - 1)) * 2 * a.Tmax;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -339,13 +341,15 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         if (k0 + tb >= rd.K) break;
         const int64_t mine0 = it.slot * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax;
         real* mine = edges + mine0;
+        if (Win::touches(warp, lo, lo + T) || Win::touches(warp, hi - T, hi)) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int p = Win::pos(warp, lane, e);
-          if (!Win::owner(warp, lane, e, nwarps)) continue;
-          if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.edges_len)) st_cg(mine + (p - lo), v[e]);
-          if (p >= hi - T && p < hi && index_ok(a.status, mine0 + a.Tmax + (p - (hi - T)), a.edges_len))
-            st_cg(mine + a.Tmax + (p - (hi - T)), v[e]);
+          for (int e = 0; e < E; ++e) {
+            const int p = Win::pos(warp, lane, e);
+            if (!Win::owner(warp, lane, e, nwarps)) continue;
+            if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.edges_len)) st_cg(mine + (p - lo), v[e]);
+            if (p >= hi - T && p < hi && index_ok(a.status, mine0 + a.Tmax + (p - (hi - T)), a.edges_len))
+              st_cg(mine + a.Tmax + (p - (hi - T)), v[e]);
+          }
         }
         __syncthreads();
         if (tid == 0) {
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
           ok = false;
           break;
         }
-        if (it.part > 0) {
+        if (it.part > 0 && Win::touches(warp, lo - T, lo)) {
           const int64_t left0 = (it.slot - 1) * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax + a.Tmax;
           const real* left = edges + left0;
 #pragma unroll
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
               v[e] = ld_cg(left + (p - (lo - T)));
           }
         }
-        if (it.part + 1 < it.nparts) {
+        if (it.part + 1 < it.nparts && Win::touches(warp, hi, hi + T)) {
           const int64_t right0 = (it.slot + 1) * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax;
           const real* right = edges + right0;
 #pragma unroll

@@ -93,17 +93,20 @@ __device__ __forceinline__ void publish_strips(const real (&v)[E], real* strips,
     const int64_t mine0 = (static_cast<int64_t>(s) * R + (ver & (R - 1))) * 2 * T;
     real* mine = strips + mine0;
     const uint32_t slot = static_cast<uint32_t>((ver & (R - 1)) * T * sizeof(real));
+    if (Win::touches(warp, lo, lo + T) || Win::touches(warp, hi - T, hi)) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int p = Win::pos(warp, lane, e);
-      if (!Win::owner(warp, lane, e, nwarps)) continue;
-      if (p >= lo && p < lo + T) {
-        if (o.global && index_ok(status, mine0 + (p - lo), strips_len)) st_cg(mine + (p - lo), v[e]);
-        if (o.l_ring) st_cluster(o.l_ring + slot + static_cast<uint32_t>((p - lo) * sizeof(real)), v[e]);
-      }
-      if (p >= hi - T && p < hi) {
-        if (o.global && index_ok(status, mine0 + T + (p - (hi - T)), strips_len)) st_cg(mine + T + (p - (hi - T)), v[e]);
-        if (o.r_ring) st_cluster(o.r_ring + slot + static_cast<uint32_t>((p - (hi - T)) * sizeof(real)), v[e]);
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        if (!Win::owner(warp, lane, e, nwarps)) continue;
+        if (p >= lo && p < lo + T) {
+          if (o.global && index_ok(status, mine0 + (p - lo), strips_len)) st_cg(mine + (p - lo), v[e]);
+          if (o.l_ring) st_cluster(o.l_ring + slot + static_cast<uint32_t>((p - lo) * sizeof(real)), v[e]);
+        }
+        if (p >= hi - T && p < hi) {
+          if (o.global && index_ok(status, mine0 + T + (p - (hi - T)), strips_len))
+            st_cg(mine + T + (p - (hi - T)), v[e]);
+          if (o.r_ring) st_cluster(o.r_ring + slot + static_cast<uint32_t>((p - (hi - T)) * sizeof(real)), v[e]);
+        }
       }
     }
   }
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
       break;
     }
     if (j > 0) {  // block 0 runs on the initial halos (version 0)
-      if (sl >= 0) {
+      if (sl >= 0 && Win::touches(warp, lo - T, lo)) {
         const int64_t left0 = (static_cast<int64_t>(sl) * R + (vl & (R - 1))) * 2 * T + T;
         const real* left = strips + left0;
         const real* lloc = lstrip + static_cast<size_t>(vl & (R - 1)) * T;
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) async_bl
             v[e] = l_intra ? lloc[p - (lo - T)] : ld_cg(left + (p - (lo - T)));
         }
       }
-      if (sr >= 0) {
+      if (sr >= 0 && Win::touches(warp, hi, hi + T)) {
         const int64_t right0 = (static_cast<int64_t>(sr) * R + (vr & (R - 1))) * 2 * T;
         const real* right = strips + right0;
         const real* rloc = rstrip + static_cast<size_t>(vr & (R - 1)) * T;

@@ -177,6 +177,12 @@ struct Window {
   // and 30 send).
   static_assert(H >= 1 && (2 * H <= E || H == E), "halo must be at most half a lane, or one whole lane");
   __device__ static __forceinline__ int pos(int warp, int lane, int e) { return warp * D + lane * E + e; }
+  // Whether the warp's window holds any of the positions [a, b): a test that
+  // is the same for every lane, so that the warps holding none of an edge
+  // strip skip the per-point loop that reads or writes it.
+  __device__ static __forceinline__ bool touches(int warp, int a, int b) {
+    return warp * D < b && warp * D + 32 * E > a;
+  }
   __device__ static __forceinline__ bool owner(int warp, int lane, int e, int nwarps) {
     if (lane == 0 && e < H) return warp == 0;
     if (lane == 31 && e >= E - H) return warp == nwarps - 1;

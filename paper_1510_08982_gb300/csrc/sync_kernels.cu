@@ -129,13 +129,15 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
     // Publish the first T and the last T points of the segment.
     const int64_t mine0 = (static_cast<int64_t>(epoch & 1u) * a.S + s) * 2 * T;
     real* mine = edges + mine0;
+    if (Win::touches(warp, lo, lo + T) || Win::touches(warp, hi - T, hi)) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int p = Win::pos(warp, lane, e);
-      if (!Win::owner(warp, lane, e, nwarps)) continue;
-      if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.edges_len)) st_cg(mine + (p - lo), v[e]);
-      if (p >= hi - T && p < hi && index_ok(a.status, mine0 + T + (p - (hi - T)), a.edges_len))
-        st_cg(mine + T + (p - (hi - T)), v[e]);
+      for (int e = 0; e < E; ++e) {
+        const int p = Win::pos(warp, lane, e);
+        if (!Win::owner(warp, lane, e, nwarps)) continue;
+        if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.edges_len)) st_cg(mine + (p - lo), v[e]);
+        if (p >= hi - T && p < hi && index_ok(a.status, mine0 + T + (p - (hi - T)), a.edges_len))
+          st_cg(mine + T + (p - (hi - T)), v[e]);
+      }
     }
     __syncthreads();
     if (tid == 0) {
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
 
     // Reload the halos (every copy): the left neighbour's last T points, the
     // right neighbour's first T points.
-    if (sl >= 0) {
+    if (sl >= 0 && Win::touches(warp, lo - T, lo)) {
       const int64_t left0 = (static_cast<int64_t>(epoch & 1u) * a.S + sl) * 2 * T + T;
       const real* left = edges + left0;
 #pragma unroll
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) sync_per
           v[e] = ld_cg(left + (p - (lo - T)));
       }
     }
-    if (sr >= 0) {
+    if (sr >= 0 && Win::touches(warp, hi, hi + T)) {
       const int64_t right0 = (static_cast<int64_t>(epoch & 1u) * a.S + sr) * 2 * T;
       const real* right = edges + right0;
 #pragma unroll
