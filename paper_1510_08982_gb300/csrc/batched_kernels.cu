@@ -119,6 +119,32 @@ __device__ void run_warp_rod(const BatchRod& rd, real* u, int lane, double one, 
   }
 }
 
+// The bookkeeping of the part a CTA holds (tile bounds, its neighbours'
+// slots, the rod's step count and placement).  It is written once per item
+// into shared memory and re-read at every exchange, so that none of it stays
+// in registers across the steps of a block: the step loop, the part's tile
+// and the warp refresh then have the registers to themselves (measured: with
+// the bookkeeping live, the compiler re-derived lane, warp and shared
+// addresses at every warp refresh, about five more instructions per step).
+struct PartState {
+  int lo, hi, T, slot, part, nparts;
+  int64_t K, a0, offset;
+};
+__device__ __forceinline__ PartState load_part(const PartState& s) {
+  const volatile PartState& v = s;
+  PartState r;
+  r.lo = v.lo;
+  r.hi = v.hi;
+  r.T = v.T;
+  r.slot = v.slot;
+  r.part = v.part;
+  r.nparts = v.nparts;
+  r.K = v.K;
+  r.a0 = v.a0;
+  r.offset = v.offset;
+  return r;
+}
+
 // kAsync: the launch of an asynchronous batched run (a separate instance, so
 // that the synchronous launch carries none of the asynchronous code).
 template <typename real, int E, bool kAsync>
@@ -128,6 +154,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
   __shared__ int sh_item;
   __shared__ int sh_ok;
   __shared__ int sh_v[2];  // asynchronous parts: strip versions read by this block (-1: failed)
+  __shared__ PartState sh_part;  // the part this CTA holds
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   real* u = static_cast<real*>(a.u);
   real* edges = static_cast<real*>(a.edges);
@@ -185,7 +212,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
       const BatchRod rd = a.rods[it.rod];
       real* x = u + rd.offset;
       const int64_t N = rd.N;
-      const int T = it.T, L = it.L, R = a.R;
+      const int T = it.T, L = it.L;
       const int64_t a0 = it.a0;
       const bool first = it.part == 0, last = it.part + 1 == it.nparts;
       const int P = nwarps * Win::D + 2 * Win::H;
@@ -195,10 +222,7 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
       const real c1 = kparam<real>(rd.c1, rd.c1_f), cN = kparam<real>(rd.cN, rd.cN_f);
       const Coef<real> coef{kparam<real>(rd.r, rd.r_f), kparam<real>(one, one_f)};
       real* strips = static_cast<real*>(a.strips);
-      const int64_t sstride = static_cast<int64_t>(R) * 2 * a.Tmax;  // values per part
       int* myflag = a.flags + it.slot;
-      const int64_t nb = (rd.K + T - 1) / T;
-      const int64_t toff = a.toff[it.slot];
       real v[E];
       unsigned fixed = 0;
 #pragma unroll
@@ -213,39 +237,44 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         if (p < tile_end && (g == 0 || g == N - 1)) fixed |= 1u << e;
       }
       const int mode = Win::pos(warp, 0, 0) >= tile_end ? static_cast<int>(kTileIdle) : tile_mode<E>(fixed);
+      if (tid == 0) sh_part = PartState{lo, hi, T, it.slot, it.part, it.nparts, rd.K, a0, rd.offset};
       // Strip version `ver` of this part; the CTA barrier inside orders every
       // thread's stores before the release of the version counter.
-      auto publish = [&](int ver) {
-        const int64_t mine0 = it.slot * sstride + static_cast<int64_t>(ver & (R - 1)) * 2 * a.Tmax;
-        if (Win::touches(warp, lo, lo + T) || Win::touches(warp, hi - T, hi)) {
+      auto publish = [&](const PartState& ps, int ver) {
+        const int64_t sstride = static_cast<int64_t>(a.R) * 2 * a.Tmax;  // values per part
+        const int64_t mine0 = ps.slot * sstride + static_cast<int64_t>(ver & (a.R - 1)) * 2 * a.Tmax;
+        if (Win::touches(warp, ps.lo, ps.lo + ps.T) || Win::touches(warp, ps.hi - ps.T, ps.hi)) {
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int p = Win::pos(warp, lane, e);
             if (!Win::owner(warp, lane, e, nwarps)) continue;
-            if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.strips_len))
-              st_cg(strips + mine0 + (p - lo), v[e]);
-            if (p >= hi - T && p < hi && index_ok(a.status, mine0 + a.Tmax + (p - (hi - T)), a.strips_len))
-              st_cg(strips + mine0 + a.Tmax + (p - (hi - T)), v[e]);
+            if (p >= ps.lo && p < ps.lo + ps.T && index_ok(a.status, mine0 + (p - ps.lo), a.strips_len))
+              st_cg(strips + mine0 + (p - ps.lo), v[e]);
+            if (p >= ps.hi - ps.T && p < ps.hi &&
+                index_ok(a.status, mine0 + a.Tmax + (p - (ps.hi - ps.T)), a.strips_len))
+              st_cg(strips + mine0 + a.Tmax + (p - (ps.hi - ps.T)), v[e]);
           }
         }
         __syncthreads();
-        if (tid == 0 && it.slot != a.stall_slot) st_release_gpu(a.pver + it.slot, ver);
+        if (tid == 0 && ps.slot != a.stall_slot) st_release_gpu(a.pver + ps.slot, ver);
       };
+      __syncthreads();  // every thread has loaded its points; sh_part written
       if (tid == 0) st_release_gpu(myflag, 1);  // loaded: neighbours may now overwrite their own points
-      publish(0);  // version 0: the initial state
+      publish(load_part(sh_part), 0);           // version 0: the initial state
       bool ok = true;
-      int j = 0;
-      for (int64_t k0 = 0; k0 < rd.K; k0 += T, ++j) {
+      for (int j = 0;; ++j) {
         if (j > 0) {  // block 0 runs on the initial halos (version 0)
+          const PartState ps = load_part(sh_part);
           if (tid == 0 || tid == 32 || (blockDim.x <= 32 && tid == 0)) {
+            const int64_t toff = a.toff[ps.slot];
             const bool left = tid == 0;
             int ver = j;
-            if (left && it.part > 0) ver = part_strip_version(a, a.pver + it.slot - 1, j, toff + 2 * j + 0);
-            if (!left && it.part + 1 < it.nparts) ver = part_strip_version(a, a.pver + it.slot + 1, j, toff + 2 * j + 1);
+            if (left && ps.part > 0) ver = part_strip_version(a, a.pver + ps.slot - 1, j, toff + 2 * j + 0);
+            if (!left && ps.part + 1 < ps.nparts) ver = part_strip_version(a, a.pver + ps.slot + 1, j, toff + 2 * j + 1);
             sh_v[left ? 0 : 1] = ver;
             if (blockDim.x <= 32) {  // one-warp CTA: thread 0 takes both sides
               int vr = j;
-              if (it.part + 1 < it.nparts) vr = part_strip_version(a, a.pver + it.slot + 1, j, toff + 2 * j + 1);
+              if (ps.part + 1 < ps.nparts) vr = part_strip_version(a, a.pver + ps.slot + 1, j, toff + 2 * j + 1);
               sh_v[1] = vr;
             }
           }
@@ -255,47 +284,56 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
             ok = false;
             break;
           }
-          if (it.part > 0 && Win::touches(warp, lo - T, lo)) {
-            const int64_t left0 = (it.slot - 1) * sstride + static_cast<int64_t>(vl & (R - 1)) * 2 * a.Tmax + a.Tmax;
+          const int64_t sstride = static_cast<int64_t>(a.R) * 2 * a.Tmax;
+          if (ps.part > 0 && Win::touches(warp, ps.lo - ps.T, ps.lo)) {
+            const int64_t left0 = (ps.slot - 1) * sstride + static_cast<int64_t>(vl & (a.R - 1)) * 2 * a.Tmax + a.Tmax;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
               const int p = Win::pos(warp, lane, e);
-              if (p >= lo - T && p < lo && index_ok(a.status, left0 + (p - (lo - T)), a.strips_len))
-                v[e] = ld_cg(strips + left0 + (p - (lo - T)));
+              if (p >= ps.lo - ps.T && p < ps.lo && index_ok(a.status, left0 + (p - (ps.lo - ps.T)), a.strips_len))
+                v[e] = ld_cg(strips + left0 + (p - (ps.lo - ps.T)));
             }
           }
-          if (it.part + 1 < it.nparts && Win::touches(warp, hi, hi + T)) {
-            const int64_t right0 = (it.slot + 1) * sstride + static_cast<int64_t>(vr & (R - 1)) * 2 * a.Tmax;
+          if (ps.part + 1 < ps.nparts && Win::touches(warp, ps.hi, ps.hi + ps.T)) {
+            const int64_t right0 = (ps.slot + 1) * sstride + static_cast<int64_t>(vr & (a.R - 1)) * 2 * a.Tmax;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
               const int p = Win::pos(warp, lane, e);
-              if (p >= hi && p < hi + T && index_ok(a.status, right0 + (p - hi), a.strips_len))
-                v[e] = ld_cg(strips + right0 + (p - hi));
+              if (p >= ps.hi && p < ps.hi + ps.T && index_ok(a.status, right0 + (p - ps.hi), a.strips_len))
+                v[e] = ld_cg(strips + right0 + (p - ps.hi));
             }
           }
         }
-        const int tb = static_cast<int>(std::min<int64_t>(T, rd.K - k0));
+        int tb;
+        {
+          const PartState ps = load_part(sh_part);
+          tb = static_cast<int>(std::min<int64_t>(ps.T, ps.K - static_cast<int64_t>(j) * ps.T));
+        }
         warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
-        if (k0 + tb >= rd.K) break;
+        const PartState ps = load_part(sh_part);
+        if (static_cast<int64_t>(j) * ps.T + tb >= ps.K) break;
         // (the barrier inside also keeps sh_v stable until every thread has read it)
-        publish(j + 1);
+        publish(ps, j + 1);
       }
-      (void)nb;
       if (!ok) return;  // CTA-uniform; the status word holds the failure
+      const PartState ps = load_part(sh_part);
+      int* pflag = a.flags + ps.slot;
       // The neighbours must have loaded their halos before our points change.
       if (tid == 0) {
         bool w = true;
-        if (it.part > 0) w = wait_flag_at_least(myflag - 1, 1, a.status, a.spin_limit_ns);
-        if (w && it.part + 1 < it.nparts) w = wait_flag_at_least(myflag + 1, 1, a.status, a.spin_limit_ns);
+        if (ps.part > 0) w = wait_flag_at_least(pflag - 1, 1, a.status, a.spin_limit_ns);
+        if (w && ps.part + 1 < ps.nparts) w = wait_flag_at_least(pflag + 1, 1, a.status, a.spin_limit_ns);
         sh_ok = w;
       }
       __syncthreads();
       if (!sh_ok) return;
+      real* px = u + ps.offset;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, rd.offset + a0 - lo + p, a.u_len))
-          x[a0 - lo + p] = v[e];
+        if (p >= ps.lo && p < ps.hi && Win::owner(warp, lane, e, nwarps) &&
+            index_ok(a.status, ps.offset + ps.a0 - ps.lo + p, a.u_len))
+          px[ps.a0 - ps.lo + p] = v[e];
       }
     } else {
       // One part: position p holds rod point a0 - lo + p, owned points
@@ -315,7 +353,6 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
       const int tile_end = last ? hi : hi + T;
       const real c1 = kparam<real>(rd.c1, rd.c1_f), cN = kparam<real>(rd.cN, rd.cN_f);
       const Coef<real> coef{kparam<real>(rd.r, rd.r_f), kparam<real>(one, one_f)};
-      const size_t estride = static_cast<size_t>(4) * a.Tmax;
       int* myflag = a.flags + it.slot;
       real v[E];
       unsigned fixed = 0;
@@ -331,34 +368,42 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
         if (p < tile_end && (g == 0 || g == N - 1)) fixed |= 1u << e;
       }
       const int mode = Win::pos(warp, 0, 0) >= tile_end ? static_cast<int>(kTileIdle) : tile_mode<E>(fixed);
+      if (tid == 0) sh_part = PartState{lo, hi, T, it.slot, it.part, it.nparts, rd.K, a0, rd.offset};
       __syncthreads();
       if (tid == 0) st_release_gpu(myflag, 1);  // loaded: neighbours may now overwrite their own points
       bool ok = true;
-      int epoch = 0;
-      for (int64_t k0 = 0; k0 < rd.K; k0 += T) {
-        const int tb = static_cast<int>(std::min<int64_t>(T, rd.K - k0));
+      for (int epoch = 0;; ++epoch) {
+        int tb;
+        {
+          const PartState ps = load_part(sh_part);
+          tb = static_cast<int>(std::min<int64_t>(ps.T, ps.K - static_cast<int64_t>(epoch) * ps.T));
+        }
         warp_advance<real, E, Win::H>(mode, v, fixed, coef, sh, parity, warp, lane, nwarps, blockDim.x, tb);
-        if (k0 + tb >= rd.K) break;
-        const int64_t mine0 = it.slot * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax;
+        const PartState ps = load_part(sh_part);
+        if (static_cast<int64_t>(epoch) * ps.T + tb >= ps.K) break;
+        const int pT = ps.T, plo = ps.lo, phi = ps.hi;
+        const size_t estride = static_cast<size_t>(4) * a.Tmax;
+        int* pflag = a.flags + ps.slot;
+        const int64_t mine0 = ps.slot * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax;
         real* mine = edges + mine0;
-        if (Win::touches(warp, lo, lo + T) || Win::touches(warp, hi - T, hi)) {
+        if (Win::touches(warp, plo, plo + pT) || Win::touches(warp, phi - pT, phi)) {
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int p = Win::pos(warp, lane, e);
             if (!Win::owner(warp, lane, e, nwarps)) continue;
-            if (p >= lo && p < lo + T && index_ok(a.status, mine0 + (p - lo), a.edges_len)) st_cg(mine + (p - lo), v[e]);
-            if (p >= hi - T && p < hi && index_ok(a.status, mine0 + a.Tmax + (p - (hi - T)), a.edges_len))
-              st_cg(mine + a.Tmax + (p - (hi - T)), v[e]);
+            if (p >= plo && p < plo + pT && index_ok(a.status, mine0 + (p - plo), a.edges_len)) st_cg(mine + (p - plo), v[e]);
+            if (p >= phi - pT && p < phi && index_ok(a.status, mine0 + a.Tmax + (p - (phi - pT)), a.edges_len))
+              st_cg(mine + a.Tmax + (p - (phi - pT)), v[e]);
           }
         }
         __syncthreads();
         if (tid == 0) {
           // A release at GPU scope after the CTA barrier orders every thread's
           // edge stores before the flag (cumulativity); no separate fence.
-          if (it.slot != a.stall_slot) st_release_gpu(myflag, epoch + 2);
+          if (ps.slot != a.stall_slot) st_release_gpu(pflag, epoch + 2);
           bool w = true;
-          if (it.part > 0) w = wait_flag_at_least(myflag - 1, epoch + 2, a.status, a.spin_limit_ns);
-          if (w && it.part + 1 < it.nparts) w = wait_flag_at_least(myflag + 1, epoch + 2, a.status, a.spin_limit_ns);
+          if (ps.part > 0) w = wait_flag_at_least(pflag - 1, epoch + 2, a.status, a.spin_limit_ns);
+          if (w && ps.part + 1 < ps.nparts) w = wait_flag_at_least(pflag + 1, epoch + 2, a.status, a.spin_limit_ns);
           sh_ok = w;
         }
         __syncthreads();
@@ -366,42 +411,46 @@ __global__ void __launch_bounds__(max_tile_threads(sizeof(real), E), 1) batched_
           ok = false;
           break;
         }
-        if (it.part > 0 && Win::touches(warp, lo - T, lo)) {
-          const int64_t left0 = (it.slot - 1) * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax + a.Tmax;
+        if (ps.part > 0 && Win::touches(warp, plo - pT, plo)) {
+          const int64_t left0 = (ps.slot - 1) * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax + a.Tmax;
           const real* left = edges + left0;
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int p = Win::pos(warp, lane, e);
-            if (p >= lo - T && p < lo && index_ok(a.status, left0 + (p - (lo - T)), a.edges_len))
-              v[e] = ld_cg(left + (p - (lo - T)));
+            if (p >= plo - pT && p < plo && index_ok(a.status, left0 + (p - (plo - pT)), a.edges_len))
+              v[e] = ld_cg(left + (p - (plo - pT)));
           }
         }
-        if (it.part + 1 < it.nparts && Win::touches(warp, hi, hi + T)) {
-          const int64_t right0 = (it.slot + 1) * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax;
+        if (ps.part + 1 < ps.nparts && Win::touches(warp, phi, phi + pT)) {
+          const int64_t right0 = (ps.slot + 1) * static_cast<int64_t>(estride) + (epoch & 1) * 2 * a.Tmax;
           const real* right = edges + right0;
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int p = Win::pos(warp, lane, e);
-            if (p >= hi && p < hi + T && index_ok(a.status, right0 + (p - hi), a.edges_len)) v[e] = ld_cg(right + (p - hi));
+            if (p >= phi && p < phi + pT && index_ok(a.status, right0 + (p - phi), a.edges_len))
+              v[e] = ld_cg(right + (p - phi));
           }
         }
-        ++epoch;
       }
       if (!ok) return;  // CTA-uniform (sh_ok); the status word holds the failure
+      const PartState ps = load_part(sh_part);
+      int* pflag = a.flags + ps.slot;
       // The neighbours must have loaded their halos before our points change.
       if (tid == 0) {
         bool w = true;
-        if (it.part > 0) w = wait_flag_at_least(myflag - 1, 1, a.status, a.spin_limit_ns);
-        if (w && it.part + 1 < it.nparts) w = wait_flag_at_least(myflag + 1, 1, a.status, a.spin_limit_ns);
+        if (ps.part > 0) w = wait_flag_at_least(pflag - 1, 1, a.status, a.spin_limit_ns);
+        if (w && ps.part + 1 < ps.nparts) w = wait_flag_at_least(pflag + 1, 1, a.status, a.spin_limit_ns);
         sh_ok = w;
       }
       __syncthreads();
       if (!sh_ok) return;
+      real* px = u + ps.offset;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = Win::pos(warp, lane, e);
-        if (p >= lo && p < hi && Win::owner(warp, lane, e, nwarps) && index_ok(a.status, rd.offset + a0 - lo + p, a.u_len))
-          x[a0 - lo + p] = v[e];
+        if (p >= ps.lo && p < ps.hi && Win::owner(warp, lane, e, nwarps) &&
+            index_ok(a.status, ps.offset + ps.a0 - ps.lo + p, a.u_len))
+          px[ps.a0 - ps.lo + p] = v[e];
       }
     }
     __syncthreads();
