@@ -201,8 +201,20 @@ struct WindowShared {
 // How a warp steps: every point updated; the first and/or last slot of some
 // lanes held (a Dirichlet end placed at a slot known at compile time: two
 // selects per step); any other points held (a select per point); or every
-// point held (padding warps: no arithmetic).
-enum TileMode { kTileFree = 0, kTileMasked = 1, kTileIdle = 2, kTileEnds = 3 };
+// point held (padding warps: no arithmetic).  kTileSlot + s (1 <= s <= E-2):
+// slot 0 and slot s of some lanes held -- a rod's first point and its last
+// point u_N, which falls at slot (N-1) mod E -- as a mode of its own for
+// every s, so that the two holds cost two selects per step instead of one
+// per point (measured: a warp in the per-point mode slows its whole CTA by a
+// quarter, as every warp waits for it at each refresh).
+enum TileMode { kTileFree = 0, kTileMasked = 1, kTileIdle = 2, kTileEnds = 3, kTileSlot = 4 };
+
+// Whether slot e may be held in mode kMode (then its `fixed` bit decides).
+template <int E, int kMode>
+__device__ __forceinline__ constexpr bool held_slot(int e) {
+  return kMode == kTileMasked || (kMode == kTileEnds && (e == 0 || e == E - 1)) ||
+         (kMode >= kTileSlot && (e == 0 || e == kMode - kTileSlot));
+}
 
 // Kernels hold only the Dirichlet ends: positions outside the rod or past the
 // tile are stepped like any other (their values are never stored and reach no
@@ -217,6 +229,19 @@ __device__ __forceinline__ int tile_mode(unsigned fixed) {
   return __any_sync(kFullMask, (fixed & ~ends) != 0u) ? kTileMasked : kTileEnds;
 }
 
+// tile_mode, with the slot modes: a warp whose held points are at slot 0 and
+// at one other slot s (the same in every lane) steps in mode kTileSlot + s.
+// Only for E <= 16 (the number of step-loop copies grows with E).
+template <int E>
+__device__ __forceinline__ int tile_mode_slot(unsigned fixed) {
+  const int mode = tile_mode<E>(fixed);
+  if (E > 16 || mode != kTileMasked) return mode;
+  const unsigned inner = __reduce_or_sync(kFullMask, fixed) & ~1u;
+  if ((inner & (inner - 1u)) != 0u) return kTileMasked;  // two inner slots
+  const int s = __ffs(static_cast<int>(inner)) - 1;
+  return (s >= 1 && s <= E - 2) ? kTileSlot + s : kTileMasked;
+}
+
 // One step of one warp (no other warp involved).
 template <typename real, int E, int kMode>
 __device__ __forceinline__ void warp_step(real (&v)[E], unsigned fixed, Coef<real> c) {
@@ -229,7 +254,7 @@ __device__ __forceinline__ void warp_step(real (&v)[E], unsigned fixed, Coef<rea
     const real cur = v[e];
     const real nxt = (e + 1 < E) ? v[e + 1] : right;
     const real nv = ftcs(c.r, c.one, prev, cur, nxt);
-    if (kMode == kTileMasked || (kMode == kTileEnds && (e == 0 || e == E - 1))) {
+    if (held_slot<E, kMode>(e)) {
       v[e] = ((fixed >> e) & 1u) ? cur : nv;
     } else {
       v[e] = nv;
@@ -248,7 +273,7 @@ __device__ __forceinline__ void warp_step_to(const real (&in)[E], real (&out)[E]
     const real prev = e > 0 ? in[e - 1] : left;
     const real nxt = (e + 1 < E) ? in[e + 1] : right;
     const real nv = ftcs(c.r, c.one, prev, in[e], nxt);
-    if (kMode == kTileMasked || (kMode == kTileEnds && (e == 0 || e == E - 1))) {
+    if (held_slot<E, kMode>(e)) {
       out[e] = ((fixed >> e) & 1u) ? in[e] : nv;
     } else {
       out[e] = nv;
@@ -381,6 +406,45 @@ __device__ __forceinline__ void warp_advance(int mode, real (&v)[E], unsigned fi
   else
     warp_advance_mode<real, E, H, kTileIdle>(v, fixed, c, sh, parity, warp, lane, nwarps, nthreads, steps,
                                              final_refresh);
+}
+
+// warp_advance with the slot modes of tile_mode_slot (one copy of the step
+// loop per slot, chosen once per call).
+template <typename real, int E, int H, int S = 1>
+__device__ __forceinline__ void warp_advance_slot(int s, real (&v)[E], unsigned fixed, Coef<real> c,
+                                                  WindowShared<real, H>& sh, int& parity, int warp, int lane,
+                                                  int nwarps, unsigned nthreads, int steps, bool final_refresh) {
+  if constexpr (S <= E - 2) {
+    if (s == S)
+      warp_advance_mode<real, E, H, kTileSlot + S>(v, fixed, c, sh, parity, warp, lane, nwarps, nthreads, steps,
+                                                   final_refresh);
+    else
+      warp_advance_slot<real, E, H, S + 1>(s, v, fixed, c, sh, parity, warp, lane, nwarps, nthreads, steps,
+                                           final_refresh);
+  }
+}
+template <typename real, int E, int H>
+__device__ __forceinline__ void warp_advance_slots(int mode, real (&v)[E], unsigned fixed, Coef<real> c,
+                                                   WindowShared<real, H>& sh, int& parity, int warp, int lane,
+                                                   int nwarps, unsigned nthreads, int steps,
+                                                   bool final_refresh = true) {
+  if (steps <= 0) return;
+  if (mode >= kTileSlot)
+    warp_advance_slot<real, E, H>(mode - kTileSlot, v, fixed, c, sh, parity, warp, lane, nwarps, nthreads, steps,
+                                  final_refresh);
+  else
+    warp_advance<real, E, H>(mode, v, fixed, c, sh, parity, warp, lane, nwarps, nthreads, steps, final_refresh);
+}
+
+// warp_steps with the slot modes (a warp that holds a whole rod).
+template <typename real, int E, int S = 1>
+__device__ __forceinline__ void warp_steps_slot(int s, real (&v)[E], unsigned fixed, Coef<real> c, int64_t n) {
+  if constexpr (S <= E - 2) {
+    if (s == S)
+      warp_steps<real, E, kTileSlot + S>(v, fixed, c, n);
+    else
+      warp_steps_slot<real, E, S + 1>(s, v, fixed, c, n);
+  }
 }
 
 __device__ __forceinline__ int ld_volatile_shared(const int* p) { return *reinterpret_cast<const volatile int*>(p); }

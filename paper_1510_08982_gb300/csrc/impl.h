@@ -258,6 +258,9 @@ struct BatchRun {
 // per thread (4, 8 or 16).
 int launch_batched(const BatchRun& a, int dtype, int E, int threads, int grid, cudaStream_t st);
 int max_resident_batched(int dtype, int E, int threads);
+// The FP32 instances (compiled in their own translation unit).
+int launch_batched_f32(const BatchRun& a, int E, int threads, int grid, cudaStream_t st);
+int max_resident_batched_f32(int E, int threads);
 
 // ------------------------------------------------------------ adjoint
 
