@@ -157,3 +157,146 @@ class AsyncProtocol:
         for t in threads:
             t.join(timeout=self.limit_s * (self.K + 10))
         return self.status
+
+
+class BlockedProtocol:
+    """CPU-thread model of the blocked asynchronous run's exchange (strips of
+    T edge points once per block of T steps) on segments given by S+1
+    offsets: the on-chip blocked kernel's segments and the parts of a split
+    rod in the batched launch.
+
+    Segment s starts block b from a tile of its own points and T halo points
+    per side (clipped at the rod's ends), the halos being the neighbours'
+    strips of version v -- their first / last T points after v blocks.  In a
+    free run v is the newest version published, not newer than b, waiting
+    (with a time limit) only while v < b-q+1; a replay takes exactly
+    v = b - d.  It sweeps the tile tb = min(T, K - bT) times (tile edges and
+    Dirichlet ends held), keeps its own points, writes its first and last T
+    points as strip version b+1 into ring slot (b+1) mod R and publishes the
+    version.  The rings hold R >= 2q versions, every entry tagged with its
+    version, so a read of an overwritten slot is detected.  Delays are
+    recorded as trace[b][boundary][side], side 0 the left segment's read of
+    its right neighbour, side 1 the right segment's read of its left one.
+    The arithmetic is numpy's unfused one (the model checks the protocol, not
+    the rounding)."""
+
+    def __init__(self, u0, r, c1, cN, offsets, q, T, K, trace=None, stall=-1, limit_s=2.0, jitter_s=2e-4, seed=0):
+        self.u = np.array(u0, dtype=np.float64)
+        self.u[0], self.u[-1] = c1, cN
+        self.N, self.r, self.q, self.T, self.K = len(self.u), float(r), int(q), int(T), int(K)
+        self.off = [int(x) for x in offsets]
+        self.S = len(self.off) - 1
+        if self.off[0] != 0 or self.off[-1] != self.N:
+            raise ValueError("offsets must run from 0 to N")
+        for s in range(1, self.S - 1):
+            if self.off[s + 1] - self.off[s] < self.T:
+                raise ValueError("inner segments need at least T points")
+        self.R = 1
+        while self.R < 2 * self.q:
+            self.R *= 2
+        self.nb = (self.K + self.T - 1) // self.T
+        self.trace_in = None if trace is None else np.asarray(trace, dtype=np.uint8).reshape(self.nb, self.S - 1, 2)
+        self.trace = np.zeros((self.nb, max(self.S - 1, 0), 2), dtype=np.uint8)
+        self.stall = stall
+        self.limit_s = limit_s
+        self.jitter_s = jitter_s
+        self.seed = seed
+        # strips[s][side][slot] = (version, points); side 0: first T points, 1: last T points
+        self.strips = [[[(-1, None)] * self.R for _ in range(2)] for _ in range(self.S)]
+        self.prog = [0] * self.S
+        self.lock = threading.Lock()
+        self.status = "ok"
+        for s in range(self.S):
+            lo, hi = self.off[s], self.off[s + 1]
+            self.strips[s][0][0] = (0, self.u[lo:min(lo + self.T, hi)].copy())
+            self.strips[s][1][0] = (0, self.u[max(hi - self.T, lo):hi].copy())
+        self.max_lead = 0
+
+    def _fail(self, what):
+        with self.lock:
+            if self.status == "ok":
+                self.status = what
+
+    def _read(self, nb, side, b, tidx, d_replay):
+        need = b - min(d_replay, b) if d_replay is not None else max(b - self.q + 1, 0)
+        if d_replay is not None and d_replay >= self.q:
+            self._fail("trace")
+            return None
+        t0 = time.monotonic()
+        while True:
+            with self.lock:
+                V = self.prog[nb]
+                if self.status != "ok":
+                    return None
+                if V >= need:
+                    v = need if d_replay is not None else min(V, b)
+                    ver, pts = self.strips[nb][side][v % self.R]
+                    if ver != v:
+                        raise ProtocolError("segment read strip version %d from a slot holding version %d" % (v, ver))
+                    if v > b:
+                        raise ProtocolError("read a strip newer than the block")
+                    self.trace[b][tidx[0]][tidx[1]] = b - v
+                    return pts.copy()
+            if time.monotonic() - t0 > self.limit_s:
+                self._fail("timeout")
+                return None
+            time.sleep(0)
+
+    def _segment(self, s):
+        rng = random.Random(self.seed * 1000 + s)
+        lo, hi = self.off[s], self.off[s + 1]
+        tlo, thi = max(lo - self.T, 0), min(hi + self.T, self.N)  # the tile [tlo, thi)
+        own = self.u[lo:hi].copy()
+        for b in range(self.nb):
+            if self.status != "ok":
+                return
+            if self.jitter_s:
+                time.sleep(rng.random() * self.jitter_s)
+            x = np.empty(thi - tlo)
+            x[lo - tlo:hi - tlo] = own
+            if s > 0:
+                d = None if self.trace_in is None else int(self.trace_in[b][s - 1][1])
+                pts = self._read(s - 1, 1, b, (s - 1, 1), d)
+                if pts is None:
+                    return
+                x[:lo - tlo] = pts[len(pts) - (lo - tlo):]
+            if s + 1 < self.S:
+                d = None if self.trace_in is None else int(self.trace_in[b][s][0])
+                pts = self._read(s + 1, 0, b, (s, 0), d)
+                if pts is None:
+                    return
+                x[hi - tlo:] = pts[:thi - hi]
+            for _ in range(min(self.T, self.K - b * self.T)):
+                y = x.copy()  # the tile's two outermost points are held
+                y[1:-1] = self.r * ((x[2:] - 2.0 * x[1:-1]) + x[:-2]) + x[1:-1]
+                if tlo == 0:
+                    y[0] = self.u[0]  # the Dirichlet ends (held)
+                if thi == self.N:
+                    y[-1] = self.u[-1]
+                x = y
+            own = x[lo - tlo:hi - tlo].copy()
+            if s == self.stall:
+                continue  # never publishes
+            with self.lock:
+                slot = (b + 1) % self.R
+                self.strips[s][0][slot] = (b + 1, own[:min(self.T, hi - lo)].copy())
+                self.strips[s][1][slot] = (b + 1, own[max(hi - lo - self.T, 0):].copy())
+                self.prog[s] = b + 1
+                lead = max((b + 1) - self.prog[n] for n in (s - 1, s + 1) if 0 <= n < self.S) if self.S > 1 else 0
+                self.max_lead = max(self.max_lead, lead)
+        with self.lock:
+            self.u[lo:hi] = own
+
+    def _segment_checked(self, s):
+        try:
+            self._segment(s)
+        except ProtocolError as e:
+            self._fail("protocol: %s" % e)
+
+    def run(self):
+        threads = [threading.Thread(target=self._segment_checked, args=(s,), daemon=True) for s in range(self.S)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join(timeout=self.limit_s * (self.nb + 10))
+        return self.status
