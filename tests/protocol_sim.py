@@ -178,25 +178,35 @@ class BlockedProtocol:
     recorded as trace[b][boundary][side], side 0 the left segment's read of
     its right neighbour, side 1 the right segment's read of its left one.
     The arithmetic is numpy's unfused one (the model checks the protocol, not
-    the rounding)."""
+    the rounding).  periodic=True: the segments form a ring (Section 5.3):
+    segment s's neighbours are s-1 and s+1 mod S, no point is held but the
+    tile's two outermost ones, boundary b joins segments b and b+1 mod S and
+    the trace is [ceil(K/T)][S][2]."""
 
-    def __init__(self, u0, r, c1, cN, offsets, q, T, K, trace=None, stall=-1, limit_s=2.0, jitter_s=2e-4, seed=0):
+    def __init__(self, u0, r, c1, cN, offsets, q, T, K, trace=None, stall=-1, limit_s=2.0, jitter_s=2e-4, seed=0,
+                 periodic=False):
         self.u = np.array(u0, dtype=np.float64)
-        self.u[0], self.u[-1] = c1, cN
+        self.periodic = bool(periodic)
+        if not self.periodic:
+            self.u[0], self.u[-1] = c1, cN
         self.N, self.r, self.q, self.T, self.K = len(self.u), float(r), int(q), int(T), int(K)
         self.off = [int(x) for x in offsets]
         self.S = len(self.off) - 1
         if self.off[0] != 0 or self.off[-1] != self.N:
             raise ValueError("offsets must run from 0 to N")
-        for s in range(1, self.S - 1):
+        inner = range(self.S) if self.periodic else range(1, self.S - 1)
+        for s in inner:
             if self.off[s + 1] - self.off[s] < self.T:
-                raise ValueError("inner segments need at least T points")
+                raise ValueError("segments with a neighbour on both sides need at least T points")
+        if self.periodic and self.S < 2:
+            raise ValueError("a ring needs at least two segments")
         self.R = 1
         while self.R < 2 * self.q:
             self.R *= 2
         self.nb = (self.K + self.T - 1) // self.T
-        self.trace_in = None if trace is None else np.asarray(trace, dtype=np.uint8).reshape(self.nb, self.S - 1, 2)
-        self.trace = np.zeros((self.nb, max(self.S - 1, 0), 2), dtype=np.uint8)
+        self.nbnd = self.S if self.periodic else self.S - 1  # boundaries
+        self.trace_in = None if trace is None else np.asarray(trace, dtype=np.uint8).reshape(self.nb, self.nbnd, 2)
+        self.trace = np.zeros((self.nb, max(self.nbnd, 0), 2), dtype=np.uint8)
         self.stall = stall
         self.limit_s = limit_s
         self.jitter_s = jitter_s
@@ -242,10 +252,19 @@ class BlockedProtocol:
                 return None
             time.sleep(0)
 
+    def _neighbours(self, s):
+        if self.periodic:
+            return (s - 1) % self.S, (s + 1) % self.S
+        return (s - 1 if s > 0 else -1), (s + 1 if s + 1 < self.S else -1)
+
     def _segment(self, s):
         rng = random.Random(self.seed * 1000 + s)
         lo, hi = self.off[s], self.off[s + 1]
-        tlo, thi = max(lo - self.T, 0), min(hi + self.T, self.N)  # the tile [tlo, thi)
+        if self.periodic:  # the tile [lo - T, hi + T), indices mod N
+            tlo, thi = lo - self.T, hi + self.T
+        else:  # the tile [tlo, thi), clipped at the rod's ends
+            tlo, thi = max(lo - self.T, 0), min(hi + self.T, self.N)
+        sl, sr = self._neighbours(s)
         own = self.u[lo:hi].copy()
         for b in range(self.nb):
             if self.status != "ok":
@@ -254,24 +273,25 @@ class BlockedProtocol:
                 time.sleep(rng.random() * self.jitter_s)
             x = np.empty(thi - tlo)
             x[lo - tlo:hi - tlo] = own
-            if s > 0:
-                d = None if self.trace_in is None else int(self.trace_in[b][s - 1][1])
-                pts = self._read(s - 1, 1, b, (s - 1, 1), d)
+            if sl >= 0:
+                bnd = sl if self.periodic else s - 1  # boundary sl joins sl and s
+                d = None if self.trace_in is None else int(self.trace_in[b][bnd][1])
+                pts = self._read(sl, 1, b, (bnd, 1), d)
                 if pts is None:
                     return
                 x[:lo - tlo] = pts[len(pts) - (lo - tlo):]
-            if s + 1 < self.S:
+            if sr >= 0:
                 d = None if self.trace_in is None else int(self.trace_in[b][s][0])
-                pts = self._read(s + 1, 0, b, (s, 0), d)
+                pts = self._read(sr, 0, b, (s, 0), d)
                 if pts is None:
                     return
                 x[hi - tlo:] = pts[:thi - hi]
             for _ in range(min(self.T, self.K - b * self.T)):
                 y = x.copy()  # the tile's two outermost points are held
                 y[1:-1] = self.r * ((x[2:] - 2.0 * x[1:-1]) + x[:-2]) + x[1:-1]
-                if tlo == 0:
+                if not self.periodic and tlo == 0:
                     y[0] = self.u[0]  # the Dirichlet ends (held)
-                if thi == self.N:
+                if not self.periodic and thi == self.N:
                     y[-1] = self.u[-1]
                 x = y
             own = x[lo - tlo:hi - tlo].copy()
@@ -282,7 +302,7 @@ class BlockedProtocol:
                 self.strips[s][0][slot] = (b + 1, own[:min(self.T, hi - lo)].copy())
                 self.strips[s][1][slot] = (b + 1, own[max(hi - lo - self.T, 0):].copy())
                 self.prog[s] = b + 1
-                lead = max((b + 1) - self.prog[n] for n in (s - 1, s + 1) if 0 <= n < self.S) if self.S > 1 else 0
+                lead = max(((b + 1) - self.prog[n] for n in (sl, sr) if n >= 0), default=0)
                 self.max_lead = max(self.max_lead, lead)
         with self.lock:
             self.u[lo:hi] = own

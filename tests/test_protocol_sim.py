@@ -142,3 +142,21 @@ def test_blocked_bad_trace_entry_is_rejected():
     tr[7, 2, 1] = 2
     p = BlockedProtocol(rod(40, 53), 0.3, 0.0, 0.0, offs, 2, 3, 60, trace=tr, jitter_s=0)
     assert p.run() == "trace"
+
+
+@pytest.mark.parametrize("N,S,q,T,seed", [(64, 4, 3, 5, 0), (50, 2, 2, 7, 1), (90, 6, 4, 3, 2)])
+def test_blocked_periodic_free_run_is_a_run_of_the_ring_model(N, S, q, T, seed):
+    """The ring of Section 5.3 (S = 2: both halos from the one neighbour)."""
+    from tests.protocol_sim import segment_offsets
+    K, r = 140, 0.5
+    u0 = rod(N, 60 + seed)
+    p = BlockedProtocol(u0, r, 0.0, 0.0, segment_offsets(N, S), q, T, K, jitter_s=3e-4, seed=seed, periodic=True)
+    assert p.run() == "ok"
+    tr = p.trace
+    assert tr.shape == ((K + T - 1) // T, S, 2) and tr.max(initial=0) < q
+    ref = oracle.async_blocked_periodic(u0, r, S, q, T, K, tr)
+    assert np.abs(p.u - ref).max() <= 1e-13
+    rep = BlockedProtocol(u0, r, 0.0, 0.0, segment_offsets(N, S), q, T, K, trace=tr, jitter_s=3e-4, seed=seed + 7,
+                          periodic=True)
+    assert rep.run() == "ok"
+    assert np.array_equal(rep.u, p.u)
